@@ -1,0 +1,168 @@
+/*
+ * dugks.h -- C ABI of the GB300 (sm_103a) hot path of the incompressible discrete unified
+ * gas kinetic scheme (DUGKS) with force term of Wu, Shi, Chai and Wang (arXiv 1411.6121).
+ *
+ * One handle (dugks_t) owns one simulation on one CUDA device: the cell-averaged
+ * distribution f~ of the paper (Sec. 2.2, eq. evolution_equation) on a uniform Cartesian
+ * mesh with the D2Q9 or D3Q19 (or D3Q27) velocity set, and everything the time step needs.
+ * Every entry point returns DUGKS_OK (0) or a negative DUGKS_E_* code; none throws,
+ * aborts or exits. dugks_last_error() gives a one-line reason for the last failure on a
+ * handle (or, with a NULL handle, for the last failed dugks_create in this thread).
+ *
+ * Conventions
+ *  - Cells are indexed x fastest: cell (i, j, k) is i + nx*(j + ny*k). Field arrays
+ *    passed in or out are "component-major": component a of cell n is at a*ncell + n.
+ *  - Lattice units are not assumed: dx, RT, rho0, nu and dt are given explicitly. The
+ *    particle speed is c = sqrt(3 RT) (Sec. 2.3), the relaxation time tau = nu / RT.
+ *  - Boundary faces are ordered -x, +x, -y, +y, -z, +z. A periodic face must be paired
+ *    with a periodic opposite face. A wall axis needs at least 2 cells.
+ *  - Work is enqueued on the handle's CUDA stream (opts.stream, or a non-blocking stream
+ *    the handle creates when NULL) and runs asynchronously unless the entry point says
+ *    otherwise.
+ *  - Device memory is owned by the handle and released by dugks_destroy. Caller buffers
+ *    are never retained after a call returns.
+ */
+#ifndef DUGKS_H
+#define DUGKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------------------- */
+#define DUGKS_OK 0
+#define DUGKS_E_INVAL (-1)       /* bad argument (NULL, size, combination)              */
+#define DUGKS_E_CFL (-2)         /* dt > dx / sqrt(3RT): CFL number above one (Sec. 3)  */
+#define DUGKS_E_NOMEM (-3)       /* device or host allocation failed                    */
+#define DUGKS_E_CUDA (-4)        /* a CUDA runtime call failed                          */
+#define DUGKS_E_UNSTABLE (-5)    /* non-finite moments found by the FP64 reduction      */
+#define DUGKS_E_TIMEOUT (-6)     /* dugks_sync ran past its time limit                  */
+#define DUGKS_E_UNSUPPORTED (-7) /* lattice/storage/dimension combination not built     */
+
+/* ---- enumerations ---------------------------------------------------------------- */
+/* Velocity sets (Sec. 2.3): D2Q9 and D3Q27 are the paper's tensor-product sets; D3Q19 is
+ * D3Q27 without its 8 corner velocities (weights 1/3, 1/18, 1/36). Index order is the
+ * paper's: x component slowest. */
+#define DUGKS_D2Q9 9
+#define DUGKS_D3Q19 19
+#define DUGKS_D3Q27 27
+
+/* Storage of f~ in device memory. The stored quantity is the deviation from the rest
+ * equilibrium, g~ = f~ - W_k rho0 (exact algebra: every linear step of the scheme has
+ * coefficients summing to one or zero). F32, BF16 and F16 storage use FP32 arithmetic;
+ * BF16/F16 round to nearest even on store. F64 storage uses FP64 arithmetic throughout. */
+#define DUGKS_STORE_F32 0
+#define DUGKS_STORE_BF16 1
+#define DUGKS_STORE_F16 2
+#define DUGKS_STORE_F64 3
+
+/* Boundary conditions of Sec. 2.4 applied at a domain face. */
+#define DUGKS_BC_PERIODIC 0
+#define DUGKS_BC_NEQ_VELOCITY 1 /* eq. NEQ, velocity condition: u_a = u_w, rho_a = rho(x_c)  */
+#define DUGKS_BC_NEQ_PRESSURE 2 /* eq. NEQ, pressure condition: rho_a = rho0 + p_w/RT, u_a = u(x_c) */
+
+/* ---- parameter records ----------------------------------------------------------- */
+typedef struct {
+    int32_t dim;     /* 2 or 3 */
+    int64_t nx, ny;  /* cells per axis */
+    int64_t nz;      /* 1 in 2D */
+    double dx;       /* uniform spacing, dx = dy = dz */
+} dugks_mesh;
+
+typedef struct {
+    int32_t type;    /* DUGKS_BC_* */
+    double u[3];     /* wall velocity u_w (velocity condition) */
+    double p;        /* wall pressure p_w = (rho_w - rho0) RT (pressure condition) */
+} dugks_face_bc;
+
+typedef struct {
+    dugks_face_bc face[6]; /* -x, +x, -y, +y, -z, +z */
+} dugks_boundaries;
+
+/* Acceleration G(x, t) = (g + field(x)) * cos(omega t) of eq. S (Sec. 2.2). field is a
+ * DEVICE pointer to [dim][ncell] floats or NULL; the handle reads it during every step, so
+ * it must stay valid (and may be rewritten between steps) until it is replaced by
+ * dugks_set_force_field or the handle is destroyed. */
+typedef struct {
+    double g[3];
+    double omega;
+    const float *field;
+} dugks_force;
+
+typedef struct {
+    double rt;              /* RT (default 1/3: lattice units with c = 1)            */
+    double rho0;            /* reference density rho0 (default 1)                    */
+    int32_t store;          /* DUGKS_STORE_* (default F32)                           */
+    void *stream;           /* cudaStream_t to run on (default NULL: own stream)     */
+    int32_t use_graph;      /* 1: dugks_step replays a captured CUDA graph (default) */
+    int32_t tile_x, tile_y; /* 0: autotuned/default tile; else the fused kernel tile */
+} dugks_opts;
+
+typedef struct dugks_s *dugks_t;
+
+/* Fill *opts with the defaults listed above. */
+int dugks_opts_default(dugks_opts *opts);
+
+/* Create a simulation (Sec. 2.2 and Sec. 3): validates the mesh, boundaries and
+ * dt <= dx / sqrt(3RT) (the CFL condition of Sec. 3; DUGKS_E_CFL otherwise), allocates the
+ * state on the current CUDA device and initialises it to the rest state f~ = W rho0.
+ * lattice: DUGKS_D2Q9 (dim 2) or DUGKS_D3Q19 / DUGKS_D3Q27 (dim 3). nu > 0, dt > 0.
+ * force, bcs: required (use DUGKS_BC_PERIODIC everywhere for a periodic box).
+ * opts: NULL for defaults. On success *out receives the handle. */
+int dugks_create(const dugks_mesh *mesh, int32_t lattice, double nu, double dt,
+                 const dugks_force *force, const dugks_boundaries *bcs,
+                 const dugks_opts *opts, dugks_t *out);
+
+/* Initial state as in Sec. 3 ("the equilibrium distribution is initialised by"):
+ * f~ = f_eq(rho0 + p/RT, u) of eq. icfeq, computed on the device. p: HOST [ncell] doubles
+ * or NULL (p = 0); u: HOST [dim][ncell] doubles or NULL (rest). Resets the clock to t = 0.
+ * Synchronous. */
+int dugks_init(dugks_t h, const double *p, const double *u);
+
+/* Advance n >= 0 time steps (the Appendix algorithm, steps 1-10, one fused kernel launch
+ * per step). Asynchronous; returns after enqueueing. */
+int dugks_step(dugks_t h, int64_t n);
+
+/* Macroscopic fields of the current state (eq. macro_values with G(t)):
+ * out[0][n] = p = (rho - rho0) RT, out[1+a][n] = u_a, i.e. [dim+1][ncell] floats.
+ * out_is_device: 1 if out is device memory, 0 for host memory (pinned or pageable).
+ * Synchronous. */
+int dugks_moments(dugks_t h, float *out, int32_t out_is_device);
+
+/* FP64 reductions of the current state (the steady-state criterion of Sec. 3.1 and the
+ * conservation totals): out[0] = ||u - u_prev||_2 / ||u||_2 where u_prev is the velocity
+ * field at the previous dugks_residual call (or at dugks_init; +inf before any), then
+ * stores u as the new u_prev; out[1] = sum rho; out[2+a] = sum rho0 u_a (per cell, no
+ * volume factor). out: HOST array of dim+2 doubles. Returns DUGKS_E_UNSTABLE if any sum
+ * is not finite. Synchronous. */
+int dugks_residual(dugks_t h, double *out);
+
+/* Raw state for checkpoint/restart: g~ = f~ - W rho0 in the storage type, laid out
+ * [Q][nz][ny][nx] (unpadded). dugks_state_bytes gives the size. buf_is_device as above.
+ * The clock (time, step count) is part of the handle, see dugks_get_clock. Synchronous. */
+int dugks_state_bytes(dugks_t h, size_t *bytes);
+int dugks_get_state(dugks_t h, void *buf, size_t bytes, int32_t buf_is_device);
+int dugks_set_state(dugks_t h, const void *buf, size_t bytes, int32_t buf_is_device);
+int dugks_get_clock(dugks_t h, int64_t *step, double *time);
+int dugks_set_clock(dugks_t h, int64_t step);
+
+/* Replace the per-cell acceleration field (device [dim][ncell] floats, or NULL). */
+int dugks_set_force_field(dugks_t h, const float *field);
+
+/* Wait for the handle's stream, polling for at most timeout_s seconds (<= 0: no limit).
+ * DUGKS_E_TIMEOUT if the work has not finished by then (the work keeps running). */
+int dugks_sync(dugks_t h, double timeout_s);
+
+/* Number of kernel launches the handle enqueued since creation (diagnostics). */
+int64_t dugks_launch_count(dugks_t h);
+
+const char *dugks_last_error(dugks_t h);
+void dugks_destroy(dugks_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DUGKS_H */

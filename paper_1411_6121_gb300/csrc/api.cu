@@ -1,0 +1,442 @@
+// api.cu -- host side of the C ABI declared in include/dugks.h.
+//
+// The handle owns two ping-pong state buffers g~ (deviation from the rest equilibrium,
+// layout [Q][nz][ny][px], px = nx rounded up to a multiple of 8 elements), a device step
+// counter that drives the time-dependent force inside captured graphs, the FP64 residual
+// buffers, and a cache of captured CUDA graphs of n-step sequences.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+#include <time.h>
+
+#include <map>
+#include <string>
+#include <utility>
+
+#include "../../include/dugks.h"
+#include "dugks_internal.h"
+
+using namespace dugks;
+
+struct dugks_s {
+    int dim, q, store;
+    int64_t nx, ny, nz, px, ncell;
+    double dx, nu, dt, rt, rho0, c, tau;
+    dugks_force force;
+    dugks_boundaries bcs;
+    cudaStream_t stream;
+    int use_graph, tile_x, tile_y;
+    int own_stream;
+    size_t esize;          // bytes per stored element
+    size_t state_bytes;    // padded device bytes of one buffer
+    void *buf[2];
+    int cur;               // index of the buffer that holds the current state
+    long long *d_step;     // device step counter
+    int64_t step;          // host mirror of the step counter
+    double *d_uprev;       // [dim][ncell] velocity at the previous residual
+    int have_prev;
+    double *d_partials;
+    int res_blocks;
+    double *d_res;         // 8 doubles
+    double *h_res;         // pinned 8 doubles
+    int64_t launches;
+    std::map<std::pair<int64_t, int>, cudaGraphExec_t> graphs;
+    std::string err;
+};
+
+static thread_local std::string g_create_error;
+
+static int fail(dugks_t h, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else g_create_error = buf;
+    return code;
+}
+
+#define CUDA_TRY(h, call)                                                                         \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail((h), DUGKS_E_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                                \
+    } while (0)
+
+static StepParams make_params(const dugks_t h) {
+    StepParams p;
+    memset(&p, 0, sizeof p);
+    p.nx = (int)h->nx;
+    p.ny = (int)h->ny;
+    p.nz = (int)h->nz;
+    p.px = h->px;
+    p.plane = h->px * h->ny;
+    p.dstride = p.plane * h->nz;
+    const double tau = h->tau, dt = h->dt, hh = 0.5 * h->dt;
+    p.rho0 = h->rho0;
+    p.inv_c = (1.0 / h->c);
+    // step 1, eq. f_bar_+
+    p.a1 = ((2 * tau - hh) / (2 * tau + dt));
+    p.b1 = (3 * hh / (2 * tau + dt));
+    p.c1 = (3 * tau * hh / (2 * tau + dt));
+    // step 7, eq. original_f solved for f
+    p.a7 = (2 * tau / (2 * tau + hh));
+    p.b7 = (hh / (2 * tau + hh));
+    p.c7 = (tau * hh / (2 * tau + hh));
+    p.kappa = (hh * h->c / h->dx);
+    p.two_kappa = (dt * h->c / h->dx);
+    p.c_over_rho0 = (h->c / h->rho0);
+    p.wcell = (0.5 * dt);
+    p.wface = (0.5 * hh);
+    for (int a = 0; a < 3; a++) p.g[a] = h->force.g[a];
+    p.field = h->force.field;
+    p.omega = h->force.omega;
+    p.dt = h->dt;
+    p.step_ctr = h->d_step;
+    p.step_off = 0;
+    for (int w = 0; w < 6; w++) {
+        p.bc[w] = h->bcs.face[w].type;
+        for (int a = 0; a < 3; a++) p.bc_u[w][a] = h->bcs.face[w].u[a];
+        p.bc_drho[w] = (h->bcs.face[w].p / h->rt);
+    }
+    p.src = h->buf[h->cur];
+    p.dst = h->buf[h->cur ^ 1];
+    return p;
+}
+
+static cudaError_t launch_one_step(dugks_t h, StepParams &p) {
+    switch (h->q) {
+        case 9: return launch_step_q9(p, h->store, h->tile_x, h->tile_y, h->stream);
+        case 19: return launch_step_q19(p, h->store, h->tile_x, h->tile_y, h->stream);
+        case 27: return launch_step_q27(p, h->store, h->tile_x, h->tile_y, h->stream);
+    }
+    return cudaErrorNotSupported;
+}
+
+extern "C" {
+
+int dugks_opts_default(dugks_opts *o) {
+    if (!o) return DUGKS_E_INVAL;
+    memset(o, 0, sizeof *o);
+    o->rt = 1.0 / 3.0;
+    o->rho0 = 1.0;
+    o->store = DUGKS_STORE_F32;
+    o->stream = NULL;
+    o->use_graph = 1;
+    o->tile_x = 0;
+    o->tile_y = 0;
+    return DUGKS_OK;
+}
+
+const char *dugks_last_error(dugks_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int dugks_create(const dugks_mesh *mesh, int32_t lattice, double nu, double dt, const dugks_force *force,
+                 const dugks_boundaries *bcs, const dugks_opts *opts, dugks_t *out) {
+    if (!out) return fail(NULL, DUGKS_E_INVAL, "out is NULL");
+    *out = NULL;
+    if (!mesh || !force || !bcs) return fail(NULL, DUGKS_E_INVAL, "mesh, force and bcs are required");
+    dugks_opts o;
+    dugks_opts_default(&o);
+    if (opts) o = *opts;
+    const int dim = mesh->dim;
+    if (!(dim == 2 || dim == 3)) return fail(NULL, DUGKS_E_INVAL, "dim must be 2 or 3");
+    if (dim == 2 && lattice != DUGKS_D2Q9) return fail(NULL, DUGKS_E_UNSUPPORTED, "2D needs DUGKS_D2Q9");
+    if (dim == 3 && lattice != DUGKS_D3Q19 && lattice != DUGKS_D3Q27)
+        return fail(NULL, DUGKS_E_UNSUPPORTED, "3D needs DUGKS_D3Q19 or DUGKS_D3Q27");
+    if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || (dim == 2 && mesh->nz != 1))
+        return fail(NULL, DUGKS_E_INVAL, "bad mesh extents");
+    if (mesh->nx > (1 << 30) || mesh->ny > (1 << 30) || mesh->nz > (1 << 30))
+        return fail(NULL, DUGKS_E_INVAL, "mesh extent too large");
+    if (!(mesh->dx > 0) || !(nu > 0) || !(dt > 0) || !(o.rt > 0) || !(o.rho0 > 0))
+        return fail(NULL, DUGKS_E_INVAL, "dx, nu, dt, RT and rho0 must be positive");
+    if (o.store < 0 || o.store > 3) return fail(NULL, DUGKS_E_INVAL, "bad storage type");
+    const double c = sqrt(3.0 * o.rt);
+    if (dt > mesh->dx / c * (1.0 + 1e-12))
+        return fail(NULL, DUGKS_E_CFL, "dt = %g exceeds dx/sqrt(3RT) = %g (CFL number > 1)", dt, mesh->dx / c);
+    const int64_t n[3] = {mesh->nx, mesh->ny, mesh->nz};
+    for (int d = 0; d < 3; d++) {
+        const int lo = bcs->face[2 * d].type, hi = bcs->face[2 * d + 1].type;
+        if (d >= dim) continue;
+        if (lo < 0 || lo > 2 || hi < 0 || hi > 2) return fail(NULL, DUGKS_E_INVAL, "bad boundary type");
+        if ((lo == DUGKS_BC_PERIODIC) != (hi == DUGKS_BC_PERIODIC))
+            return fail(NULL, DUGKS_E_INVAL, "periodic faces must be paired (axis %d)", d);
+        if (lo != DUGKS_BC_PERIODIC && n[d] < 2) return fail(NULL, DUGKS_E_INVAL, "a wall axis needs >= 2 cells");
+    }
+    int tx = o.tile_x, ty = o.tile_y;
+    if (tx == 0 || ty == 0) {
+        tx = o.store == DUGKS_STORE_F64 ? 16 : 32;
+        ty = 8;
+    }
+    if (!((tx == 32 && ty == 8) || (tx == 16 && ty == 8)))
+        return fail(NULL, DUGKS_E_UNSUPPORTED, "tile %dx%d not built", tx, ty);
+
+    dugks_t h = new (std::nothrow) dugks_s();
+    if (!h) return fail(NULL, DUGKS_E_NOMEM, "host allocation failed");
+    h->dim = dim;
+    h->q = lattice;
+    h->store = o.store;
+    h->nx = mesh->nx;
+    h->ny = mesh->ny;
+    h->nz = mesh->nz;
+    h->px = (mesh->nx + 7) / 8 * 8;
+    h->ncell = h->nx * h->ny * h->nz;
+    h->dx = mesh->dx;
+    h->nu = nu;
+    h->dt = dt;
+    h->rt = o.rt;
+    h->rho0 = o.rho0;
+    h->c = c;
+    h->tau = nu / o.rt;
+    h->force = *force;
+    h->bcs = *bcs;
+    h->stream = (cudaStream_t)o.stream;
+    if (!h->stream) {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return fail(NULL, DUGKS_E_CUDA, "stream creation failed");
+        }
+        h->own_stream = 1;
+    }
+    h->use_graph = o.use_graph;
+    h->tile_x = tx;
+    h->tile_y = ty;
+    h->esize = o.store == DUGKS_STORE_F32 ? 4 : (o.store == DUGKS_STORE_F64 ? 8 : 2);
+    h->state_bytes = (size_t)h->q * h->px * h->ny * h->nz * h->esize;
+    h->res_blocks = residual_blocks(h->ncell);
+    int rc = DUGKS_OK;
+    cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, bytes)                                                                         \
+    if (e == cudaSuccess) {                                                                       \
+        e = cudaMalloc((void **)&(ptr), (bytes));                                                 \
+    }
+    ALLOC(h->buf[0], h->state_bytes);
+    ALLOC(h->buf[1], h->state_bytes);
+    ALLOC(h->d_step, sizeof(long long));
+    ALLOC(h->d_uprev, sizeof(double) * dim * h->ncell);
+    ALLOC(h->d_partials, sizeof(double) * 8 * h->res_blocks);
+    ALLOC(h->d_res, sizeof(double) * 8);
+#undef ALLOC
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_res, sizeof(double) * 8);
+    if (e != cudaSuccess) {
+        rc = fail(NULL, e == cudaErrorMemoryAllocation ? DUGKS_E_NOMEM : DUGKS_E_CUDA, "allocation: %s",
+                  cudaGetErrorString(e));
+        cudaGetLastError();
+        dugks_destroy(h);
+        return rc;
+    }
+    // padding columns stay zero forever (never read into the interior)
+    if ((e = cudaMemsetAsync(h->buf[0], 0, h->state_bytes, h->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(h->buf[1], 0, h->state_bytes, h->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(h->d_step, 0, sizeof(long long), h->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
+        rc = fail(NULL, DUGKS_E_CUDA, "initial clear: %s", cudaGetErrorString(e));
+        dugks_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return DUGKS_OK;
+}
+
+void dugks_destroy(dugks_t h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    cudaFree(h->buf[0]);
+    cudaFree(h->buf[1]);
+    cudaFree(h->d_step);
+    cudaFree(h->d_uprev);
+    cudaFree(h->d_partials);
+    cudaFree(h->d_res);
+    if (h->h_res) cudaFreeHost(h->h_res);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int dugks_init(dugks_t h, const double *pres, const double *vel) {
+    if (!h) return DUGKS_E_INVAL;
+    double *dp = NULL, *du = NULL;
+    if (pres) {
+        CUDA_TRY(h, cudaMalloc((void **)&dp, sizeof(double) * h->ncell));
+        CUDA_TRY(h, cudaMemcpyAsync(dp, pres, sizeof(double) * h->ncell, cudaMemcpyHostToDevice, h->stream));
+    }
+    if (vel) {
+        cudaError_t e = cudaMalloc((void **)&du, sizeof(double) * h->dim * h->ncell);
+        if (e != cudaSuccess) {
+            cudaFree(dp);
+            return fail(h, DUGKS_E_NOMEM, "init: %s", cudaGetErrorString(e));
+        }
+        CUDA_TRY(h, cudaMemcpyAsync(du, vel, sizeof(double) * h->dim * h->ncell, cudaMemcpyHostToDevice, h->stream));
+    }
+    h->cur = 0;
+    StepParams p = make_params(h);
+    p.dst = h->buf[0];
+    cudaError_t e = launch_init(h->q, h->store, p, dp, du, h->rt, h->stream);
+    h->launches++;
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_step, 0, sizeof(long long), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(dp);
+    cudaFree(du);
+    if (e != cudaSuccess) return fail(h, DUGKS_E_CUDA, "init: %s", cudaGetErrorString(e));
+    h->step = 0;
+    h->have_prev = 0;
+    return DUGKS_OK;
+}
+
+// Enqueue n steps starting from the current buffer (no graph).
+static int enqueue_steps(dugks_t h, int64_t n) {
+    StepParams p = make_params(h);
+    int cur = h->cur;
+    for (int64_t i = 0; i < n; i++) {
+        p.src = h->buf[cur];
+        p.dst = h->buf[cur ^ 1];
+        p.step_off = (int)i;
+        cudaError_t e = launch_one_step(h, p);
+        if (e != cudaSuccess) return fail(h, DUGKS_E_CUDA, "step launch: %s", cudaGetErrorString(e));
+        cur ^= 1;
+    }
+    cudaError_t e = launch_advance(h->d_step, (long long)n, h->stream);
+    if (e != cudaSuccess) return fail(h, DUGKS_E_CUDA, "advance: %s", cudaGetErrorString(e));
+    return DUGKS_OK;
+}
+
+int dugks_step(dugks_t h, int64_t n) {
+    if (!h || n < 0) return DUGKS_E_INVAL;
+    if (n == 0) return DUGKS_OK;
+    const int64_t chunk = 256;  // graph length
+    int64_t left = n;
+    while (left > 0) {
+        const int64_t m = left >= chunk ? chunk : left;
+        if (h->use_graph && m >= 8) {
+            auto key = std::make_pair(m, h->cur);
+            auto it = h->graphs.find(key);
+            if (it == h->graphs.end()) {
+                cudaGraph_t g;
+                CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+                int rc = enqueue_steps(h, m);
+                cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+                if (rc != DUGKS_OK) return rc;
+                if (e != cudaSuccess) return fail(h, DUGKS_E_CUDA, "capture: %s", cudaGetErrorString(e));
+                cudaGraphExec_t ge;
+                e = cudaGraphInstantiate(&ge, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return fail(h, DUGKS_E_CUDA, "instantiate: %s", cudaGetErrorString(e));
+                it = h->graphs.emplace(key, ge).first;
+            }
+            CUDA_TRY(h, cudaGraphLaunch(it->second, h->stream));
+        } else {
+            int rc = enqueue_steps(h, m);
+            if (rc != DUGKS_OK) return rc;
+        }
+        h->launches += m + 1;
+        if (m & 1) h->cur ^= 1;
+        h->step += m;
+        left -= m;
+    }
+    return DUGKS_OK;
+}
+
+int dugks_moments(dugks_t h, float *out, int32_t out_is_device) {
+    if (!h || !out) return DUGKS_E_INVAL;
+    const size_t bytes = sizeof(float) * (h->dim + 1) * h->ncell;
+    float *d = out;
+    if (!out_is_device) CUDA_TRY(h, cudaMalloc((void **)&d, bytes));
+    StepParams p = make_params(h);
+    cudaError_t e = launch_moments(h->q, h->store, p, h->step * h->dt, h->rt, d, h->stream);
+    h->launches++;
+    if (e == cudaSuccess && !out_is_device) e = cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (!out_is_device) cudaFree(d);
+    if (e != cudaSuccess) return fail(h, DUGKS_E_CUDA, "moments: %s", cudaGetErrorString(e));
+    return DUGKS_OK;
+}
+
+int dugks_residual(dugks_t h, double *out) {
+    if (!h || !out) return DUGKS_E_INVAL;
+    StepParams p = make_params(h);
+    cudaError_t e = launch_residual(h->q, h->store, p, h->step * h->dt, h->rt, h->d_uprev, h->have_prev,
+                                    h->d_partials, h->res_blocks, h->d_res, h->stream);
+    h->launches += 2;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_res, h->d_res, sizeof(double) * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(h, DUGKS_E_CUDA, "residual: %s", cudaGetErrorString(e));
+    const double *s = h->h_res;
+    out[0] = h->have_prev ? (s[1] > 0 ? sqrt(s[0]) / sqrt(s[1]) : (s[0] > 0 ? INFINITY : 0.0)) : INFINITY;
+    out[1] = s[2];
+    for (int a = 0; a < h->dim; a++) out[2 + a] = s[3 + a];
+    h->have_prev = 1;
+    for (int i = 0; i < 3 + h->dim; i++)
+        if (!isfinite(s[i])) return fail(h, DUGKS_E_UNSTABLE, "non-finite moments (slot %d)", i);
+    return DUGKS_OK;
+}
+
+int dugks_state_bytes(dugks_t h, size_t *bytes) {
+    if (!h || !bytes) return DUGKS_E_INVAL;
+    *bytes = (size_t)h->q * h->ncell * h->esize;
+    return DUGKS_OK;
+}
+
+int dugks_get_state(dugks_t h, void *buf, size_t bytes, int32_t buf_is_device) {
+    if (!h || !buf || bytes != (size_t)h->q * h->ncell * h->esize) return DUGKS_E_INVAL;
+    const size_t row = h->nx * h->esize;
+    CUDA_TRY(h, cudaMemcpy2DAsync(buf, row, h->buf[h->cur], h->px * h->esize, row, (size_t)h->q * h->ny * h->nz,
+                                  buf_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return DUGKS_OK;
+}
+
+int dugks_set_state(dugks_t h, const void *buf, size_t bytes, int32_t buf_is_device) {
+    if (!h || !buf || bytes != (size_t)h->q * h->ncell * h->esize) return DUGKS_E_INVAL;
+    const size_t row = h->nx * h->esize;
+    CUDA_TRY(h, cudaMemcpy2DAsync(h->buf[h->cur], h->px * h->esize, buf, row, row, (size_t)h->q * h->ny * h->nz,
+                                  buf_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return DUGKS_OK;
+}
+
+int dugks_get_clock(dugks_t h, int64_t *step, double *time) {
+    if (!h) return DUGKS_E_INVAL;
+    if (step) *step = h->step;
+    if (time) *time = h->step * h->dt;
+    return DUGKS_OK;
+}
+
+int dugks_set_clock(dugks_t h, int64_t step) {
+    if (!h || step < 0) return DUGKS_E_INVAL;
+    long long v = step;
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_step, &v, sizeof v, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->step = step;
+    return DUGKS_OK;
+}
+
+int dugks_set_force_field(dugks_t h, const float *field) {
+    if (!h) return DUGKS_E_INVAL;
+    h->force.field = field;
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);  // parameters are baked into graphs
+    h->graphs.clear();
+    return DUGKS_OK;
+}
+
+int dugks_sync(dugks_t h, double timeout_s) {
+    if (!h) return DUGKS_E_INVAL;
+    struct timespec t0, t1;
+    clock_gettime(CLOCK_MONOTONIC, &t0);
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(h->stream);
+        if (e == cudaSuccess) return DUGKS_OK;
+        if (e != cudaErrorNotReady) return fail(h, DUGKS_E_CUDA, "sync: %s", cudaGetErrorString(e));
+        clock_gettime(CLOCK_MONOTONIC, &t1);
+        const double el = (t1.tv_sec - t0.tv_sec) + 1e-9 * (t1.tv_nsec - t0.tv_nsec);
+        if (timeout_s > 0 && el > timeout_s) return fail(h, DUGKS_E_TIMEOUT, "sync: not done after %.3f s", el);
+        struct timespec ns = {0, 20000};
+        nanosleep(&ns, NULL);
+    }
+}
+
+int64_t dugks_launch_count(dugks_t h) { return h ? h->launches : 0; }
+
+}  // extern "C"

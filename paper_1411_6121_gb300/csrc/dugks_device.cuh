@@ -1,0 +1,249 @@
+// dugks_device.cuh -- device-side building blocks of the fused DUGKS time step (sm_103a).
+//
+// Notation follows Wu, Shi, Chai and Wang (arXiv 1411.6121): f~ cell averages, fbar+ the
+// auxiliary distribution of eq. f_bar_+, fbar the interface distribution at t + h
+// (eq. interfaceEvof), f the original distribution at the interface (eq. original_f).
+// Storage and arithmetic use the deviation from the rest equilibrium, g = f - W rho0: every
+// linear map of the scheme has coefficients summing to one (steps 1, 3, 7, 9) or zero
+// (gradients, the closed-surface flux), so the deviation form is the same algebra with
+// W rho0 removed; f_eq becomes geq = W [drho + rho0 (3 e.u^ + 4.5 (e.u^)^2 - 1.5 u^2)]
+// with u^ = u / c and c = sqrt(3 RT), and the force term S keeps the full f_eq = W rho0 + geq.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dugks {
+
+// ---------------------------------------------------------------------------------
+// Velocity sets (Sec. 2.3). Paper index order: x component slowest.
+// ---------------------------------------------------------------------------------
+template <int Q>
+struct Lat;
+
+template <>
+struct Lat<9> {
+    static constexpr int D = 2;
+    __host__ __device__ static constexpr int e(int k, int a) {
+        return a == 0 ? k / 3 - 1 : (a == 1 ? k % 3 - 1 : 0);
+    }
+    template <class T>
+    __host__ __device__ static constexpr T wt(int k) {
+        return (e(k, 0) == 0 && e(k, 1) == 0) ? T(4) / T(9) : (e(k, 0) == 0 || e(k, 1) == 0) ? T(1) / T(9) : T(1) / T(36);
+    }
+    __host__ __device__ static constexpr float w(int k) { return wt<float>(k); }
+};
+
+template <>
+struct Lat<27> {
+    static constexpr int D = 3;
+    __host__ __device__ static constexpr int e(int k, int a) {
+        return a == 0 ? k / 9 - 1 : (a == 1 ? (k / 3) % 3 - 1 : k % 3 - 1);
+    }
+    __host__ __device__ static constexpr int nnz(int k) {
+        return (e(k, 0) != 0) + (e(k, 1) != 0) + (e(k, 2) != 0);
+    }
+    template <class T>
+    __host__ __device__ static constexpr T wt(int k) {
+        return nnz(k) == 0 ? T(8) / T(27) : nnz(k) == 1 ? T(2) / T(27) : nnz(k) == 2 ? T(1) / T(54) : T(1) / T(216);
+    }
+    __host__ __device__ static constexpr float w(int k) { return wt<float>(k); }
+};
+
+template <>
+struct Lat<19> {
+    static constexpr int D = 3;
+    // D3Q27 index of the k-th D3Q19 velocity (the 8 corners removed, order kept).
+    __host__ __device__ static constexpr int k27(int k) {
+        constexpr int m[19] = {1, 3, 4, 5, 7, 9, 10, 11, 12, 13, 14, 15, 16, 17, 19, 21, 22, 23, 25};
+        return m[k];
+    }
+    __host__ __device__ static constexpr int e(int k, int a) { return Lat<27>::e(k27(k), a); }
+    template <class T>
+    __host__ __device__ static constexpr T wt(int k) {
+        return Lat<27>::nnz(k27(k)) == 0 ? T(1) / T(3) : Lat<27>::nnz(k27(k)) == 1 ? T(1) / T(18) : T(1) / T(36);
+    }
+    __host__ __device__ static constexpr float w(int k) { return wt<float>(k); }
+};
+
+// Number of velocities with a non-zero component along axis d (the directions that carry
+// flux through a face normal to d) and the compact index of velocity k among them.
+template <int Q>
+__host__ __device__ constexpr int n_flux(int d) {
+    int n = 0;
+    for (int k = 0; k < Q; k++) n += Lat<Q>::e(k, d) != 0;
+    return n;
+}
+template <int Q>
+__host__ __device__ constexpr int flux_index(int d, int k) {
+    int n = 0;
+    for (int j = 0; j < k; j++) n += Lat<Q>::e(j, d) != 0;
+    return n;
+}
+
+// ---------------------------------------------------------------------------------
+// Storage types
+// ---------------------------------------------------------------------------------
+template <class S>
+struct Store;
+template <>
+struct Store<float> {
+    __device__ static __forceinline__ float ld(const float *p) { return __ldg(p); }
+    __device__ static __forceinline__ void st(float *p, float v) { *p = v; }
+};
+template <>
+struct Store<__nv_bfloat16> {
+    __device__ static __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    __device__ static __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+template <>
+struct Store<double> {
+    __device__ static __forceinline__ double ld(const double *p) { return __ldg(p); }
+    __device__ static __forceinline__ void st(double *p, double v) { *p = v; }
+};
+template <>
+struct Store<__half> {
+    __device__ static __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
+    __device__ static __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+};
+
+// Arithmetic type for a storage type: FP32 for FP32/BF16/F16 storage, FP64 for FP64.
+template <class S>
+struct Arith { using T = float; };
+template <>
+struct Arith<double> { using T = double; };
+
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+
+// ---------------------------------------------------------------------------------
+// Parameters of one fused step launch (coefficients precomputed on the host in double;
+// the kernel rounds them once to its arithmetic type).
+// ---------------------------------------------------------------------------------
+struct StepParams {
+    int nx, ny, nz;
+    int64_t px;         // row pitch (elements)
+    int64_t plane;      // px * ny
+    int64_t dstride;    // plane * nz: distance between directions
+    double rho0;
+    double inv_c;       // 1 / c
+    double a1, b1, c1;  // step 1 (eq. f_bar_+): fbar+ = a1 g~ + b1 geq + c1 S
+    double a7, b7, c7;  // step 7 (eq. original_f): f = a7 fbar + b7 geq + c7 S
+    double kappa;       // h c / dx: reconstruction (eq. gradient)
+    double two_kappa;   // dt c / dx: flux (eq. evolution_equation)
+    double c_over_rho0; // c / rho0: velocity moment
+    double wcell;       // dt / 2: force weight in the cell moments (eq. macro_values)
+    double wface;       // h / 2: force weight in the interface moments (Appendix step 6)
+    double g[3];        // uniform acceleration
+    const float *field;        // [dim][ncell] acceleration field or null
+    double omega, dt;          // G(t) = (g + field) cos(omega t)
+    const long long *step_ctr; // device step counter: t_n = (*step_ctr + step_off) dt
+    int step_off;
+    int bc[6];                 // DUGKS_BC_* per face
+    double bc_u[6][3];         // wall velocity
+    double bc_drho[6];         // pressure condition: rho_a - rho0 = p_w / RT
+    const void *src;
+    void *dst;
+};
+
+// Coefficients in the arithmetic type T.
+template <class T>
+struct Coef {
+    T rho0, inv_rho0, inv_c, b1, c1, b7, c7, kappa, two_kappa, wcell, wface;
+    __device__ __forceinline__ explicit Coef(const StepParams &p)
+        : rho0((T)p.rho0), inv_rho0((T)(1.0 / p.rho0)), inv_c((T)p.inv_c), b1((T)p.b1), c1((T)p.c1), b7((T)p.b7),
+          c7((T)p.c7), kappa((T)p.kappa), two_kappa((T)p.two_kappa), wcell((T)p.wcell), wface((T)p.wface) {}
+};
+
+// ---------------------------------------------------------------------------------
+// Weights in the arithmetic type. In FP32 a weight like 1/9 carries a relative
+// representation error of ~1e-8 that is the same at every step, so the momentum of the
+// equilibrium, 3 sum_k W_k e_k e_k . m, would differ from m by a fixed factor and the
+// relaxation would drift by that much per step. Splitting each weight into a head and a
+// tail (W = hi + lo to ~1e-16) leaves only unbiased rounding.
+// ---------------------------------------------------------------------------------
+template <int Q, class T>
+__device__ __forceinline__ T wmul(int k, T x) {
+    // k is a compile-time constant after loop unrolling, so these fold to literals
+    const double W = Lat<Q>::template wt<double>(k);
+    if constexpr (sizeof(T) == 4) {
+        const float hi = (float)W;
+        const float lo = (float)(W - (double)hi);
+        return fmaf(lo, x, hi * x);
+    } else {
+        return (T)W * x;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Moments of a deviation distribution g = f - W rho0 (eq. macro_values / Appendix step 6),
+// in units of the particle speed c: drho = sum_k g_k, m = sum_k e_k g_k + rho0 Gh w, where
+// Gh = G / c and w the force weight (dt/2 at cells, h/2 at interfaces). The velocity is
+// u = c m / rho0. Working with m keeps every constant that feeds back into the momentum
+// exactly 1 (no c or 1/rho0 factor inside the relaxation loop).
+// ---------------------------------------------------------------------------------
+template <int Q, class T>
+__device__ __forceinline__ void moments(const T g[Q], const T rGh[3], T w, T &drho, T m[3]) {
+    constexpr int D = Lat<Q>::D;
+    T r = T(0), j[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int k = 0; k < Q; k++) {
+        r += g[k];
+#pragma unroll
+        for (int a = 0; a < D; a++) {
+            if (Lat<Q>::e(k, a) > 0) j[a] += g[k];
+            if (Lat<Q>::e(k, a) < 0) j[a] -= g[k];
+        }
+    }
+    drho = r;
+#pragma unroll
+    for (int a = 0; a < 3; a++) m[a] = (a < D) ? fmaT(rGh[a], w, j[a]) : T(0);
+}
+
+// Equilibrium deviation of eq. icfeq in the variables above:
+//   geq_k = W_k [ drho + 3 e_k.m + (4.5 (e_k.m)^2 - 1.5 m.m) / rho0 ].
+template <int Q, class T>
+__device__ __forceinline__ T geq_k(int k, T drho, const T m[3], T mm, T inv_rho0) {
+    constexpr int D = Lat<Q>::D;
+    T em = T(0);
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        if (Lat<Q>::e(k, a) > 0) em += m[a];
+        if (Lat<Q>::e(k, a) < 0) em -= m[a];
+    }
+    const T x = fmaT(em, T(3), fmaT(inv_rho0 * em, T(4.5) * em, fmaT(T(-1.5) * inv_rho0, mm, drho)));
+    return wmul<Q, T>(k, x);
+}
+
+// Relaxation with the force term, in increment form (coefficients that sum to one in the
+// paper's equations are applied as y = g + b (geq - g) + c S, which keeps exact levels
+// exact in finite precision):
+//   out_k = g_k + b (geq_k - g_k) + c S_k,  S_k = 3 (Gh.e_k - Gh.m / rho0) (W_k rho0 + geq_k)
+// (eq. S with G.(xi - u)/RT = 3 (Gh.e - Gh.u/c) for xi = c e, c^2 = 3 RT).
+// Step 1 (eq. f_bar_+) uses b = 3h/(2tau+dt), c = 3 tau h/(2tau+dt); step 7
+// (eq. original_f) uses b = h/(2tau+h), c = tau h/(2tau+h).
+template <int Q, class T>
+__device__ __forceinline__ void relax(const T g[Q], T drho, const T m[3], const T rGh[3], T rho0, T inv_rho0, T b,
+                                      T c, T out[Q]) {
+    constexpr int D = Lat<Q>::D;
+    const T mm = m[0] * m[0] + m[1] * m[1] + (D == 3 ? m[2] * m[2] : T(0));
+    const T gm = (rGh[0] * m[0] + rGh[1] * m[1] + (D == 3 ? rGh[2] * m[2] : T(0))) * inv_rho0;
+    const T base = fmaT(T(-1.5) * inv_rho0, mm, drho);
+#pragma unroll
+    for (int k = 0; k < Q; k++) {
+        T em = T(0), ge = T(0);
+#pragma unroll
+        for (int a = 0; a < D; a++) {
+            if (Lat<Q>::e(k, a) > 0) { em += m[a]; ge += rGh[a]; }
+            if (Lat<Q>::e(k, a) < 0) { em -= m[a]; ge -= rGh[a]; }
+        }
+        const T geq = wmul<Q, T>(k, fmaT(em, T(3), fmaT(inv_rho0 * em, T(4.5) * em, base)));
+        const T feq = fmaT((T)Lat<Q>::template wt<double>(k), rho0, geq);
+        const T src = T(3) * (ge - gm) * feq;
+        out[k] = fmaT(c, src, fmaT(b, geq - g[k], g[k]));
+    }
+}
+
+}  // namespace dugks

@@ -1,0 +1,30 @@
+// dugks_internal.h -- host-side declarations shared by the translation units of libdugks.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dugks_device.cuh"
+
+namespace dugks {
+
+// Launch one fused step (fused_step<Q, S, TX, TY>) on `stream`. store: DUGKS_STORE_*.
+// Returns cudaSuccess or the launch error; cudaErrorNotSupported for a tile that was not
+// instantiated.
+cudaError_t launch_step_q9(const StepParams &p, int store, int tx, int ty, cudaStream_t stream);
+cudaError_t launch_step_q19(const StepParams &p, int store, int tx, int ty, cudaStream_t stream);
+cudaError_t launch_step_q27(const StepParams &p, int store, int tx, int ty, cudaStream_t stream);
+
+// Auxiliary kernels (aux.cu).
+cudaError_t launch_init(int q, int store, const StepParams &p, const double *pres, const double *vel, double rt,
+                        cudaStream_t stream);
+cudaError_t launch_moments(int q, int store, const StepParams &p, double t, double rt, float *out,
+                           cudaStream_t stream);
+// FP64 residual and totals: per-block partial sums into `partials` ([nblocks][8] doubles),
+// then a fixed-order final sum into `out` (8 doubles on the device).
+cudaError_t launch_residual(int q, int store, const StepParams &p, double t, double rt, double *uprev,
+                            int have_prev, double *partials, int nblocks, double *out, cudaStream_t stream);
+int residual_blocks(int64_t ncell);
+cudaError_t launch_advance(long long *ctr, long long n, cudaStream_t stream);
+
+}  // namespace dugks

@@ -1,0 +1,392 @@
+// dugks_step.cuh -- the fused DUGKS time step (Appendix steps 1-10 of arXiv 1411.6121) as
+// one kernel per step on sm_103a.
+//
+// A CTA owns a TX x TY tile of cell columns and marches through its z range (2.5D
+// blocking). For every z plane it
+//   1. loads g~ for the tile plus a one-cell halo and forms fbar+ (step 1, eq. f_bar_+)
+//      into a three-plane shared-memory ring, filling wall ghost cells by linear
+//      extrapolation (step 2) in the order x, y, z;
+//   2. reconstructs fbar at every x, y and z interface of the tile's cells (steps 3-4,
+//      eq. gradient: two-cell mean, normal difference, cross-point tangential
+//      differences), applies the NEQ condition at wall interfaces (step 5, eq. NEQ),
+//      takes the interface moments (step 6) and forms the original f (step 7,
+//      eq. original_f) for the directions that cross the interface;
+//   3. updates the cell: f~(t+dt) = 4/3 fbar+ - 1/3 f~ - dt/|V| flux (steps 8-9,
+//      eqs. f_tilde_+ and evolution_equation).
+// Each interface value is computed once and used by both adjacent cells, so the discrete
+// flux telescopes exactly (mass conservation to rounding).
+#pragma once
+
+#include "dugks_device.cuh"
+
+namespace dugks {
+
+template <int Q, int TX, int TY, class T = float>
+struct StepShape {
+    static constexpr int D = Lat<Q>::D;
+    static constexpr int RX = TX + 2, RY = TY + 2;      // tile + halo
+    static constexpr int NP = D == 3 ? 3 : 1;           // fbar+ planes held
+    static constexpr int NT = TX * TY;
+    static constexpr int NFX = n_flux<Q>(0), NFY = n_flux<Q>(1), NFZ = D == 3 ? n_flux<Q>(2) : 1;
+    static constexpr int SX = NFX | 1, SY = NFY | 1;    // odd strides: no bank conflicts
+    static constexpr int PLANE = RY * RX * Q;
+    static constexpr size_t smem_floats = (size_t)NP * PLANE + (size_t)TY * (TX + 1) * SX + (size_t)(TY + 1) * TX * SY;
+    static constexpr size_t smem_bytes = smem_floats * sizeof(T);
+};
+
+// Step 4 (eq. gradient): fbar(x_b, t+h) = fbar+(x_b) - h xi . sigma_b for every velocity,
+// at the interface normal to axis d between cells L and R. fbar+(x_b) is the mean of L and
+// R (step 3); the normal gradient is (R - L)/dx; the gradient along a tangential axis t is
+// the difference of the two cross points on the interface, each the mean of the 4 cells
+// around it (step 3), which reduces to [(L+R)_{t+1} - (L+R)_{t-1}] / (4 dx).
+// T1m/T1p (T2m/T2p) point at the (L, R) pairs one cell below/above along the first (second)
+// tangential axis; in 2D the second pair is unused.
+template <int Q, int d, class T>
+__device__ __forceinline__ void reconstruct(const T *L, const T *R, const T *L1m, const T *R1m, const T *L1p,
+                                            const T *R1p, const T *L2m, const T *R2m, const T *L2p, const T *R2p,
+                                            T kappa, T F[Q]) {
+    constexpr int D = Lat<Q>::D;
+    constexpr int t1 = d == 0 ? 1 : 0;
+    constexpr int t2 = d == 2 ? 1 : 2;
+    const T qk = T(0.25) * kappa;
+#pragma unroll
+    for (int k = 0; k < Q; k++) {
+        const T l = L[k], r = R[k];
+        T v = T(0.5) * (l + r);
+        if (Lat<Q>::e(k, d) != 0) v = fmaT(-kappa * (T)Lat<Q>::e(k, d), r - l, v);
+        if (Lat<Q>::e(k, t1) != 0) v = fmaT(-qk * (T)Lat<Q>::e(k, t1), (L1p[k] + R1p[k]) - (L1m[k] + R1m[k]), v);
+        if (D == 3 && Lat<Q>::e(k, t2) != 0)
+            v = fmaT(-qk * (T)Lat<Q>::e(k, t2), (L2p[k] + R2p[k]) - (L2m[k] + R2m[k]), v);
+        F[k] = v;
+    }
+}
+
+// Steps 5-7 at one interface normal to axis d. F: step-4 values (modified in place by the
+// NEQ condition when wall != 0). Fc: step-4 values at x_c, the boundary cell's opposite
+// interface (read only when wall != 0). side: 0 for the low wall (outward normal -e_d),
+// 1 for the high wall. Writes the original f of eq. original_f for the velocities with
+// e_d != 0 into out[flux_index(d, k)] (stride 1).
+template <int Q, int d, class T>
+__device__ __forceinline__ void interface_f(const StepParams &p, const Coef<T> &cf, T F[Q], const T Gh[3], int wall,
+                                            int side, const T *Fc, const T Ghc[3], T *out) {
+    constexpr int D = Lat<Q>::D;
+    if (wall) {
+        // Step 5, eq. NEQ: f(x_w) = f_eq(rho_a, u_a) + [f(x_c) - f_eq(rho_c, u_c)] for
+        // xi . n < 0, applied to fbar (Appendix step 5) with the moments of step 6 at x_c.
+        const int wid = 2 * d + side;
+        T drc, mc[3];
+        moments<Q, T>(Fc, Ghc, cf.wface * cf.rho0, drc, mc);
+        T dra, ma[3];
+        if (p.bc[wid] == 1) {  // velocity condition: u_a = u_w, rho_a = rho_c
+            dra = drc;
+            ma[0] = (T)(p.bc_u[wid][0] * p.rho0 * p.inv_c);
+            ma[1] = (T)(p.bc_u[wid][1] * p.rho0 * p.inv_c);
+            ma[2] = (T)(p.bc_u[wid][2] * p.rho0 * p.inv_c);
+        } else {               // pressure condition: rho_a = rho0 + p_w/RT, u_a = u_c
+            dra = (T)p.bc_drho[wid];
+            ma[0] = mc[0]; ma[1] = mc[1]; ma[2] = mc[2];
+        }
+        const T mma = ma[0] * ma[0] + ma[1] * ma[1] + (D == 3 ? ma[2] * ma[2] : T(0));
+        const T mmc = mc[0] * mc[0] + mc[1] * mc[1] + (D == 3 ? mc[2] * mc[2] : T(0));
+        const int sgn = side == 0 ? -1 : 1;
+#pragma unroll
+        for (int k = 0; k < Q; k++) {
+            if (Lat<Q>::e(k, d) == 0) continue;
+            if (sgn * Lat<Q>::e(k, d) < 0)
+                F[k] = geq_k<Q, T>(k, dra, ma, mma, cf.inv_rho0) + (Fc[k] - geq_k<Q, T>(k, drc, mc, mmc, cf.inv_rho0));
+        }
+    }
+    // Step 6: interface moments (weight h/2 on G). Step 7: original distribution.
+    T drb, mb[3];
+    moments<Q, T>(F, Gh, cf.wface * cf.rho0, drb, mb);
+    T t[Q];
+    relax<Q, T>(F, drb, mb, Gh, cf.rho0, cf.inv_rho0, cf.b7, cf.c7, t);
+#pragma unroll
+    for (int k = 0; k < Q; k++)
+        if (Lat<Q>::e(k, d) != 0) out[flux_index<Q>(d, k)] = t[k];
+}
+
+__device__ __forceinline__ int wrap_idx(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// Acceleration at a cell (unpadded index) in units of c, times the time factor:
+// Gh = (g + field) cos(omega t) / c.
+template <int D, class T>
+__device__ __forceinline__ void cell_G(const StepParams &p, int64_t cell, int64_t ncell, T ct_over_c, T G[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        T v = (a < D) ? (T)p.g[a] : T(0);
+        if (p.field && a < D) v += (T)__ldg(p.field + a * ncell + cell);
+        G[a] = v * ct_over_c;
+    }
+}
+
+template <int Q, class S, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY) fused_step(const StepParams p, int zchunk) {
+    using T = typename Arith<S>::T;
+    using K = StepShape<Q, TX, TY, T>;
+    constexpr int D = K::D;
+    constexpr int RX = K::RX, RY = K::RY, NT = K::NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *smem = reinterpret_cast<T *>(smem_raw);
+    T *phi = smem;                                       // [NP][RY][RX][Q]
+    T *xf = phi + K::NP * K::PLANE;                      // [TY][TX+1][SX]
+    T *yf = xf + TY * (TX + 1) * K::SX;                  // [TY+1][TX][SY]
+    const Coef<T> cf(p);
+
+    const int tid = threadIdx.x;
+    const int lx = tid % TX, ly = tid / TX;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int z0 = blockIdx.z * zchunk;
+    const int z1 = min(nz, z0 + zchunk);
+    const int64_t ncell = (int64_t)nx * ny * nz;
+    const bool perx = p.bc[0] == 0, pery = p.bc[2] == 0, perz = D == 3 ? p.bc[4] == 0 : true;
+    const S *src = reinterpret_cast<const S *>(p.src);
+    S *dst = reinterpret_cast<S *>(p.dst);
+
+    // time factors of G(t) (reading: cells at t_n, interfaces at t_n + h), over c
+    T ct = (T)p.inv_c, cth = (T)p.inv_c;
+    if (p.omega != 0.0) {
+        const double tn = ((double)(*p.step_ctr) + (double)p.step_off) * p.dt;
+        ct = (T)(cos(p.omega * tn) * p.inv_c);
+        cth = (T)(cos(p.omega * (tn + 0.5 * p.dt)) * p.inv_c);
+    }
+
+    auto slot_of = [](int pz) { return D == 3 ? (pz + 3) % 3 : 0; };
+    auto cellp = [&](int slot, int ry, int rx) -> T * { return phi + slot * K::PLANE + (ry * RX + rx) * Q; };
+
+    // ---- step 1 (+ step 2 in x and y) for global plane pz (real or periodic image) ----
+    auto make_plane = [&](int pz) {
+        const int slot = slot_of(pz);
+        const int gz = D == 3 ? wrap_idx(pz, nz) : 0;
+        for (int r = tid; r < RX * RY; r += NT) {
+            const int rx = r % RX, ry = r / RX;
+            int gx = x0 + rx - 1, gy = y0 + ry - 1;
+            T *out = cellp(slot, ry, rx);
+            bool ok = true;
+            if (gx < 0 || gx >= nx) { if (perx && gx >= -1 && gx <= nx) gx = wrap_idx(gx, nx); else ok = false; }
+            if (gy < 0 || gy >= ny) { if (pery && gy >= -1 && gy <= ny) gy = wrap_idx(gy, ny); else ok = false; }
+            if (!ok) {
+#pragma unroll
+                for (int k = 0; k < Q; k++) out[k] = T(0);
+                continue;
+            }
+            const int64_t cell = (int64_t)gx + (int64_t)nx * ((int64_t)gy + (int64_t)ny * gz);
+            const int64_t off = (int64_t)gz * p.plane + (int64_t)gy * p.px + gx;
+            T g[Q];
+#pragma unroll
+            for (int k = 0; k < Q; k++) g[k] = (T)Store<S>::ld(src + k * p.dstride + off);
+            T Gh[3], drho, m[3];
+            cell_G<D, T>(p, cell, ncell, ct, Gh);
+            moments<Q, T>(g, Gh, cf.wcell * cf.rho0, drho, m);
+            relax<Q, T>(g, drho, m, Gh, cf.rho0, cf.inv_rho0, cf.b1, cf.c1, out);
+        }
+        // Step 2 (reading: linear extrapolation ghost = 2 f0 - f1, axis by axis).
+        const bool xwall = !perx && (x0 == 0 || x0 + TX >= nx);
+        const bool ywall = !pery && (y0 == 0 || y0 + TY >= ny);
+        if (xwall) {
+            __syncthreads();
+            for (int r = tid; r < 2 * RY; r += NT) {
+                const int ry = r >> 1, hi = r & 1;
+                const int gy = y0 + ry - 1;
+                if (!((gy >= 0 && gy < ny) || (pery && gy >= -1 && gy <= ny))) continue;
+                const int rx = hi ? nx - x0 + 1 : -x0;  // region index of gx = nx or gx = -1
+                if (rx < 0 || rx >= RX) continue;
+                const int s1 = hi ? -1 : 1;
+                T *o = cellp(slot, ry, rx);
+                const T *a = cellp(slot, ry, rx + s1), *b = cellp(slot, ry, rx + 2 * s1);
+#pragma unroll
+                for (int k = 0; k < Q; k++) o[k] = T(2) * a[k] - b[k];
+            }
+        }
+        if (ywall) {
+            __syncthreads();
+            for (int r = tid; r < 2 * RX; r += NT) {
+                const int rx = r >> 1, hi = r & 1;
+                const int gx = x0 + rx - 1;
+                if (gx < -1 || gx > nx) continue;
+                const int ry = hi ? ny - y0 + 1 : -y0;
+                if (ry < 0 || ry >= RY) continue;
+                const int s1 = hi ? -1 : 1;
+                T *o = cellp(slot, ry, rx);
+                const T *a = cellp(slot, ry + s1, rx), *b = cellp(slot, ry + 2 * s1, rx);
+#pragma unroll
+                for (int k = 0; k < Q; k++) o[k] = T(2) * a[k] - b[k];
+            }
+        }
+    };
+    // z ghost plane (step 2 along z): 2 fbar+(inner) - fbar+(next inner), whole region.
+    auto ghost_plane = [&](int pz) {
+        const int s = slot_of(pz);
+        const int sa = slot_of(pz < 0 ? 0 : nz - 1), sb = slot_of(pz < 0 ? 1 : nz - 2);
+        for (int i = tid; i < K::PLANE; i += NT) phi[s * K::PLANE + i] = T(2) * phi[sa * K::PLANE + i] - phi[sb * K::PLANE + i];
+    };
+    auto plane = [&](int pz) {  // real or periodic planes only
+        make_plane(pz);
+    };
+
+    // Field index for interface G (reading: mean of the two adjacent cells; at a wall the
+    // one adjacent cell).
+    auto face_G = [&](int d, int gx, int gy, int gz, int gfd, T G[3]) {
+        // gfd: interface index along d (between cells gfd-1 and gfd)
+        int nd = d == 0 ? nx : (d == 1 ? ny : nz);
+        bool per = d == 0 ? perx : (d == 1 ? pery : perz);
+        int lo = gfd - 1, hi = gfd;
+        if (per) { lo = wrap_idx(lo, nd); hi = wrap_idx(hi, nd); }
+        else { if (lo < 0) lo = 0; if (hi >= nd) hi = nd - 1; }
+        int cl[3] = {gx, gy, gz}, ch[3] = {gx, gy, gz};
+        cl[d] = lo; ch[d] = hi;
+        const int64_t il = (int64_t)cl[0] + (int64_t)nx * ((int64_t)cl[1] + (int64_t)ny * cl[2]);
+        const int64_t ih = (int64_t)ch[0] + (int64_t)nx * ((int64_t)ch[1] + (int64_t)ny * ch[2]);
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            T v = (a < D) ? (T)p.g[a] : T(0);
+            if (p.field && a < D) v += T(0.5) * ((T)__ldg(p.field + a * ncell + il) + (T)__ldg(p.field + a * ncell + ih));
+            G[a] = v * cth;
+        }
+    };
+
+    // z interface between global planes pl and pl+1 for the thread's own column (3D only).
+    auto zface = [&](int pl, int gfz, T *out) {
+        if constexpr (D == 3) {
+            const int sL = slot_of(pl), sR = slot_of(pl + 1);
+            T F[Q];
+            reconstruct<Q, 2, T>(cellp(sL, ly + 1, lx + 1), cellp(sR, ly + 1, lx + 1), cellp(sL, ly + 1, lx),
+                              cellp(sR, ly + 1, lx), cellp(sL, ly + 1, lx + 2), cellp(sR, ly + 1, lx + 2),
+                              cellp(sL, ly, lx + 1), cellp(sR, ly, lx + 1), cellp(sL, ly + 2, lx + 1),
+                              cellp(sR, ly + 2, lx + 1), cf.kappa, F);
+            const int gx = min(x0 + lx, nx - 1), gy = min(y0 + ly, ny - 1);
+            T Gb[3];
+            face_G(2, gx, gy, 0, gfz, Gb);
+            const int wall = !perz && (gfz == 0 || gfz == nz);
+            T Fc[Q], Gc[3] = {T(0), T(0), T(0)};
+            if (wall) {
+                const int pc = gfz == 0 ? 0 : nz - 2;  // x_c between planes pc and pc+1
+                const int cL = slot_of(pc), cR = slot_of(pc + 1);
+                reconstruct<Q, 2, T>(cellp(cL, ly + 1, lx + 1), cellp(cR, ly + 1, lx + 1), cellp(cL, ly + 1, lx),
+                                  cellp(cR, ly + 1, lx), cellp(cL, ly + 1, lx + 2), cellp(cR, ly + 1, lx + 2),
+                                  cellp(cL, ly, lx + 1), cellp(cR, ly, lx + 1), cellp(cL, ly + 2, lx + 1),
+                                  cellp(cR, ly + 2, lx + 1), cf.kappa, Fc);
+                face_G(2, gx, gy, 0, gfz == 0 ? 1 : nz - 1, Gc);
+            }
+            interface_f<Q, 2, T>(p, cf, F, Gb, wall, gfz == 0 ? 0 : 1, Fc, Gc, out);
+        }
+    };
+
+    // ---- prologue: planes z0-1, z0, z0+1 ----
+    if constexpr (D == 3) {
+        const bool wz = !perz;
+        for (int pz = z0 - 1; pz <= z0 + 1; pz++) {
+            if (wz && (pz < 0 || pz >= nz)) continue;
+            plane(pz);
+        }
+        __syncthreads();
+        for (int pz = z0 - 1; pz <= z0 + 1; pz++) {
+            if (wz && (pz < 0 || pz >= nz)) { ghost_plane(pz); }
+        }
+        __syncthreads();
+    } else {
+        plane(0);
+        __syncthreads();
+    }
+
+    T zf_lo[K::NFZ], zf_hi[K::NFZ];
+    if constexpr (D == 3) zface(z0 - 1, z0, zf_lo);
+
+    for (int kz = z0; kz < z1; kz++) {
+        const int s = slot_of(kz);
+        const int sm = slot_of(kz - 1), sp = slot_of(kz + 1);
+        // ---- x interfaces of plane kz ----
+        for (int f = tid; f < (TX + 1) * TY; f += NT) {
+            const int fx = f % (TX + 1), fy = f / (TX + 1);
+            const int gfx = x0 + fx, gy = y0 + fy;
+            if (gy >= ny || gfx > nx) continue;
+            T F[Q];
+            reconstruct<Q, 0, T>(cellp(s, fy + 1, fx), cellp(s, fy + 1, fx + 1), cellp(s, fy, fx), cellp(s, fy, fx + 1),
+                              cellp(s, fy + 2, fx), cellp(s, fy + 2, fx + 1), cellp(sm, fy + 1, fx),
+                              cellp(sm, fy + 1, fx + 1), cellp(sp, fy + 1, fx), cellp(sp, fy + 1, fx + 1), cf.kappa,
+                              F);
+            T Gb[3];
+            face_G(0, gfx, gy, kz, gfx, Gb);
+            const int wall = !perx && (gfx == 0 || gfx == nx);
+            T Fc[Q], Gc[3] = {T(0), T(0), T(0)};
+            if (wall) {
+                const int cx = gfx == 0 ? fx + 1 : fx - 1;  // x_c: interface 1 or nx-1
+                reconstruct<Q, 0, T>(cellp(s, fy + 1, cx), cellp(s, fy + 1, cx + 1), cellp(s, fy, cx),
+                                  cellp(s, fy, cx + 1), cellp(s, fy + 2, cx), cellp(s, fy + 2, cx + 1),
+                                  cellp(sm, fy + 1, cx), cellp(sm, fy + 1, cx + 1), cellp(sp, fy + 1, cx),
+                                  cellp(sp, fy + 1, cx + 1), cf.kappa, Fc);
+                face_G(0, gfx, gy, kz, gfx == 0 ? 1 : nx - 1, Gc);
+            }
+            interface_f<Q, 0, T>(p, cf, F, Gb, wall, gfx == 0 ? 0 : 1, Fc, Gc, xf + (fy * (TX + 1) + fx) * K::SX);
+        }
+        // ---- y interfaces of plane kz ----
+        for (int f = tid; f < TX * (TY + 1); f += NT) {
+            const int fx = f % TX, fy = f / TX;
+            const int gx = x0 + fx, gfy = y0 + fy;
+            if (gx >= nx || gfy > ny) continue;
+            T F[Q];
+            reconstruct<Q, 1, T>(cellp(s, fy, fx + 1), cellp(s, fy + 1, fx + 1), cellp(s, fy, fx), cellp(s, fy + 1, fx),
+                              cellp(s, fy, fx + 2), cellp(s, fy + 1, fx + 2), cellp(sm, fy, fx + 1),
+                              cellp(sm, fy + 1, fx + 1), cellp(sp, fy, fx + 1), cellp(sp, fy + 1, fx + 1), cf.kappa,
+                              F);
+            T Gb[3];
+            face_G(1, gx, gfy, kz, gfy, Gb);
+            const int wall = !pery && (gfy == 0 || gfy == ny);
+            T Fc[Q], Gc[3] = {T(0), T(0), T(0)};
+            if (wall) {
+                const int cy = gfy == 0 ? fy + 1 : fy - 1;
+                reconstruct<Q, 1, T>(cellp(s, cy, fx + 1), cellp(s, cy + 1, fx + 1), cellp(s, cy, fx),
+                                  cellp(s, cy + 1, fx), cellp(s, cy, fx + 2), cellp(s, cy + 1, fx + 2),
+                                  cellp(sm, cy, fx + 1), cellp(sm, cy + 1, fx + 1), cellp(sp, cy, fx + 1),
+                                  cellp(sp, cy + 1, fx + 1), cf.kappa, Fc);
+                face_G(1, gx, gfy == 0 ? 1 : ny - 1, kz, gfy == 0 ? 1 : ny - 1, Gc);
+            }
+            interface_f<Q, 1, T>(p, cf, F, Gb, wall, gfy == 0 ? 0 : 1, Fc, Gc, yf + (fy * TX + fx) * K::SY);
+        }
+        // ---- z interface kz+1/2 of the own column ----
+        if constexpr (D == 3) zface(kz, kz + 1, zf_hi);
+        __syncthreads();
+
+        // ---- steps 8-9: update of cell (lx, ly, kz) ----
+        const int gx = x0 + lx, gy = y0 + ly;
+        if (gx < nx && gy < ny) {
+            const int64_t off = (int64_t)kz * p.plane + (int64_t)gy * p.px + gx;
+            const T *ph = cellp(s, ly + 1, lx + 1);
+            const T *xm = xf + (ly * (TX + 1) + lx) * K::SX, *xp = xm + K::SX;
+            const T *ym = yf + (ly * TX + lx) * K::SY, *yp = ym + TX * K::SY;
+#pragma unroll
+            for (int k = 0; k < Q; k++) {
+                T acc = T(0);
+                if (Lat<Q>::e(k, 0) != 0) acc = fmaT((T)Lat<Q>::e(k, 0), xp[flux_index<Q>(0, k)] - xm[flux_index<Q>(0, k)], acc);
+                if (Lat<Q>::e(k, 1) != 0) acc = fmaT((T)Lat<Q>::e(k, 1), yp[flux_index<Q>(1, k)] - ym[flux_index<Q>(1, k)], acc);
+                if constexpr (D == 3) {
+                    if (Lat<Q>::e(k, 2) != 0)
+                        acc = fmaT((T)Lat<Q>::e(k, 2), zf_hi[flux_index<Q>(2, k)] - zf_lo[flux_index<Q>(2, k)], acc);
+                }
+                const T gold = (T)Store<S>::ld(src + k * p.dstride + off);
+                // eq. f_tilde_+ in increment form: 4/3 fbar+ - 1/3 f~ = fbar+ + (fbar+ - f~)/3
+                const T v = fmaT(T(1) / T(3), ph[k] - gold, ph[k]) - cf.two_kappa * acc;
+                Store<S>::st(dst + k * p.dstride + off, v);
+            }
+        }
+        if constexpr (D == 3) {
+#pragma unroll
+            for (int j = 0; j < K::NFZ; j++) zf_lo[j] = zf_hi[j];
+            // next plane kz+2 into the slot of kz-1
+            if (kz + 1 < z1) {
+                const int pz = kz + 2;
+                __syncthreads();  // every thread is done reading the slot of kz-1 and the faces
+                if (perz || pz < nz) {
+                    plane(pz);
+                    __syncthreads();
+                } else if (pz == nz) {
+                    ghost_plane(pz);
+                    __syncthreads();
+                }
+            }
+        }
+    }
+}
+
+}  // namespace dugks

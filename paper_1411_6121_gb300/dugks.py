@@ -1,0 +1,238 @@
+"""Thin Python binding of ``libdugks.so`` (the C ABI in ``include/dugks.h``).
+
+Argument marshalling only: every step of the scheme runs in the library's CUDA kernels.
+The entry points keep the C names (``dugks_create``, ``dugks_step``, ...); ``Sim`` wraps a
+handle for convenience. PyTorch supplies streams and device buffers where a caller wants
+device-resident outputs. Loading fails loudly when the library has not been built or no
+CUDA device is present: there is no CPU fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+DUGKS_OK = 0
+ERRORS = {
+    -1: "DUGKS_E_INVAL", -2: "DUGKS_E_CFL", -3: "DUGKS_E_NOMEM", -4: "DUGKS_E_CUDA",
+    -5: "DUGKS_E_UNSTABLE", -6: "DUGKS_E_TIMEOUT", -7: "DUGKS_E_UNSUPPORTED",
+}
+D2Q9, D3Q19, D3Q27 = 9, 19, 27
+STORE_F32, STORE_BF16, STORE_F16, STORE_F64 = 0, 1, 2, 3
+BC_PERIODIC, BC_NEQ_VELOCITY, BC_NEQ_PRESSURE = 0, 1, 2
+
+LIB_PATH = _build.LIB
+
+# Every symbol declared in include/dugks.h (checked by the CPU test suite).
+EXPORTS = [
+    "dugks_opts_default", "dugks_create", "dugks_init", "dugks_step", "dugks_moments",
+    "dugks_residual", "dugks_state_bytes", "dugks_get_state", "dugks_set_state",
+    "dugks_get_clock", "dugks_set_clock", "dugks_set_force_field", "dugks_sync",
+    "dugks_launch_count", "dugks_last_error", "dugks_destroy",
+]
+
+
+class Mesh(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64), ("dx", C.c_double)]
+
+
+class FaceBC(C.Structure):
+    _fields_ = [("type", C.c_int32), ("u", C.c_double * 3), ("p", C.c_double)]
+
+
+class Boundaries(C.Structure):
+    _fields_ = [("face", FaceBC * 6)]
+
+
+class Force(C.Structure):
+    _fields_ = [("g", C.c_double * 3), ("omega", C.c_double), ("field", C.c_void_p)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("rt", C.c_double), ("rho0", C.c_double), ("store", C.c_int32), ("stream", C.c_void_p),
+                ("use_graph", C.c_int32), ("tile_x", C.c_int32), ("tile_y", C.c_int32)]
+
+
+class DugksError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def load(path=None):
+    """Load ``libdugks.so`` (building it first if the sources are newer). Raises if the
+    library cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path) or not _build.up_to_date():
+        _build.build()
+    lib = C.CDLL(path)
+    P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double)
+    lib.dugks_opts_default.argtypes = [C.POINTER(Opts)]
+    lib.dugks_create.argtypes = [C.POINTER(Mesh), I32, C.c_double, C.c_double, C.POINTER(Force),
+                                 C.POINTER(Boundaries), C.POINTER(Opts), C.POINTER(P)]
+    lib.dugks_init.argtypes = [P, D, D]
+    lib.dugks_step.argtypes = [P, I64]
+    lib.dugks_moments.argtypes = [P, P, I32]
+    lib.dugks_residual.argtypes = [P, D]
+    lib.dugks_state_bytes.argtypes = [P, C.POINTER(C.c_size_t)]
+    lib.dugks_get_state.argtypes = [P, P, C.c_size_t, I32]
+    lib.dugks_set_state.argtypes = [P, P, C.c_size_t, I32]
+    lib.dugks_get_clock.argtypes = [P, C.POINTER(C.c_int64), D]
+    lib.dugks_set_clock.argtypes = [P, I64]
+    lib.dugks_set_force_field.argtypes = [P, P]
+    lib.dugks_sync.argtypes = [P, C.c_double]
+    lib.dugks_launch_count.argtypes = [P]
+    lib.dugks_launch_count.restype = I64
+    lib.dugks_last_error.argtypes = [P]
+    lib.dugks_last_error.restype = C.c_char_p
+    lib.dugks_destroy.argtypes = [P]
+    lib.dugks_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _check(rc, h=None):
+    if rc != DUGKS_OK:
+        msg = load().dugks_last_error(h).decode(errors="replace")
+        raise DugksError(rc, msg)
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def make_bcs(bcs):
+    """6 tuples (type, (ux, uy, uz), p) in the order -x, +x, -y, +y, -z, +z (missing
+    entries periodic)."""
+    b = Boundaries()
+    bcs = list(bcs or [])
+    bcs += [(BC_PERIODIC, (0.0, 0.0, 0.0), 0.0)] * (6 - len(bcs))
+    for w, (t, u, p) in enumerate(bcs[:6]):
+        b.face[w].type = int(t)
+        for a in range(3):
+            b.face[w].u[a] = float(u[a]) if a < len(u) else 0.0
+        b.face[w].p = float(p)
+    return b
+
+
+class Sim:
+    """One simulation handle (see ``include/dugks.h``)."""
+
+    def __init__(self, shape, q, nu, dt, dx=1.0, rt=1.0 / 3.0, rho0=1.0, g=(0.0, 0.0, 0.0), omega=0.0,
+                 bcs=None, field=None, store=STORE_F32, stream=None, use_graph=True, tile=None):
+        lib = load()
+        self.lib = lib
+        dim = len(shape)
+        self.dim, self.q = dim, int(q)
+        self.shape = tuple(int(s) for s in shape)
+        self.ncell = int(np.prod(self.shape))
+        m = Mesh(dim, self.shape[0], self.shape[1], self.shape[2] if dim == 3 else 1, float(dx))
+        f = Force()
+        for a in range(3):
+            f.g[a] = float(g[a]) if a < len(g) else 0.0
+        f.omega = float(omega)
+        self._field = field  # keep a reference: the handle reads it every step
+        f.field = None if field is None else int(field.data_ptr())
+        o = Opts()
+        lib.dugks_opts_default(C.byref(o))
+        o.rt, o.rho0, o.store = float(rt), float(rho0), int(store)
+        o.stream = None if stream is None else int(stream)
+        o.use_graph = 1 if use_graph else 0
+        if tile:
+            o.tile_x, o.tile_y = int(tile[0]), int(tile[1])
+        self.bcs = make_bcs(bcs)
+        h = C.c_void_p()
+        rc = lib.dugks_create(C.byref(m), int(q), float(nu), float(dt), C.byref(f), C.byref(self.bcs), C.byref(o),
+                              C.byref(h))
+        _check(rc, None)
+        self.h = h
+        self.store = int(store)
+        self.rt, self.rho0, self.dt = float(rt), float(rho0), float(dt)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dugks_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def init(self, p=None, u=None):
+        p = None if p is None else np.ascontiguousarray(p, dtype=np.float64).ravel()
+        u = None if u is None else np.ascontiguousarray(u, dtype=np.float64).ravel()
+        if p is not None:
+            assert p.size == self.ncell
+        if u is not None:
+            assert u.size == self.dim * self.ncell
+        _check(self.lib.dugks_init(self.h, _dp(p), _dp(u)), self.h)
+
+    def step(self, n=1):
+        _check(self.lib.dugks_step(self.h, int(n)), self.h)
+
+    def moments(self, out=None):
+        """Host numpy [dim+1][ncell] (p, u...) or, with a CUDA torch tensor ``out``, fills it."""
+        if out is not None:
+            _check(self.lib.dugks_moments(self.h, C.c_void_p(out.data_ptr()), 1), self.h)
+            return out
+        a = np.zeros((self.dim + 1, self.ncell), dtype=np.float32)
+        _check(self.lib.dugks_moments(self.h, a.ctypes.data_as(C.c_void_p), 0), self.h)
+        return a
+
+    def residual(self):
+        out = np.zeros(2 + self.dim)
+        _check(self.lib.dugks_residual(self.h, _dp(out)), self.h)
+        return out
+
+    def state_bytes(self):
+        n = C.c_size_t()
+        _check(self.lib.dugks_state_bytes(self.h, C.byref(n)), self.h)
+        return n.value
+
+    def _dtype(self):
+        return {STORE_F32: np.float32, STORE_BF16: np.uint16, STORE_F16: np.float16, STORE_F64: np.float64}[self.store]
+
+    def get_state(self, out=None):
+        """Raw stored deviation g~ = f~ - W rho0, [Q][ncell] in the storage type (bf16 as
+        uint16 bit patterns on the host)."""
+        nb = self.state_bytes()
+        if out is not None:
+            _check(self.lib.dugks_get_state(self.h, C.c_void_p(out.data_ptr()), nb, 1), self.h)
+            return out
+        a = np.zeros((self.q, self.ncell), dtype=self._dtype())
+        _check(self.lib.dugks_get_state(self.h, a.ctypes.data_as(C.c_void_p), nb, 0), self.h)
+        return a
+
+    def set_state(self, a):
+        nb = self.state_bytes()
+        if hasattr(a, "data_ptr"):
+            dev = 1 if a.is_cuda else 0
+            _check(self.lib.dugks_set_state(self.h, C.c_void_p(a.data_ptr()), nb, dev), self.h)
+            return
+        a = np.ascontiguousarray(a, dtype=self._dtype())
+        _check(self.lib.dugks_set_state(self.h, a.ctypes.data_as(C.c_void_p), nb, 0), self.h)
+
+    def clock(self):
+        s = C.c_int64()
+        t = C.c_double()
+        _check(self.lib.dugks_get_clock(self.h, C.byref(s), C.byref(t)), self.h)
+        return s.value, t.value
+
+    def set_clock(self, step):
+        _check(self.lib.dugks_set_clock(self.h, int(step)), self.h)
+
+    def set_force_field(self, field):
+        self._field = field
+        _check(self.lib.dugks_set_force_field(self.h, None if field is None else C.c_void_p(field.data_ptr())), self.h)
+
+    def sync(self, timeout_s=0.0):
+        _check(self.lib.dugks_sync(self.h, float(timeout_s)), self.h)
+
+    def launch_count(self):
+        return self.lib.dugks_launch_count(self.h)

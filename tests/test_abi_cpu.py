@@ -1,0 +1,64 @@
+"""The C-ABI library loads on a machine without a GPU, exports every symbol that
+include/dugks.h declares, and rejects invalid arguments before touching the device."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_1411_6121_gb300 import dugks
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "dugks.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dugks_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_and_binding_agree():
+    assert sorted(dugks.EXPORTS) == _declared()
+
+
+def test_library_exports_every_declared_symbol():
+    lib = dugks.load()
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def _create(**kw):
+    lib = dugks.load()
+    args = dict(dim=2, nx=8, ny=8, nz=1, dx=1.0, q=9, nu=0.1, dt=0.5, rt=1.0 / 3.0, bcs=None)
+    args.update(kw)
+    m = dugks.Mesh(args["dim"], args["nx"], args["ny"], args["nz"], args["dx"])
+    f = dugks.Force()
+    b = dugks.make_bcs(args["bcs"])
+    o = dugks.Opts()
+    lib.dugks_opts_default(C.byref(o))
+    o.rt = args["rt"]
+    h = C.c_void_p()
+    rc = lib.dugks_create(C.byref(m), args["q"], args["nu"], args["dt"], C.byref(f), C.byref(b), C.byref(o), C.byref(h))
+    return rc, h, lib.dugks_last_error(None).decode()
+
+
+def test_cfl_violation_rejected():
+    # Sec. 3: dt = a dx / sqrt(3RT); a > 1 is rejected before any device work
+    rc, h, msg = _create(dt=1.01)
+    assert rc == -2 and not h.value and "CFL" in msg
+
+
+@pytest.mark.parametrize("kw", [dict(dim=4), dict(q=19), dict(dim=3, q=9, nz=4), dict(nx=0), dict(nu=-1.0),
+                                dict(bcs=[(1, (0, 0, 0), 0.0), (0, (0, 0, 0), 0.0)]),
+                                dict(nx=1, bcs=[(1, (0, 0, 0), 0.0), (1, (0, 0, 0), 0.0)])])
+def test_invalid_arguments_rejected(kw):
+    rc, h, msg = _create(**kw)
+    assert rc in (-1, -7) and not h.value and msg
+
+
+def test_null_handle_calls_fail_cleanly():
+    lib = dugks.load()
+    assert lib.dugks_step(None, 1) == -1
+    assert lib.dugks_init(None, None, None) == -1
+    assert lib.dugks_sync(None, 0.1) == -1
+    lib.dugks_destroy(None)
