@@ -1,0 +1,358 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the fused DUGKS time step on GB300.
+
+Workload: the D3Q19 lid-driven cube, 256^3 cells, Re = 1000 (lid u = 0.1 along x on the
++y face, NEQ velocity walls on all six faces; lattice units dx = 1, RT = 1/3, dt = 0.5),
+started from rest. One benchmark step = one time step of the whole hot path (the fused
+step kernel; the FP64 residual/conservation reduction runs every RESIDUAL_EVERY steps
+inside the timed region). The 2.5 GB of state is far larger than the 129 MB L2, so no
+flush is needed between steps.
+
+Reported (one JSON line on rank 0): MLUPS (million cell updates per second) for FP32
+storage, the roofline of the fused kernel against the measured HBM copy bandwidth, the
+BF16-storage and F16-storage forms beside it, the end-to-end MLUPS through the C ABI with
+host buffers, the clocks seen during the timed region, and the FP64 CPU oracle on a
+bounded sample of the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (launched by torchrun) every rank runs an independent replica on its own GPU
+(the workload is one domain; the path is not sharded): weak scaling, value = sum over
+ranks.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "D3Q19 256³ MLUPS + % HBM roofline (fp32 vs bf16-store); adjoint MLUPS"
+N = 256
+RE = 1000.0
+LID = 0.1
+RESIDUAL_EVERY = 100
+Q = 19
+BYTES_PER_VALUE = {0: 4, 1: 2, 2: 2, 3: 8}
+
+
+def workload():
+    from paper_1411_6121_gb300 import workloads as W
+    return W.cavity3d(n=N, re=RE, lid_u=LID, q=Q)
+
+
+def config_json(extra=None):
+    c = {"workload": "D3Q19 lid-driven cube %d^3, Re=1000, lid u=0.1, NEQ walls, from rest" % N,
+         "cells": N ** 3, "lattice": "D3Q19", "global_batch": 1, "seq_len": None,
+         "parallelism": "replicas", "l2": "state 2.5 GB per buffer pair >> 129 MB L2 (no flush needed)",
+         "residual_every": RESIDUAL_EVERY}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha1()
+    for name in ("dugks_step.cuh", "dugks_device.cuh", "step_q19.cu"):
+        with open(os.path.join(ROOT, "paper_1411_6121_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the fused D3Q19 FP32 kernel from the committed ncu summary,
+    if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "fused_step_d3q19_256.md")
+    try:
+        kv = {}
+        for line in open(path):
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                kv[k.strip()] = v.strip().strip("`")
+        if kv.get("kernel_source_sha1") != kernel_source_hash():
+            return None
+        return float(kv["dram_bytes_per_launch_256"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = sorted(v for v in (num(r[1]) for r in rows) if v is not None)
+        mx = max((v for v in (num(r[2]) for r in rows) if v is not None), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = []
+        for i, n in enumerate(names):
+            if any(r[5 + i].lower() == "active" for r in rows):
+                reasons.append(n)
+        # median over samples taken under load (top half of the clock samples' power)
+        pw = [num(r[3]) or 0.0 for r in rows]
+        thr = sorted(pw)[len(pw) // 2]
+        load = sorted(num(r[1]) for r in rows if (num(r[3]) or 0.0) >= thr and num(r[1]) is not None)
+        med = load[len(load) // 2] if load else (sm[len(sm) // 2] if sm else None)
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(pw) if pw else None}
+
+
+def run_form(torch, store, steps, warmup, dev, launches_out=None):
+    """Times `steps` fused steps of the 256^3 cube (storage `store`) after `warmup`.
+    Returns (ms per step, mean fused-kernel ms, launches of our kernels in the region)."""
+    from paper_1411_6121_gb300 import dugks
+    cfg = workload()
+    stream = torch.cuda.Stream(device=dev)
+    sim = dugks.Sim(store=store, stream=stream.cuda_stream, use_graph=False, **cfg)
+    sim.init()
+    sim.residual()
+    for i in range(warmup):
+        sim.step(1)
+    torch.cuda.synchronize(dev)
+    n_ev = steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_ev)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    l0 = sim.launch_count()
+    res = None
+    t0.record(stream)
+    for i in range(steps):
+        ev[i][0].record(stream)
+        sim.step(1)
+        ev[i][1].record(stream)
+        if (i + 1) % RESIDUAL_EVERY == 0:
+            res = sim.residual()  # FP64 residual + conservation (a10), synchronous
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    l1 = sim.launch_count()
+    total_ms = t0.elapsed_time(t1)
+    kern = [a.elapsed_time(b) for a, b in ev]
+    if res is None:
+        res = sim.residual()
+    sim.close()
+    del sim
+    return total_ms / steps, sum(kern) / len(kern), l1 - l0, res
+
+
+def run_e2e(torch, steps, dev):
+    """End to end through the C ABI with host buffers: every step uploads the state from
+    pinned host memory, advances one step and reads the moments back to pinned host memory."""
+    import numpy as np
+    from paper_1411_6121_gb300 import dugks
+    cfg = workload()
+    stream = torch.cuda.Stream(device=dev)
+    sim = dugks.Sim(store=0, stream=stream.cuda_stream, use_graph=False, **cfg)
+    sim.init()
+    nb = sim.state_bytes()
+    host_state = torch.empty(nb // 4, dtype=torch.float32, pin_memory=True)
+    host_mom = torch.empty((4, N ** 3), dtype=torch.float32, pin_memory=True)
+    # one warm pass
+    dptr = host_state.data_ptr()
+    import ctypes as C
+    lib = sim.lib
+    rc = lib.dugks_get_state(sim.h, C.c_void_p(dptr), nb, 0)
+    assert rc == 0
+    for _ in range(2):
+        lib.dugks_set_state(sim.h, C.c_void_p(dptr), nb, 0)
+        sim.step(1)
+        lib.dugks_moments(sim.h, C.c_void_p(host_mom.data_ptr()), 0)
+    torch.cuda.synchronize(dev)
+    t = time.perf_counter()
+    for _ in range(steps):
+        assert lib.dugks_set_state(sim.h, C.c_void_p(dptr), nb, 0) == 0
+        sim.step(1)
+        assert lib.dugks_moments(sim.h, C.c_void_p(host_mom.data_ptr()), 0) == 0
+    el = time.perf_counter() - t
+    sim.close()
+    return el / steps, nb, 4 * 4 * N ** 3
+
+
+def cpu_baseline(seconds=12.0):
+    """The FP64 oracle as it stands on a bounded sample of the same workload: a 40^3 cube
+    at the same Reynolds number (same lid speed, nu scaled with the size), single thread."""
+    from oracle import Oracle
+    from paper_1411_6121_gb300 import workloads as W
+    n = 40
+    cfg = W.cavity3d(n=n, re=RE, lid_u=LID, q=Q)
+    o = Oracle(**cfg)
+    o.init()
+    o.step(1)
+    steps = 0
+    t = time.perf_counter()
+    while True:
+        o.step(1)
+        steps += 1
+        el = time.perf_counter() - t
+        if el > seconds:
+            break
+    return {"value": n ** 3 * steps / el / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "D3Q19 cube %d^3 at Re=1000 (lid 0.1, nu=0.1*%d/1000), %d steps, FP64, 1 thread" % (n, n, steps)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the BF16/F16/e2e/CPU legs")
+    ap.add_argument("--size", type=int, default=256, help="cube edge (256 for the benchmark; smaller for ncu)")
+    ap.add_argument("--store", type=int, default=0, help="storage of the main leg (0 f32, 1 bf16, 2 f16, 3 f64)")
+    args = ap.parse_args()
+    global N
+    N = args.size
+    ws, rank, local = dist_env()
+    warmup = max(3, args.warmup)
+
+    if args.impl == "reference":
+        # The reference arm is the FP64 CPU oracle, as it stands, on the host cores; rank 0
+        # alone runs it. Each step is one oracle step of a 32^3 sample of the workload.
+        if rank != 0:
+            return 0
+        from oracle import Oracle
+        from paper_1411_6121_gb300 import workloads as W
+        n = 32
+        cfg = W.cavity3d(n=n, re=RE, lid_u=LID, q=Q)
+        o = Oracle(**cfg)
+        o.init()
+        o.step(warmup)
+        t = time.perf_counter()
+        o.step(args.steps)
+        el = time.perf_counter() - t
+        v = n ** 3 * args.steps / el / 1e6
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": warmup, "ms_per_step": el / args.steps * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": config_json({"sample": "oracle on a %d^3 cube (same Re and lid), per step" % n}),
+                "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                                 "sample": "D3Q19 cube %d^3, %d steps, FP64, 1 thread" % (n, args.steps)},
+                "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_1411_6121_gb300 import dugks
+    dugks.load()
+
+    sampler = ClockSampler(local)
+    if ws > 1:
+        dist.barrier()
+    sampler.start()
+    ms_step, ms_kernel, launches, res = run_form(torch, args.store, args.steps, warmup, dev)
+    clocks = sampler.stop()
+    if ws > 1:
+        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    cells = N ** 3
+    value = ws * cells / (ms_step * 1e-3) / 1e6
+    peak, peak_kind = hbm_peak()
+    alg_bytes = 2 * Q * BYTES_PER_VALUE[args.store] * cells
+    achieved = alg_bytes / (ms_kernel * 1e-3) / 1e9
+    traffic = profiled_traffic() if (N == 256 and args.store == 0) else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_source": peak_kind, "kernel": "fused_step<19,float,32,8>",
+                "bytes_per_cell_update": 2 * Q * BYTES_PER_VALUE[args.store], "kernel_ms": ms_kernel}
+    extras = {}
+    if not args.no_extras and rank == 0:
+        for store, name in ((1, "bf16_store"), (2, "f16_store")):
+            try:
+                ms_s, ms_k, _, _ = run_form(torch, store, max(20, args.steps // 4), warmup, dev)
+                ach = 2 * Q * BYTES_PER_VALUE[store] * cells / (ms_k * 1e-3) / 1e9
+                extras[name] = {"value": cells / (ms_s * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms_s,
+                                "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                             "frac": ach / peak, "bytes_per_cell_update": 2 * Q * BYTES_PER_VALUE[store]}}
+            except Exception as ex:  # reported, not hidden
+                extras[name] = {"error": str(ex)}
+    e2e = None
+    if rank == 0 and not args.no_extras:
+        sec, bi, bo = run_e2e(torch, max(3, min(10, args.steps // 20)), dev)
+        e2e = {"value": cells / sec / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+               "note": "per step: state upload from pinned host, one step, moments to pinned host, via the C ABI"}
+    cpu = cpu_baseline() if (rank == 0 and ws == 1 and not args.no_extras) else None
+    if ws > 1:
+        dist.barrier()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+                "warmup": warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_json(),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks, "residual": {"rel_du": res[0], "mass": res[1]}}
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -99,6 +99,8 @@ typedef struct {
     void *stream;           /* cudaStream_t to run on (default NULL: own stream)     */
     int32_t use_graph;      /* 1: dugks_step replays a captured CUDA graph (default) */
     int32_t tile_x, tile_y; /* 0: autotuned/default tile; else the fused kernel tile */
+    int32_t kernel;         /* 0: fastest kernel built for the case (default);
+                               1: the reference fused kernel (any lattice/storage)     */
 } dugks_opts;
 
 typedef struct dugks_s *dugks_t;

@@ -27,6 +27,7 @@ struct dugks_s {
     dugks_boundaries bcs;
     cudaStream_t stream;
     int use_graph, tile_x, tile_y;
+    int kernel;            // 0: throughput kernel where built, 1: reference kernel
     int own_stream;
     size_t esize;          // bytes per stored element
     size_t state_bytes;    // padded device bytes of one buffer
@@ -39,6 +40,7 @@ struct dugks_s {
     double *d_partials;
     int res_blocks;
     double *d_res;         // 8 doubles
+    float *d_mom;          // moments staging for host outputs (allocated on first use)
     double *h_res;         // pinned 8 doubles
     int64_t launches;
     std::map<std::pair<int64_t, int>, cudaGraphExec_t> graphs;
@@ -108,6 +110,7 @@ static StepParams make_params(const dugks_t h) {
 }
 
 static cudaError_t launch_one_step(dugks_t h, StepParams &p) {
+    if (h->kernel == 0 && h->q == 19 && h->store != DUGKS_STORE_F64) return launch_step3d_q19(p, h->store, 10, h->stream);
     switch (h->q) {
         case 9: return launch_step_q9(p, h->store, h->tile_x, h->tile_y, h->stream);
         case 19: return launch_step_q19(p, h->store, h->tile_x, h->tile_y, h->stream);
@@ -153,6 +156,7 @@ int dugks_create(const dugks_mesh *mesh, int32_t lattice, double nu, double dt, 
     if (!(mesh->dx > 0) || !(nu > 0) || !(dt > 0) || !(o.rt > 0) || !(o.rho0 > 0))
         return fail(NULL, DUGKS_E_INVAL, "dx, nu, dt, RT and rho0 must be positive");
     if (o.store < 0 || o.store > 3) return fail(NULL, DUGKS_E_INVAL, "bad storage type");
+    if (o.kernel < 0 || o.kernel > 1) return fail(NULL, DUGKS_E_INVAL, "bad kernel selector");
     const double c = sqrt(3.0 * o.rt);
     if (dt > mesh->dx / c * (1.0 + 1e-12))
         return fail(NULL, DUGKS_E_CFL, "dt = %g exceeds dx/sqrt(3RT) = %g (CFL number > 1)", dt, mesh->dx / c);
@@ -204,6 +208,7 @@ int dugks_create(const dugks_mesh *mesh, int32_t lattice, double nu, double dt, 
     h->use_graph = o.use_graph;
     h->tile_x = tx;
     h->tile_y = ty;
+    h->kernel = o.kernel;
     h->esize = o.store == DUGKS_STORE_F32 ? 4 : (o.store == DUGKS_STORE_F64 ? 8 : 2);
     h->state_bytes = (size_t)h->q * h->px * h->ny * h->nz * h->esize;
     h->res_blocks = residual_blocks(h->ncell);
@@ -251,6 +256,7 @@ void dugks_destroy(dugks_t h) {
     cudaFree(h->d_uprev);
     cudaFree(h->d_partials);
     cudaFree(h->d_res);
+    cudaFree(h->d_mom);
     if (h->h_res) cudaFreeHost(h->h_res);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -298,8 +304,10 @@ static int enqueue_steps(dugks_t h, int64_t n) {
         if (e != cudaSuccess) return fail(h, DUGKS_E_CUDA, "step launch: %s", cudaGetErrorString(e));
         cur ^= 1;
     }
-    cudaError_t e = launch_advance(h->d_step, (long long)n, h->stream);
-    if (e != cudaSuccess) return fail(h, DUGKS_E_CUDA, "advance: %s", cudaGetErrorString(e));
+    if (h->force.omega != 0.0) {  // the device clock only feeds G(t)
+        cudaError_t e = launch_advance(h->d_step, (long long)n, h->stream);
+        if (e != cudaSuccess) return fail(h, DUGKS_E_CUDA, "advance: %s", cudaGetErrorString(e));
+    }
     return DUGKS_OK;
 }
 
@@ -331,7 +339,7 @@ int dugks_step(dugks_t h, int64_t n) {
             int rc = enqueue_steps(h, m);
             if (rc != DUGKS_OK) return rc;
         }
-        h->launches += m + 1;
+        h->launches += m + (h->force.omega != 0.0 ? 1 : 0);
         if (m & 1) h->cur ^= 1;
         h->step += m;
         left -= m;
@@ -343,13 +351,15 @@ int dugks_moments(dugks_t h, float *out, int32_t out_is_device) {
     if (!h || !out) return DUGKS_E_INVAL;
     const size_t bytes = sizeof(float) * (h->dim + 1) * h->ncell;
     float *d = out;
-    if (!out_is_device) CUDA_TRY(h, cudaMalloc((void **)&d, bytes));
+    if (!out_is_device) {
+        if (!h->d_mom) CUDA_TRY(h, cudaMalloc((void **)&h->d_mom, bytes));
+        d = h->d_mom;
+    }
     StepParams p = make_params(h);
     cudaError_t e = launch_moments(h->q, h->store, p, h->step * h->dt, h->rt, d, h->stream);
     h->launches++;
     if (e == cudaSuccess && !out_is_device) e = cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (!out_is_device) cudaFree(d);
     if (e != cudaSuccess) return fail(h, DUGKS_E_CUDA, "moments: %s", cudaGetErrorString(e));
     return DUGKS_OK;
 }
@@ -405,6 +415,8 @@ int dugks_get_clock(dugks_t h, int64_t *step, double *time) {
 }
 
 int dugks_set_clock(dugks_t h, int64_t step) {
+    /* the device counter is the step index of the next launch: keep it in step with the
+       host clock whether or not it is advanced by the kernels (omega == 0 skips it) */
     if (!h || step < 0) return DUGKS_E_INVAL;
     long long v = step;
     CUDA_TRY(h, cudaMemcpyAsync(h->d_step, &v, sizeof v, cudaMemcpyHostToDevice, h->stream));

@@ -15,7 +15,22 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+#include <utility>
+
 namespace dugks {
+
+// Compile-time loop: f(std::integral_constant<int, i>) for i = 0 .. N-1, so that indices
+// derived from i (direction components, compact flux indices) are constant expressions and
+// register arrays are never indexed at run time.
+template <class F, int... I>
+__host__ __device__ __forceinline__ void sfor_impl(F &&f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__host__ __device__ __forceinline__ void sfor(F &&f) {
+    sfor_impl(f, std::make_integer_sequence<int, N>{});
+}
 
 // ---------------------------------------------------------------------------------
 // Velocity sets (Sec. 2.3). Paper index order: x component slowest.
@@ -57,8 +72,8 @@ struct Lat<19> {
     static constexpr int D = 3;
     // D3Q27 index of the k-th D3Q19 velocity (the 8 corners removed, order kept).
     __host__ __device__ static constexpr int k27(int k) {
-        constexpr int m[19] = {1, 3, 4, 5, 7, 9, 10, 11, 12, 13, 14, 15, 16, 17, 19, 21, 22, 23, 25};
-        return m[k];
+        // 1, 3, 4, 5, 7, 9, 10, ..., 17, 19, 21, 22, 23, 25
+        return k < 1 ? 1 : k < 4 ? k + 2 : k < 5 ? 7 : k < 14 ? k + 4 : k < 15 ? 19 : k < 18 ? k + 6 : 25;
     }
     __host__ __device__ static constexpr int e(int k, int a) { return Lat<27>::e(k27(k), a); }
     template <class T>

@@ -14,6 +14,8 @@ namespace dugks {
 cudaError_t launch_step_q9(const StepParams &p, int store, int tx, int ty, cudaStream_t stream);
 cudaError_t launch_step_q19(const StepParams &p, int store, int tx, int ty, cudaStream_t stream);
 cudaError_t launch_step_q27(const StepParams &p, int store, int tx, int ty, cudaStream_t stream);
+// Throughput kernel for D3Q19 with F32/BF16/F16 storage (dugks_step3d.cuh); ry = CTA rows.
+cudaError_t launch_step3d_q19(const StepParams &p, int store, int ry, cudaStream_t stream);
 
 // Auxiliary kernels (aux.cu).
 cudaError_t launch_init(int q, int store, const StepParams &p, const double *pres, const double *vel, double rt,

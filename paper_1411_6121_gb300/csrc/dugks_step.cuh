@@ -101,9 +101,10 @@ __device__ __forceinline__ void interface_f(const StepParams &p, const Coef<T> &
     moments<Q, T>(F, Gh, cf.wface * cf.rho0, drb, mb);
     T t[Q];
     relax<Q, T>(F, drb, mb, Gh, cf.rho0, cf.inv_rho0, cf.b7, cf.c7, t);
-#pragma unroll
-    for (int k = 0; k < Q; k++)
-        if (Lat<Q>::e(k, d) != 0) out[flux_index<Q>(d, k)] = t[k];
+    sfor<Q>([&](auto kc) {
+        constexpr int k = kc;
+        if constexpr (Lat<Q>::e(k, d) != 0) out[flux_index<Q>(d, k)] = t[k];
+    });
 }
 
 __device__ __forceinline__ int wrap_idx(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
@@ -121,7 +122,7 @@ __device__ __forceinline__ void cell_G(const StepParams &p, int64_t cell, int64_
 }
 
 template <int Q, class S, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) fused_step(const StepParams p, int zchunk) {
+__global__ void __launch_bounds__(TX *TY) fused_step(const __grid_constant__ StepParams p, int zchunk) {
     using T = typename Arith<S>::T;
     using K = StepShape<Q, TX, TY, T>;
     constexpr int D = K::D;
@@ -152,11 +153,11 @@ __global__ void __launch_bounds__(TX *TY) fused_step(const StepParams p, int zch
         cth = (T)(cos(p.omega * (tn + 0.5 * p.dt)) * p.inv_c);
     }
 
-    auto slot_of = [](int pz) { return D == 3 ? (pz + 3) % 3 : 0; };
-    auto cellp = [&](int slot, int ry, int rx) -> T * { return phi + slot * K::PLANE + (ry * RX + rx) * Q; };
+    auto slot_of = [](int pz) __attribute__((always_inline)) { return D == 3 ? (pz + 3) % 3 : 0; };
+    auto cellp = [&](int slot, int ry, int rx) __attribute__((always_inline)) -> T * { return phi + slot * K::PLANE + (ry * RX + rx) * Q; };
 
     // ---- step 1 (+ step 2 in x and y) for global plane pz (real or periodic image) ----
-    auto make_plane = [&](int pz) {
+    auto make_plane = [&](int pz) __attribute__((always_inline)) {
         const int slot = slot_of(pz);
         const int gz = D == 3 ? wrap_idx(pz, nz) : 0;
         for (int r = tid; r < RX * RY; r += NT) {
@@ -216,18 +217,18 @@ __global__ void __launch_bounds__(TX *TY) fused_step(const StepParams p, int zch
         }
     };
     // z ghost plane (step 2 along z): 2 fbar+(inner) - fbar+(next inner), whole region.
-    auto ghost_plane = [&](int pz) {
+    auto ghost_plane = [&](int pz) __attribute__((always_inline)) {
         const int s = slot_of(pz);
         const int sa = slot_of(pz < 0 ? 0 : nz - 1), sb = slot_of(pz < 0 ? 1 : nz - 2);
         for (int i = tid; i < K::PLANE; i += NT) phi[s * K::PLANE + i] = T(2) * phi[sa * K::PLANE + i] - phi[sb * K::PLANE + i];
     };
-    auto plane = [&](int pz) {  // real or periodic planes only
+    auto plane = [&](int pz) __attribute__((always_inline)) {  // real or periodic planes only
         make_plane(pz);
     };
 
     // Field index for interface G (reading: mean of the two adjacent cells; at a wall the
     // one adjacent cell).
-    auto face_G = [&](int d, int gx, int gy, int gz, int gfd, T G[3]) {
+    auto face_G = [&](int d, int gx, int gy, int gz, int gfd, T G[3]) __attribute__((always_inline)) {
         // gfd: interface index along d (between cells gfd-1 and gfd)
         int nd = d == 0 ? nx : (d == 1 ? ny : nz);
         bool per = d == 0 ? perx : (d == 1 ? pery : perz);
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(TX *TY) fused_step(const StepParams p, int zch
     };
 
     // z interface between global planes pl and pl+1 for the thread's own column (3D only).
-    auto zface = [&](int pl, int gfz, T *out) {
+    auto zface = [&](int pl, int gfz, T *out) __attribute__((always_inline)) {
         if constexpr (D == 3) {
             const int sL = slot_of(pl), sR = slot_of(pl + 1);
             T F[Q];
@@ -355,20 +356,26 @@ __global__ void __launch_bounds__(TX *TY) fused_step(const StepParams p, int zch
             const T *ph = cellp(s, ly + 1, lx + 1);
             const T *xm = xf + (ly * (TX + 1) + lx) * K::SX, *xp = xm + K::SX;
             const T *ym = yf + (ly * TX + lx) * K::SY, *yp = ym + TX * K::SY;
-#pragma unroll
-            for (int k = 0; k < Q; k++) {
+            sfor<Q>([&](auto kc) {
+                constexpr int k = kc;
                 T acc = T(0);
-                if (Lat<Q>::e(k, 0) != 0) acc = fmaT((T)Lat<Q>::e(k, 0), xp[flux_index<Q>(0, k)] - xm[flux_index<Q>(0, k)], acc);
-                if (Lat<Q>::e(k, 1) != 0) acc = fmaT((T)Lat<Q>::e(k, 1), yp[flux_index<Q>(1, k)] - ym[flux_index<Q>(1, k)], acc);
-                if constexpr (D == 3) {
-                    if (Lat<Q>::e(k, 2) != 0)
-                        acc = fmaT((T)Lat<Q>::e(k, 2), zf_hi[flux_index<Q>(2, k)] - zf_lo[flux_index<Q>(2, k)], acc);
+                if constexpr (Lat<Q>::e(k, 0) != 0) {
+                    constexpr int i = flux_index<Q>(0, k);
+                    acc = fmaT((T)Lat<Q>::e(k, 0), xp[i] - xm[i], acc);
+                }
+                if constexpr (Lat<Q>::e(k, 1) != 0) {
+                    constexpr int i = flux_index<Q>(1, k);
+                    acc = fmaT((T)Lat<Q>::e(k, 1), yp[i] - ym[i], acc);
+                }
+                if constexpr (D == 3 && Lat<Q>::e(k, 2) != 0) {
+                    constexpr int i = flux_index<Q>(2, k);
+                    acc = fmaT((T)Lat<Q>::e(k, 2), zf_hi[i] - zf_lo[i], acc);
                 }
                 const T gold = (T)Store<S>::ld(src + k * p.dstride + off);
                 // eq. f_tilde_+ in increment form: 4/3 fbar+ - 1/3 f~ = fbar+ + (fbar+ - f~)/3
                 const T v = fmaT(T(1) / T(3), ph[k] - gold, ph[k]) - cf.two_kappa * acc;
                 Store<S>::st(dst + k * p.dstride + off, v);
-            }
+            });
         }
         if constexpr (D == 3) {
 #pragma unroll

@@ -51,7 +51,7 @@ class Force(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("rt", C.c_double), ("rho0", C.c_double), ("store", C.c_int32), ("stream", C.c_void_p),
-                ("use_graph", C.c_int32), ("tile_x", C.c_int32), ("tile_y", C.c_int32)]
+                ("use_graph", C.c_int32), ("tile_x", C.c_int32), ("tile_y", C.c_int32), ("kernel", C.c_int32)]
 
 
 class DugksError(RuntimeError):
@@ -126,7 +126,7 @@ class Sim:
     """One simulation handle (see ``include/dugks.h``)."""
 
     def __init__(self, shape, q, nu, dt, dx=1.0, rt=1.0 / 3.0, rho0=1.0, g=(0.0, 0.0, 0.0), omega=0.0,
-                 bcs=None, field=None, store=STORE_F32, stream=None, use_graph=True, tile=None):
+                 bcs=None, field=None, store=STORE_F32, stream=None, use_graph=True, tile=None, kernel=0):
         lib = load()
         self.lib = lib
         dim = len(shape)
@@ -147,6 +147,7 @@ class Sim:
         o.use_graph = 1 if use_graph else 0
         if tile:
             o.tile_x, o.tile_y = int(tile[0]), int(tile[1])
+        o.kernel = int(kernel)
         self.bcs = make_bcs(bcs)
         h = C.c_void_p()
         rc = lib.dugks_create(C.byref(m), int(q), float(nu), float(dt), C.byref(f), C.byref(self.bcs), C.byref(o),

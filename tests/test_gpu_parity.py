@@ -33,13 +33,13 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def run_pair(cfg, steps, p=None, u=None, field=None, store=0, tile=None):
+def run_pair(cfg, steps, p=None, u=None, field=None, store=0, tile=None, kernel=0):
     import torch
     o = Oracle(field=field, **cfg)
     o.init(p=p, u=u)
     o.step(steps)
     tf = None if field is None else torch.tensor(field, dtype=torch.float32, device="cuda")
-    s = _sim(field=tf, store=store, tile=tile, **cfg)
+    s = _sim(field=tf, store=store, tile=tile, kernel=kernel, **cfg)
     s.init(p=p, u=u)
     s.step(steps)
     return o, s
@@ -122,16 +122,30 @@ CASES_3D = {
 
 
 @pytest.mark.parametrize("name", sorted(CASES_3D))
-@pytest.mark.parametrize("store", [0, 3])
-def test_3d_state_elementwise(name, store):
+@pytest.mark.parametrize("store,kernel", [(0, 0), (0, 1), (3, 0)])
+def test_3d_state_elementwise(name, store, kernel):
+    """kernel 0 is the D3Q19 throughput kernel (F32), kernel 1 the reference fused kernel;
+    F64 storage always runs the reference kernel in FP64."""
     cfg = CASES_3D[name]
     p, u = W.random_state_fields(cfg["shape"], seed=len(name), u_amp=0.03, p_amp=1e-3)
-    o, s = run_pair(cfg, 8, p, u, store=store)
+    o, s = run_pair(cfg, 8, p, u, store=store, kernel=kernel)
     ref = state_dev(o)
     got = state_f64(s)
     scale = np.abs(ref).max()
     tol = 1e-11 if store == 3 else 2e-6
     assert np.abs(got - ref).max() < tol * scale, (np.abs(got - ref).max(), scale)
+
+
+def test_d3q19_force_field_time_dependent():
+    cfg = dict(shape=(37, 18, 11), q=19, nu=0.04, dt=0.5, g=(1e-5, 0.0, -1e-5), omega=0.02,
+               bcs=[W.periodic(), W.periodic(), W.wall(), W.wall((0.02, 0.0, 0.01)), W.periodic(), W.periodic()])
+    field = W.force_field(cfg["shape"], 1e-5, seed=19, rel=1.0)
+    p, u = W.random_state_fields(cfg["shape"], seed=7, u_amp=0.02, p_amp=1e-4)
+    for kernel in (0, 1):
+        o, s = run_pair(cfg, 30, p, u, field=field, kernel=kernel)
+        ref = state_dev(o)
+        d = np.abs(state_f64(s) - ref).max() / np.abs(ref).max()
+        assert d < 2e-6, (kernel, d)
 
 
 def test_d3q19_cavity_1000_steps():
@@ -140,13 +154,14 @@ def test_d3q19_cavity_1000_steps():
     o.init()
     o.step(1000)
     ref = o.moments()
-    for store, tol in ((3, 1e-6), (0, 2e-5)):
+    for store, tol in ((3, 1e-6), (0, 2e-5), (2, 1e-3)):  # F16: pressure to 5e-3 (below)
         s = _sim(store=store, **cfg)
         s.init()
         s.step(1000)
         got = s.moments()
         assert rel_l2(got[1:], ref[1:]) < tol, (store, rel_l2(got[1:], ref[1:]))
-        assert rel_l2(got[0], ref[0]) < max(tol, 2e-5)
+        ptol = 5e-3 if store == 2 else max(tol, 2e-5)  # F16 resolves drho = sum g~ to ~1e-3
+        assert rel_l2(got[0], ref[0]) < ptol, (store, rel_l2(got[0], ref[0]))
 
 
 def test_f16_storage():
