@@ -153,13 +153,13 @@ class ClockSampler:
                 "power_w_max": max(pw) if pw else None}
 
 
-def run_form(torch, store, steps, warmup, dev, launches_out=None):
+def run_form(torch, store, steps, warmup, dev, tile=None):
     """Times `steps` fused steps of the 256^3 cube (storage `store`) after `warmup`.
     Returns (ms per step, mean fused-kernel ms, launches of our kernels in the region)."""
     from paper_1411_6121_gb300 import dugks
     cfg = workload()
     stream = torch.cuda.Stream(device=dev)
-    sim = dugks.Sim(store=store, stream=stream.cuda_stream, use_graph=False, **cfg)
+    sim = dugks.Sim(store=store, stream=stream.cuda_stream, use_graph=False, tile=tile, **cfg)
     sim.init()
     sim.residual()
     for i in range(warmup):
@@ -261,6 +261,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the BF16/F16/e2e/CPU legs")
     ap.add_argument("--size", type=int, default=256, help="cube edge (256 for the benchmark; smaller for ncu)")
     ap.add_argument("--store", type=int, default=0, help="storage of the main leg (0 f32, 1 bf16, 2 f16, 3 f64)")
+    ap.add_argument("--rows", type=int, default=0, help="thread-block rows of the 3D kernel (0: library default)")
     args = ap.parse_args()
     global N
     N = args.size
@@ -307,7 +308,8 @@ def main():
     if ws > 1:
         dist.barrier()
     sampler.start()
-    ms_step, ms_kernel, launches, res = run_form(torch, args.store, args.steps, warmup, dev)
+    ms_step, ms_kernel, launches, res = run_form(torch, args.store, args.steps, warmup, dev,
+                                                 tile=(32, args.rows) if args.rows else None)
     clocks = sampler.stop()
     if ws > 1:
         t = torch.tensor([ms_step], device=dev, dtype=torch.float64)

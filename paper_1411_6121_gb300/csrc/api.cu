@@ -28,6 +28,7 @@ struct dugks_s {
     cudaStream_t stream;
     int use_graph, tile_x, tile_y;
     int kernel;            // 0: throughput kernel where built, 1: reference kernel
+    int ry3d;              // CTA rows of the 3D throughput kernel
     int own_stream;
     size_t esize;          // bytes per stored element
     size_t state_bytes;    // padded device bytes of one buffer
@@ -110,7 +111,8 @@ static StepParams make_params(const dugks_t h) {
 }
 
 static cudaError_t launch_one_step(dugks_t h, StepParams &p) {
-    if (h->kernel == 0 && h->q == 19 && h->store != DUGKS_STORE_F64) return launch_step3d_q19(p, h->store, 10, h->stream);
+    if (h->kernel == 0 && h->q == 19 && h->store != DUGKS_STORE_F64)
+        return launch_step3d_q19(p, h->store, h->ry3d, h->stream);
     switch (h->q) {
         case 9: return launch_step_q9(p, h->store, h->tile_x, h->tile_y, h->stream);
         case 19: return launch_step_q19(p, h->store, h->tile_x, h->tile_y, h->stream);
@@ -169,13 +171,24 @@ int dugks_create(const dugks_mesh *mesh, int32_t lattice, double nu, double dt, 
             return fail(NULL, DUGKS_E_INVAL, "periodic faces must be paired (axis %d)", d);
         if (lo != DUGKS_BC_PERIODIC && n[d] < 2) return fail(NULL, DUGKS_E_INVAL, "a wall axis needs >= 2 cells");
     }
+    // tile of the reference kernel (tile_x x tile_y cells), or, for the D3Q19 throughput
+    // kernel, tile_y = rows of its 32 x tile_y thread block
+    const bool thr3d = o.kernel == 0 && lattice == DUGKS_D3Q19 && o.store != DUGKS_STORE_F64;
     int tx = o.tile_x, ty = o.tile_y;
-    if (tx == 0 || ty == 0) {
-        tx = o.store == DUGKS_STORE_F64 ? 16 : 32;
+    int ry3d = 8;
+    if (thr3d) {
+        if (ty != 0) ry3d = ty;
+        if (!(ry3d == 8 || ry3d == 10)) return fail(NULL, DUGKS_E_UNSUPPORTED, "3D kernel rows %d not built", ry3d);
+        tx = 32;
         ty = 8;
+    } else {
+        if (tx == 0 || ty == 0) {
+            tx = o.store == DUGKS_STORE_F64 ? 16 : 32;
+            ty = 8;
+        }
+        if (!((tx == 32 && ty == 8) || (tx == 16 && ty == 8)))
+            return fail(NULL, DUGKS_E_UNSUPPORTED, "tile %dx%d not built", tx, ty);
     }
-    if (!((tx == 32 && ty == 8) || (tx == 16 && ty == 8)))
-        return fail(NULL, DUGKS_E_UNSUPPORTED, "tile %dx%d not built", tx, ty);
 
     dugks_t h = new (std::nothrow) dugks_s();
     if (!h) return fail(NULL, DUGKS_E_NOMEM, "host allocation failed");
@@ -209,6 +222,7 @@ int dugks_create(const dugks_mesh *mesh, int32_t lattice, double nu, double dt, 
     h->tile_x = tx;
     h->tile_y = ty;
     h->kernel = o.kernel;
+    h->ry3d = ry3d;
     h->esize = o.store == DUGKS_STORE_F32 ? 4 : (o.store == DUGKS_STORE_F64 ? 8 : 2);
     h->state_bytes = (size_t)h->q * h->px * h->ny * h->nz * h->esize;
     h->res_blocks = residual_blocks(h->ncell);

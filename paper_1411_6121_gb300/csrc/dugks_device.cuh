@@ -83,6 +83,17 @@ struct Lat<19> {
     __host__ __device__ static constexpr float w(int k) { return wt<float>(k); }
 };
 
+// Index of the velocity opposite to k.
+template <int Q>
+__host__ __device__ constexpr int opposite(int k) {
+    int r = -1;
+    for (int j = 0; j < Q; j++)
+        if (Lat<Q>::e(j, 0) == -Lat<Q>::e(k, 0) && Lat<Q>::e(j, 1) == -Lat<Q>::e(k, 1) &&
+            Lat<Q>::e(j, 2) == -Lat<Q>::e(k, 2))
+            r = j;
+    return r;
+}
+
 // Number of velocities with a non-zero component along axis d (the directions that carry
 // flux through a face normal to d) and the compact index of velocity k among them.
 template <int Q>
@@ -238,27 +249,46 @@ __device__ __forceinline__ T geq_k(int k, T drho, const T m[3], T mm, T inv_rho0
 //   out_k = g_k + b (geq_k - g_k) + c S_k,  S_k = 3 (Gh.e_k - Gh.m / rho0) (W_k rho0 + geq_k)
 // (eq. S with G.(xi - u)/RT = 3 (Gh.e - Gh.u/c) for xi = c e, c^2 = 3 RT).
 // Step 1 (eq. f_bar_+) uses b = 3h/(2tau+dt), c = 3 tau h/(2tau+dt); step 7
-// (eq. original_f) uses b = h/(2tau+h), c = tau h/(2tau+h).
-template <int Q, class T>
+// (eq. original_f) uses b = h/(2tau+h), c = tau h/(2tau+h). FORCE = false drops S
+// (G = 0 everywhere). Opposite velocities share e.m and the quadratic part of geq.
+template <int Q, class T, bool FORCE = true>
 __device__ __forceinline__ void relax(const T g[Q], T drho, const T m[3], const T rGh[3], T rho0, T inv_rho0, T b,
                                       T c, T out[Q]) {
     constexpr int D = Lat<Q>::D;
     const T mm = m[0] * m[0] + m[1] * m[1] + (D == 3 ? m[2] * m[2] : T(0));
-    const T gm = (rGh[0] * m[0] + rGh[1] * m[1] + (D == 3 ? rGh[2] * m[2] : T(0))) * inv_rho0;
+    T gm = T(0);
+    if constexpr (FORCE) gm = (rGh[0] * m[0] + rGh[1] * m[1] + (D == 3 ? rGh[2] * m[2] : T(0))) * inv_rho0;
     const T base = fmaT(T(-1.5) * inv_rho0, mm, drho);
+    const T c45 = T(4.5) * inv_rho0;
+    sfor<Q>([&](auto kc) {
+        constexpr int k = kc;
+        constexpr int kb = opposite<Q>(k);
+        if constexpr (k <= kb) {  // handle the pair (k, -k) once (k == kb for the rest velocity)
+            T em = T(0), ge = T(0);
 #pragma unroll
-    for (int k = 0; k < Q; k++) {
-        T em = T(0), ge = T(0);
-#pragma unroll
-        for (int a = 0; a < D; a++) {
-            if (Lat<Q>::e(k, a) > 0) { em += m[a]; ge += rGh[a]; }
-            if (Lat<Q>::e(k, a) < 0) { em -= m[a]; ge -= rGh[a]; }
+            for (int a = 0; a < D; a++) {
+                if (Lat<Q>::e(k, a) > 0) { em += m[a]; if (FORCE) ge += rGh[a]; }
+                if (Lat<Q>::e(k, a) < 0) { em -= m[a]; if (FORCE) ge -= rGh[a]; }
+            }
+            const T q = fmaT(c45 * em, em, base);   // even part of the bracket
+            const T geq = wmul<Q, T>(k, fmaT(em, T(3), q));
+            T v = fmaT(b, geq - g[k], g[k]);
+            if constexpr (FORCE) {
+                const T feq = fmaT((T)Lat<Q>::template wt<double>(k), rho0, geq);
+                v = fmaT(c, T(3) * (ge - gm) * feq, v);
+            }
+            out[k] = v;
+            if constexpr (kb != k) {
+                const T geqb = wmul<Q, T>(kb, fmaT(em, T(-3), q));
+                T vb = fmaT(b, geqb - g[kb], g[kb]);
+                if constexpr (FORCE) {
+                    const T feqb = fmaT((T)Lat<Q>::template wt<double>(kb), rho0, geqb);
+                    vb = fmaT(c, T(3) * (-ge - gm) * feqb, vb);
+                }
+                out[kb] = vb;
+            }
         }
-        const T geq = wmul<Q, T>(k, fmaT(em, T(3), fmaT(inv_rho0 * em, T(4.5) * em, base)));
-        const T feq = fmaT((T)Lat<Q>::template wt<double>(k), rho0, geq);
-        const T src = T(3) * (ge - gm) * feq;
-        out[k] = fmaT(c, src, fmaT(b, geq - g[k], g[k]));
-    }
+    });
 }
 
 }  // namespace dugks

@@ -4,9 +4,10 @@
 // Same scheme and the same readings as the reference kernel in dugks_step.cuh (Appendix
 // steps 1-10 of arXiv 1411.6121); what differs is how the work is organised:
 //
-//  * A CTA is 32 x RY threads, one per cell column; the 30 x (RY-2) inner columns are
-//    updated, the outer ring is halo. The CTA marches through its z range keeping fbar+
-//    (step 1) of three planes in a shared-memory ring.
+//  * A CTA is 32 x RY threads, one per cell column (lanes along x, warps along y); the
+//    30 x (RY-2) inner columns are updated, the outer ring is halo. The CTA marches through
+//    its z range keeping fbar+ (step 1) and its moments for three planes in a
+//    shared-memory ring.
 //  * Step 3-4 reconstruction is split per cell. For the interface normal to d between
 //    cells L and R (eq. gradient with the cross-point tangential gradients):
 //        F_k = alpha_k(L) + beta_k(R),
@@ -14,14 +15,15 @@
 //        beta_k  = (1/2 - kappa e_dk) fbar+_k - kappa/4 sum_t e_tk C^t_k,
 //    with C^t_k the central difference of fbar+_k along the tangential axis t. Only the
 //    velocities that cross the interface (e_dk != 0) are formed per direction.
-//  * Step 6 interface moments are sums of the same per-cell parts, taken in moment space:
+//  * Step 6 interface moments are sums of the same per-cell parts taken in moment space:
 //        sum_k F_k = A0(L) + B0(R),  sum_k e_k F_k = A1(L) + B1(R),
-//    A0 = M0/2 + kappa M_d - kappa/4 (E_t1 + E_t2) etc., where M are moments of fbar+ and
-//    E moments of the central differences. This avoids reconstructing the velocities that
-//    do not cross the interface just to sum them.
-//  * Each cell forms the relaxed interface values (step 7) for its +x, +y, +z interfaces;
-//    neighbours exchange the beta parts and the finished interface values through shared
-//    memory, so every interface is computed once and both cells use the same bits.
+//        A0 = M0/2 + kappa M_d - kappa/4 (dM_t1 + dM_t2),
+//        A1_a = M_a/2 + kappa M_ad - kappa/4 (dM_a,t1 + dM_a,t2),
+//    (B with -kappa), where M are moments of fbar+ and dM_.,t their central differences
+//    along t, read from the neighbours' moments in the ring.
+//  * Each cell forms the relaxed interface values (step 7) of its +x, +y, +z interfaces;
+//    x neighbours exchange through warp shuffles, y neighbours through shared memory, so
+//    every interface is computed once and both cells use the same bits.
 //  * Wall interfaces (and the chunk's first z interface) take the direct path of
 //    dugks_step.cuh: all velocities reconstructed from the ring, NEQ (step 5), relax.
 #pragma once
@@ -32,109 +34,111 @@ namespace dugks {
 
 template <int Q, int RY>
 struct Shape3 {
-    static constexpr int D = 3;
     static constexpr int RX = 32;
     static constexpr int NT = RX * RY;
     static constexpr int TXI = RX - 2, TYI = RY - 2;  // inner columns
-    static constexpr int NF = n_flux<Q>(0);           // same for every axis
-    static constexpr int XS = (2 * (NF + 4)) | 1;     // exchange slots per cell (odd stride)
-    static constexpr int PLANE = RY * RX * Q;
-    static constexpr size_t smem_floats = 3 * (size_t)PLANE + (size_t)NT * XS;
+    static constexpr int NF = n_flux<Q>(0);           // crossing velocities per interface
+    static constexpr int NM = 10;                     // moments kept per cell
+    static constexpr int CS = Q + NM;                 // ring floats per cell (odd: no conflicts)
+    static constexpr int BS = (NF + 4) | 1;           // y exchange: beta_y + B_y
+    static constexpr int FS = NF | 1;                 // y exchange: f at +y
+    static constexpr int PLANE = RY * RX * CS;
+    static constexpr int US = Q | 1;                  // u0 of a plane (own column), two planes
+    static constexpr size_t smem_floats = 3 * (size_t)PLANE + (size_t)NT * (BS + FS + 2 * US);
     static constexpr size_t smem_bytes = smem_floats * sizeof(float);
 };
 
-// Moments of fbar+ of one cell.
-struct Mom {
-    float M0, M1[3], M2[3][3];
-};
+// Moment slots in the ring: 0 M0, 1..3 M_x,y,z, 4..6 M_xx,yy,zz, 7 M_xy, 8 M_xz, 9 M_yz.
+__host__ __device__ constexpr int mslot2(int a, int b) {
+    return a == b ? 4 + a : (a + b == 1 ? 7 : (a + b == 2 ? 8 : 9));
+}
 
-// Moments of fbar+ of one cell: M0, M1[a] = sum e_a f, M2[a][b] = sum e_a e_b f.
+// Moments of fbar+ of one cell into m[10] (layout above), from partial sums over the
+// velocities with e_a = +1, -1 and 0.
 template <int Q>
-__device__ __forceinline__ void phi_moments(const float f[Q], float &M0, float M1[3], float M2[3][3]) {
-    M0 = 0.0f;
+__device__ __forceinline__ void phi_moments(const float f[Q], float m[10]) {
+    float sp[3] = {0.0f, 0.0f, 0.0f}, sn[3] = {0.0f, 0.0f, 0.0f}, s0 = 0.0f, mxy = 0.0f, mxz = 0.0f, myz = 0.0f;
+    sfor<Q>([&](auto kc) {
+        constexpr int k = kc;
+        constexpr int ex = Lat<Q>::e(k, 0), ey = Lat<Q>::e(k, 1), ez = Lat<Q>::e(k, 2);
+        if constexpr (ex > 0) sp[0] += f[k];
+        if constexpr (ex < 0) sn[0] += f[k];
+        if constexpr (ex == 0) s0 += f[k];
+        if constexpr (ey > 0) sp[1] += f[k];
+        if constexpr (ey < 0) sn[1] += f[k];
+        if constexpr (ez > 0) sp[2] += f[k];
+        if constexpr (ez < 0) sn[2] += f[k];
+        if constexpr (ex * ey != 0) mxy += ex * ey > 0 ? f[k] : -f[k];
+        if constexpr (ex * ez != 0) mxz += ex * ez > 0 ? f[k] : -f[k];
+        if constexpr (ey * ez != 0) myz += ey * ez > 0 ? f[k] : -f[k];
+    });
+    m[0] = s0 + (sp[0] + sn[0]);
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        M1[a] = 0.0f;
-#pragma unroll
-        for (int b = 0; b < 3; b++) M2[a][b] = 0.0f;
+        m[1 + a] = sp[a] - sn[a];
+        m[4 + a] = sp[a] + sn[a];
     }
-#pragma unroll
-    for (int k = 0; k < Q; k++) {
-        M0 += f[k];
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            if (Lat<Q>::e(k, a) > 0) M1[a] += f[k];
-            if (Lat<Q>::e(k, a) < 0) M1[a] -= f[k];
-#pragma unroll
-            for (int b = a; b < 3; b++) {
-                const int s = Lat<Q>::e(k, a) * Lat<Q>::e(k, b);
-                if (s > 0) M2[a][b] += f[k];
-                if (s < 0) M2[a][b] -= f[k];
-            }
-        }
-    }
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-        for (int b = 0; b < a; b++) M2[a][b] = M2[b][a];
+    m[7] = mxy;
+    m[8] = mxz;
+    m[9] = myz;
 }
 
-// Moments of the central differences along t: E0 = sum_k e_tk C_k, E1[a] = sum_k e_ak e_tk C_k
-// (C_k defined for e_tk != 0).
-template <int Q, int t>
-__device__ __forceinline__ void diff_moments(const float C[Q], float &E0, float E1[3]) {
-    E0 = 0.0f;
-    E1[0] = E1[1] = E1[2] = 0.0f;
+// Tangential moment differences of a cell along t from its two neighbours' moments:
+// dM[0] = difference of M_t, dM[1+a] = difference of M_at.
+template <int t>
+__device__ __forceinline__ void moment_diff(const float *lo, const float *hi, float dM[4]) {
+    dM[0] = hi[1 + t] - lo[1 + t];
 #pragma unroll
-    for (int k = 0; k < Q; k++) {
-        if (Lat<Q>::e(k, t) == 0) continue;
-        const float c = Lat<Q>::e(k, t) > 0 ? C[k] : -C[k];  // e_t C
-        E0 += c;
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            if (Lat<Q>::e(k, a) > 0) E1[a] += c;
-            if (Lat<Q>::e(k, a) < 0) E1[a] -= c;
-        }
-    }
+    for (int a = 0; a < 3; a++) dM[1 + a] = hi[mslot2(a, t)] - lo[mslot2(a, t)];
 }
 
-// Per-cell parts of the interface normal to d (see the file comment). ph: fbar+ of the
-// cell; C1, C2: central differences along the tangential axes t1 < t2; E: their moments.
-// Writes alpha, beta (compact flux index) and A = (A0, A1[3]), B = (B0, B1[3]).
+// Per-cell parts of the interface normal to d (see the file comment): alpha, beta for the
+// crossing velocities (compact index), A = (A0, A1[3]), B = (B0, B1[3]). ph: fbar+ of the
+// cell; m: its moments; C1/C2: per-velocity central differences along t1 < t2 (only the
+// velocities that cross d and have a component along t are read); dM1/dM2: moment
+// differences along t1, t2.
 template <int Q, int d>
-__device__ __forceinline__ void face_parts(const float ph[Q], const float C1[Q], const float C2[Q], float E01,
-                                           const float E11[3], float E02, const float E12[3], float M0,
-                                           const float M1[3], const float M2[3][3], float kappa, float *alpha,
+__device__ __forceinline__ void face_parts(const float *ph, const float *m, const float C1[Q], const float C2[Q],
+                                           const float dM1[4], const float dM2[4], float kappa, float *alpha,
                                            float *beta, float A[4], float B[4]) {
     constexpr int t1 = d == 0 ? 1 : 0;
     constexpr int t2 = d == 2 ? 1 : 2;
     const float qk = -0.25f * kappa;
-    const float g0 = qk * (E01 + E02);
-    A[0] = fmaf(0.5f, M0, fmaf(kappa, M1[d], g0));
-    B[0] = fmaf(0.5f, M0, fmaf(-kappa, M1[d], g0));
+    const float g0 = qk * (dM1[0] + dM2[0]);
+    A[0] = fmaf(0.5f, m[0], fmaf(kappa, m[1 + d], g0));
+    B[0] = fmaf(0.5f, m[0], fmaf(-kappa, m[1 + d], g0));
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        const float g1 = qk * (E11[a] + E12[a]);
-        A[1 + a] = fmaf(0.5f, M1[a], fmaf(kappa, M2[a][d], g1));
-        B[1 + a] = fmaf(0.5f, M1[a], fmaf(-kappa, M2[a][d], g1));
+        const float g1 = qk * (dM1[1 + a] + dM2[1 + a]);
+        const float mad = m[mslot2(a, d)];
+        A[1 + a] = fmaf(0.5f, m[1 + a], fmaf(kappa, mad, g1));
+        B[1 + a] = fmaf(0.5f, m[1 + a], fmaf(-kappa, mad, g1));
     }
     sfor<Q>([&](auto kc) {
         constexpr int k = kc;
         if constexpr (Lat<Q>::e(k, d) != 0) {
             constexpr int i = flux_index<Q>(d, k);
-            float tg = 0.0f;
-            if constexpr (Lat<Q>::e(k, t1) != 0) tg = Lat<Q>::e(k, t1) > 0 ? C1[k] : -C1[k];
-            if constexpr (Lat<Q>::e(k, t2) != 0) tg += Lat<Q>::e(k, t2) > 0 ? C2[k] : -C2[k];
-            const float gam = qk * tg;
+            constexpr int e1 = Lat<Q>::e(k, t1), e2 = Lat<Q>::e(k, t2);
             constexpr float ed = (float)Lat<Q>::e(k, d);
-            alpha[i] = fmaf(fmaf(kappa, ed, 0.5f), ph[k], gam);
-            beta[i] = fmaf(fmaf(-kappa, ed, 0.5f), ph[k], gam);
+            const float f = ph[k];
+            if constexpr (e1 != 0 || e2 != 0) {
+                float tg = 0.0f;
+                if constexpr (e1 != 0) tg = e1 > 0 ? C1[k] : -C1[k];
+                if constexpr (e2 != 0) tg += e2 > 0 ? C2[k] : -C2[k];
+                const float gam = qk * tg;
+                alpha[i] = fmaf(fmaf(kappa, ed, 0.5f), f, gam);
+                beta[i] = fmaf(fmaf(-kappa, ed, 0.5f), f, gam);
+            } else {
+                alpha[i] = fmaf(kappa, ed, 0.5f) * f;
+                beta[i] = fmaf(-kappa, ed, 0.5f) * f;
+            }
         }
     });
 }
 
 // Step 6-7 for the crossing velocities of the interface normal to d from its step-4 values
-// F (compact) and moments (drho, j): f = F + b7 (geq - F) + c7 S.
+// F (compact) and moments (drho, j): f = F + b7 (geq - F) + c7 S. Opposite velocities (both
+// cross the interface) share e.m and the quadratic part of geq.
 template <int Q, int d, bool FORCE>
 __device__ __forceinline__ void face_relax(const Coef<float> &cf, const float *F, float drho, const float j[3],
                                            const float Gh[3], float *out) {
@@ -145,43 +149,69 @@ __device__ __forceinline__ void face_relax(const Coef<float> &cf, const float *F
     const float base = fmaf(-1.5f * cf.inv_rho0, mm, drho);
     float gm = 0.0f;
     if (FORCE) gm = (Gh[0] * m[0] + Gh[1] * m[1] + Gh[2] * m[2]) * cf.inv_rho0;
+    const float c45 = 4.5f * cf.inv_rho0;
     sfor<Q>([&](auto kc) {
         constexpr int k = kc;
-        if constexpr (Lat<Q>::e(k, d) != 0) {
+        constexpr int kb = opposite<Q>(k);
+        if constexpr (Lat<Q>::e(k, d) > 0) {  // the pair (k, kb), e_d = +1 / -1
             float em = 0.0f, ge = 0.0f;
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 if (Lat<Q>::e(k, a) > 0) { em += m[a]; if (FORCE) ge += Gh[a]; }
                 if (Lat<Q>::e(k, a) < 0) { em -= m[a]; if (FORCE) ge -= Gh[a]; }
             }
-            constexpr int i = flux_index<Q>(d, k);
-            constexpr float w = Lat<Q>::w(k);
+            constexpr int i = flux_index<Q>(d, k), ib = flux_index<Q>(d, kb);
+            constexpr float w = Lat<Q>::w(k);  // = W of the opposite velocity
             // interface values need no conservation-exact form (the same value is used by
             // both cells, so the flux telescopes exactly whatever its rounding)
-            const float geq = w * fmaf(em, 3.0f, fmaf(cf.inv_rho0 * em, 4.5f * em, base));
-            float v = fmaf(cf.b7, geq - F[i], F[i]);
-            if (FORCE) v = fmaf(cf.c7 * 3.0f * (ge - gm), fmaf(w, cf.rho0, geq), v);
+            const float q = fmaf(c45 * em, em, base);
+            const float geq = w * fmaf(em, 3.0f, q), geqb = w * fmaf(em, -3.0f, q);
+            float v = fmaf(cf.b7, geq - F[i], F[i]), vb = fmaf(cf.b7, geqb - F[ib], F[ib]);
+            if (FORCE) {
+                v = fmaf(cf.c7 * 3.0f * (ge - gm), fmaf(w, cf.rho0, geq), v);
+                vb = fmaf(cf.c7 * 3.0f * (-ge - gm), fmaf(w, cf.rho0, geqb), vb);
+            }
             out[i] = v;
+            out[ib] = vb;
         }
     });
 }
 
+// One segment of work: the z planes [z0, z1) of the tile whose inner columns start at
+// (x0, y0). The kernel below walks a contiguous run of (tile, plane) units.
+template <int Q, class S, int RY, bool FORCE>
+__device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned char *smem_raw, int x0, int y0, int z0,
+                                               int z1);
+
+// Grid: (tiles along x, tiles along y, z chunks); neighbouring CTAs stream the same z
+// planes of neighbouring tiles together, so the halo columns they share hit in L2.
 template <int Q, class S, int RY, bool FORCE>
 __global__ void __launch_bounds__(32 * RY, 1) fused_step3d(const __grid_constant__ StepParams p, int zchunk) {
     using K = Shape3<Q, RY>;
-    constexpr int NF = K::NF;
-    constexpr int XS = K::XS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *phi = reinterpret_cast<float *>(smem_raw);  // [3][RY][32][Q]
-    float *xch = phi + 3 * K::PLANE;                   // [RY][32][XS]
+    const int z0 = blockIdx.z * zchunk;
+    const int z1 = min(p.nz, z0 + zchunk);
+    step3d_segment<Q, S, RY, FORCE>(p, smem_raw, blockIdx.x * K::TXI, blockIdx.y * K::TYI, z0, z1);
+}
+
+template <int Q, class S, int RY, bool FORCE>
+__device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned char *smem_raw, int x0, int y0, int z0,
+                                               int z1) {
+    using K = Shape3<Q, RY>;
+    constexpr int NF = K::NF;
+    constexpr int CS = K::CS;
+    float *ring = reinterpret_cast<float *>(smem_raw);  // [3][RY][32][CS]: fbar+ then moments
+    float *xb = ring + 3 * K::PLANE;                     // [RY][32][BS]: beta_y, B_y
+    float *xf = xb + K::NT * K::BS;                      // [RY][32][FS]: f at +y
     const Coef<float> cf(p);
 
     const int lane = threadIdx.x, row = threadIdx.y;
+    // own u0 = fbar+ + (fbar+ - f~)/3 (the cell's part of eq. f_tilde_+) of planes with
+    // even / odd index
+    float *usb = xf + K::NT * K::FS + (row * 32 + lane) * (2 * K::US);
+    auto US = [&](int pz) __attribute__((always_inline)) -> float * { return usb + (pz & 1) * K::US; };
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const int x0 = blockIdx.x * K::TXI, y0 = blockIdx.y * K::TYI;
     const int gx = x0 - 1 + lane, gy = y0 - 1 + row;
-    const int z0 = blockIdx.z * zchunk;
-    const int z1 = min(nz, z0 + zchunk);
     const int64_t ncell = (int64_t)nx * ny * nz;
     const bool perx = p.bc[0] == 0, pery = p.bc[2] == 0, perz = p.bc[4] == 0;
     const S *src = reinterpret_cast<const S *>(p.src);
@@ -189,16 +219,20 @@ __global__ void __launch_bounds__(32 * RY, 1) fused_step3d(const __grid_constant
 
     // column classification
     const bool inner = lane >= 1 && lane <= K::TXI && row >= 1 && row <= K::TYI;
-    const bool own_real = gx >= 0 && gx < nx && gy >= 0 && gy < ny;       // a cell of the domain
-    const bool upd = inner && own_real;                                  // this thread updates cells
-    int cx = gx, cy = gy;                                                // column whose data is loaded
-    bool load = true;                                                    // real or periodic image
+    const bool upd = inner && gx < nx && gy < ny;            // this thread updates cells
+    int cx = gx, cy = gy;                                    // column whose data is loaded
+    bool load = true;                                        // real cell or periodic image
     if (gx < 0 || gx >= nx) { if (perx && gx >= -1 && gx <= nx) cx = wrap_idx(gx, nx); else load = false; }
     if (gy < 0 || gy >= ny) { if (pery && gy >= -1 && gy <= ny) cy = wrap_idx(gy, ny); else load = false; }
-    const bool xghost = !perx && (gx == -1 || gx == nx) && ((gy >= 0 && gy < ny) || (pery && gy >= -1 && gy <= ny));
+    const bool yreal = (gy >= 0 && gy < ny) || (pery && gy >= -1 && gy <= ny);
+    const bool xghost = !perx && (gx == -1 || gx == nx) && yreal;
     const bool yghost = !pery && (gy == -1 || gy == ny) && gx >= -1 && gx <= nx;
     const bool xwall_tile = !perx && (x0 == 0 || x0 + K::TXI >= nx);
     const bool ywall_tile = !pery && (y0 == 0 || y0 + K::TYI >= ny);
+    // which interfaces this column owns
+    const bool need_x = row >= 1 && row <= K::TYI && gy >= 0 && gy < ny && lane <= K::TXI && gx >= -1 && gx < nx;
+    const bool ycol = lane >= 1 && lane <= K::TXI && gx >= 0 && gx < nx && gy >= -1 && gy <= ny;
+    const bool need_y = ycol && row <= K::TYI && gy < ny;
 
     float ct = (float)p.inv_c, cth = (float)p.inv_c;
     if (FORCE && p.omega != 0.0) {
@@ -207,18 +241,14 @@ __global__ void __launch_bounds__(32 * RY, 1) fused_step3d(const __grid_constant
         cth = (float)(cos(p.omega * (tn + 0.5 * p.dt)) * p.inv_c);
     }
 
-    auto P = [&](int slot, int r, int l) __attribute__((always_inline)) -> float * { return phi + ((slot * RY + r) * 32 + l) * Q; };
-    auto slot_of = [](int pz) __attribute__((always_inline)) { return (pz + 3) % 3; };
-    auto X = [&](int r, int l) __attribute__((always_inline)) -> float * { return xch + (r * 32 + l) * XS; };
-
-    // cell G / c (with time factor) at (x, y, z) of the domain
-    auto cellG = [&](int x, int y, int z, float Gh[3]) __attribute__((always_inline)) {
-        const int64_t c = (int64_t)x + (int64_t)nx * ((int64_t)y + (int64_t)ny * z);
-        cell_G<3, float>(p, c, ncell, ct, Gh);
+    auto R = [&](int slot, int r, int l) __attribute__((always_inline)) -> float * {
+        return ring + ((slot * RY + r) * 32 + l) * CS;
     };
-    // interface G / c at time t+h: mean of the two cells (one cell at a wall)
+    auto slot_of = [](int pz) __attribute__((always_inline)) { return (pz + 3) % 3; };
+
+    // interface G / c at time t+h between (x,y,z) - e_d and (x,y,z): mean of the two cells,
+    // one cell at a wall (reading R2)
     auto faceG = [&](int d, int x, int y, int z, float Gh[3]) __attribute__((always_inline)) {
-        // interface between (x,y,z) - e_d and (x,y,z)
         int lo[3] = {x, y, z}, hi[3] = {x, y, z};
         const int nd = d == 0 ? nx : (d == 1 ? ny : nz);
         const bool per = d == 0 ? perx : (d == 1 ? pery : perz);
@@ -235,21 +265,14 @@ __global__ void __launch_bounds__(32 * RY, 1) fused_step3d(const __grid_constant
         }
     };
 
-    // ---- step 1 for the own column at plane pz into the ring (returns the moments) ----
-    auto make_phi = [&](int pz) __attribute__((always_inline)) -> Mom {
-        Mom r;
-        float *o = P(slot_of(pz), row, lane);
+    // ---- step 1 for the own column at plane pz into the ring; u0 = fbar+ + (fbar+ - f~)/3
+    //      (the cell's part of eq. f_tilde_+, applied in increment form) is returned ----
+    auto make_phi = [&](int pz, float *u0) __attribute__((always_inline)) {
+        float *o = R(slot_of(pz), row, lane);
         if (!load) {
 #pragma unroll
-            for (int k = 0; k < Q; k++) o[k] = 0.0f;
-            r.M0 = 0.0f;
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                r.M1[a] = 0.0f;
-#pragma unroll
-                for (int b = 0; b < 3; b++) r.M2[a][b] = 0.0f;
-            }
-            return r;
+            for (int k = 0; k < CS; k++) o[k] = 0.0f;
+            return;
         }
         const int gz = wrap_idx(pz, nz);
         const int64_t off = (int64_t)gz * p.plane + (int64_t)cy * p.px + cx;
@@ -257,102 +280,79 @@ __global__ void __launch_bounds__(32 * RY, 1) fused_step3d(const __grid_constant
 #pragma unroll
         for (int k = 0; k < Q; k++) g[k] = (float)Store<S>::ld(src + k * p.dstride + off);
         float Gh[3] = {0.0f, 0.0f, 0.0f}, drho, m[3];
-        if (FORCE) cellG(cx, cy, gz, Gh);
+        if (FORCE) {
+            const int64_t c = (int64_t)cx + (int64_t)nx * ((int64_t)cy + (int64_t)ny * gz);
+            cell_G<3, float>(p, c, ncell, ct, Gh);
+        }
         moments<Q, float>(g, Gh, cf.wcell * cf.rho0, drho, m);
         float f[Q];
-        relax<Q, float>(g, drho, m, Gh, cf.rho0, cf.inv_rho0, cf.b1, cf.c1, f);
+        relax<Q, float, FORCE>(g, drho, m, Gh, cf.rho0, cf.inv_rho0, cf.b1, cf.c1, f);
+        float mo[10];
+        phi_moments<Q>(f, mo);
 #pragma unroll
-        for (int k = 0; k < Q; k++) o[k] = f[k];
-        phi_moments<Q>(f, r.M0, r.M1, r.M2);
-        return r;
-    };
-    auto ring_moments = [&](int pz) __attribute__((always_inline)) -> Mom {
-        Mom r;
-        const float *q = P(slot_of(pz), row, lane);
-        float fv[Q];
+        for (int k = 0; k < Q; k++) {
+            o[k] = f[k];
+            u0[k] = fmaf(1.0f / 3.0f, f[k] - g[k], f[k]);
+        }
 #pragma unroll
-        for (int k = 0; k < Q; k++) fv[k] = q[k];
-        phi_moments<Q>(fv, r.M0, r.M1, r.M2);
-        return r;
+        for (int i = 0; i < 10; i++) o[Q + i] = mo[i];
     };
-    // step 2 in x and y for the ghost columns of a plane (reading R3: linear, x then y)
+    // step 2 (reading R3: ghost = 2 f0 - f1, x then y then z): fbar+ and, by linearity,
+    // its moments extrapolate the same way
     auto ghosts_xy = [&](int pz) __attribute__((always_inline)) {
         const int s = slot_of(pz);
         if (xwall_tile) {
             __syncthreads();
             if (xghost) {
                 const int d1 = gx < 0 ? 1 : -1;
-                float *o = P(s, row, lane);
-                const float *a = P(s, row, lane + d1), *b = P(s, row, lane + 2 * d1);
+                float *o = R(s, row, lane);
+                const float *a = R(s, row, lane + d1), *b = R(s, row, lane + 2 * d1);
 #pragma unroll
-                for (int k = 0; k < Q; k++) o[k] = 2.0f * a[k] - b[k];
+                for (int k = 0; k < CS; k++) o[k] = 2.0f * a[k] - b[k];
             }
         }
         if (ywall_tile) {
             __syncthreads();
             if (yghost) {
                 const int d1 = gy < 0 ? 1 : -1;
-                float *o = P(s, row, lane);
-                const float *a = P(s, row + d1, lane), *b = P(s, row + 2 * d1, lane);
+                float *o = R(s, row, lane);
+                const float *a = R(s, row + d1, lane), *b = R(s, row + 2 * d1, lane);
 #pragma unroll
-                for (int k = 0; k < Q; k++) o[k] = 2.0f * a[k] - b[k];
+                for (int k = 0; k < CS; k++) o[k] = 2.0f * a[k] - b[k];
             }
         }
     };
-    // step 2 along z: whole plane by extrapolation from the two inner planes (own column)
     auto ghost_z = [&](int pz) __attribute__((always_inline)) {
-        float *o = P(slot_of(pz), row, lane);
-        const float *a = P(slot_of(pz < 0 ? 0 : nz - 1), row, lane), *b = P(slot_of(pz < 0 ? 1 : nz - 2), row, lane);
+        float *o = R(slot_of(pz), row, lane);
+        const float *a = R(slot_of(pz < 0 ? 0 : nz - 1), row, lane);
+        const float *b = R(slot_of(pz < 0 ? 1 : nz - 2), row, lane);
 #pragma unroll
-        for (int k = 0; k < Q; k++) o[k] = 2.0f * a[k] - b[k];
-    };
-
-    // central differences of the own column at plane pz along x or y (from the ring)
-    auto cdiff_x = [&](int pz, float C[Q]) __attribute__((always_inline)) {
-        const int s = slot_of(pz);
-        const float *lo = P(s, row, max(lane - 1, 0)), *hi = P(s, row, min(lane + 1, 31));
-#pragma unroll
-        for (int k = 0; k < Q; k++)
-            if (Lat<Q>::e(k, 0) != 0) C[k] = hi[k] - lo[k];
-    };
-    auto cdiff_y = [&](int pz, float C[Q]) __attribute__((always_inline)) {
-        const int s = slot_of(pz);
-        const float *lo = P(s, max(row - 1, 0), lane), *hi = P(s, min(row + 1, RY - 1), lane);
-#pragma unroll
-        for (int k = 0; k < Q; k++)
-            if (Lat<Q>::e(k, 1) != 0) C[k] = hi[k] - lo[k];
-    };
-    auto cdiff_z = [&](int pz, float C[Q]) __attribute__((always_inline)) {
-        const float *lo = P(slot_of(pz - 1), row, lane), *hi = P(slot_of(pz + 1), row, lane);
-#pragma unroll
-        for (int k = 0; k < Q; k++)
-            if (Lat<Q>::e(k, 2) != 0) C[k] = hi[k] - lo[k];
+        for (int k = 0; k < CS; k++) o[k] = 2.0f * a[k] - b[k];
     };
 
     // direct path for one interface (walls, chunk start): all velocities from the ring,
-    // NEQ at walls, relax. Interface normal to d, L at (rl, ll, plane pl) and R the next cell.
-    auto direct_face = [&](int d, int pl, int gfd, float *out) __attribute__((always_inline)) {
-        const int sL = slot_of(pl), sR = d == 2 ? slot_of(pl + 1) : sL;
-        const int rl = row, ll = lane;
-        auto ptr = [&](int s, int r, int l) __attribute__((always_inline)) -> const float * { return P(s, r, l); };
-        auto rec = [&](int sl, int sr, int r, int l, float F[Q]) __attribute__((always_inline)) {
+    // NEQ at walls, relax. Interface normal to d between the own cell at plane pl and the
+    // next cell along d; gfd is its index along d.
+    auto direct_face = [&](int d, int pl, int gfd, float *out) {
+        auto ptr = [&](int s, int r, int l) __attribute__((always_inline)) -> const float * { return R(s, r, l); };
+        auto rec = [&](int r, int l, int pc, float F[Q]) __attribute__((always_inline)) {
+            // interface normal to d whose low cell is (r, l) at plane pc
+            const int a = slot_of(pc - 1), b = slot_of(pc), c = slot_of(pc + 1);
             if (d == 0)
-                reconstruct<Q, 0, float>(ptr(sl, r, l), ptr(sl, r, l + 1), ptr(sl, r - 1, l), ptr(sl, r - 1, l + 1),
-                                         ptr(sl, r + 1, l), ptr(sl, r + 1, l + 1), ptr(slot_of(pl - 1), r, l),
-                                         ptr(slot_of(pl - 1), r, l + 1), ptr(slot_of(pl + 1), r, l),
-                                         ptr(slot_of(pl + 1), r, l + 1), cf.kappa, F);
+                reconstruct<Q, 0, float>(ptr(b, r, l), ptr(b, r, l + 1), ptr(b, r - 1, l), ptr(b, r - 1, l + 1),
+                                         ptr(b, r + 1, l), ptr(b, r + 1, l + 1), ptr(a, r, l), ptr(a, r, l + 1),
+                                         ptr(c, r, l), ptr(c, r, l + 1), cf.kappa, F);
             else if (d == 1)
-                reconstruct<Q, 1, float>(ptr(sl, r, l), ptr(sl, r + 1, l), ptr(sl, r, l - 1), ptr(sl, r + 1, l - 1),
-                                         ptr(sl, r, l + 1), ptr(sl, r + 1, l + 1), ptr(slot_of(pl - 1), r, l),
-                                         ptr(slot_of(pl - 1), r + 1, l), ptr(slot_of(pl + 1), r, l),
-                                         ptr(slot_of(pl + 1), r + 1, l), cf.kappa, F);
+                reconstruct<Q, 1, float>(ptr(b, r, l), ptr(b, r + 1, l), ptr(b, r, l - 1), ptr(b, r + 1, l - 1),
+                                         ptr(b, r, l + 1), ptr(b, r + 1, l + 1), ptr(a, r, l), ptr(a, r + 1, l),
+                                         ptr(c, r, l), ptr(c, r + 1, l), cf.kappa, F);
             else
-                reconstruct<Q, 2, float>(ptr(sl, r, l), ptr(sr, r, l), ptr(sl, r, l - 1), ptr(sr, r, l - 1),
-                                         ptr(sl, r, l + 1), ptr(sr, r, l + 1), ptr(sl, r - 1, l), ptr(sr, r - 1, l),
-                                         ptr(sl, r + 1, l), ptr(sr, r + 1, l), cf.kappa, F);
+                reconstruct<Q, 2, float>(ptr(b, r, l), ptr(c, r, l), ptr(b, r, l - 1), ptr(c, r, l - 1),
+                                         ptr(b, r, l + 1), ptr(c, r, l + 1), ptr(b, r - 1, l), ptr(c, r - 1, l),
+                                         ptr(b, r + 1, l), ptr(c, r + 1, l), cf.kappa, F);
         };
         float F[Q];
-        rec(sL, sR, rl, ll, F);
+        rec(row, lane, pl, F);
         const int nd = d == 0 ? nx : (d == 1 ? ny : nz);
         const bool per = d == 0 ? perx : (d == 1 ? pery : perz);
         const int wall = !per && (gfd == 0 || gfd == nd);
@@ -363,17 +363,11 @@ __global__ void __launch_bounds__(32 * RY, 1) fused_step3d(const __grid_constant
         if (FORCE) faceG(d, fx, fy, fz, Gb);
         float Fc[Q];
         if (wall) {
-            // x_c: the boundary cell's opposite interface, one cell inward
+            // x_c: the boundary cell's opposite interface, one cell inward (reading R4)
             const int sh = gfd == 0 ? 1 : -1;
-            if (d == 0) rec(sL, sR, rl, ll + sh, Fc);
-            else if (d == 1) rec(sL, sR, rl + sh, ll, Fc);
-            else {
-                const int pc = gfd == 0 ? 0 : nz - 2;
-                const int cL = slot_of(pc), cR = slot_of(pc + 1);
-                reconstruct<Q, 2, float>(ptr(cL, rl, ll), ptr(cR, rl, ll), ptr(cL, rl, ll - 1), ptr(cR, rl, ll - 1),
-                                         ptr(cL, rl, ll + 1), ptr(cR, rl, ll + 1), ptr(cL, rl - 1, ll),
-                                         ptr(cR, rl - 1, ll), ptr(cL, rl + 1, ll), ptr(cR, rl + 1, ll), cf.kappa, Fc);
-            }
+            if (d == 0) rec(row, lane + sh, pl, Fc);
+            else if (d == 1) rec(row + sh, lane, pl, Fc);
+            else rec(row, lane, gfd == 0 ? 0 : nz - 2, Fc);
             if (FORCE) faceG(d, d == 0 ? gfd + sh : fx, d == 1 ? gfd + sh : fy, d == 2 ? gfd + sh : fz, Gc);
         }
         if (d == 0) interface_f<Q, 0, float>(p, cf, F, Gb, wall, gfd == 0 ? 0 : 1, Fc, Gc, out);
@@ -381,59 +375,161 @@ __global__ void __launch_bounds__(32 * RY, 1) fused_step3d(const __grid_constant
         else interface_f<Q, 2, float>(p, cf, F, Gb, wall, gfd == 0 ? 0 : 1, Fc, Gc, out);
     };
 
+    // per-velocity central differences of the own column at plane pz along t (edge
+    // velocities only: a velocity along one axis has no tangential part)
+    auto cdiff = [&](int pz, auto tc, float C[Q]) __attribute__((always_inline)) {
+        constexpr int t = decltype(tc)::value;
+        const float *lo, *hi;
+        if constexpr (t == 0) { lo = R(slot_of(pz), row, max(lane - 1, 0)); hi = R(slot_of(pz), row, min(lane + 1, 31)); }
+        else if constexpr (t == 1) { lo = R(slot_of(pz), max(row - 1, 0), lane); hi = R(slot_of(pz), min(row + 1, RY - 1), lane); }
+        else { lo = R(slot_of(pz - 1), row, lane); hi = R(slot_of(pz + 1), row, lane); }
+        sfor<Q>([&](auto kc) {
+            constexpr int k = kc;
+            constexpr int nzc = (Lat<Q>::e(k, 0) != 0) + (Lat<Q>::e(k, 1) != 0) + (Lat<Q>::e(k, 2) != 0);
+            if constexpr (nzc >= 2 && Lat<Q>::e(k, t) != 0) C[k] = hi[k] - lo[k];
+            else C[k] = 0.0f;
+        });
+    };
+    auto mdiff = [&](int pz, auto tc, float dM[4]) __attribute__((always_inline)) {
+        constexpr int t = decltype(tc)::value;
+        const float *lo, *hi;
+        if constexpr (t == 0) { lo = R(slot_of(pz), row, max(lane - 1, 0)); hi = R(slot_of(pz), row, min(lane + 1, 31)); }
+        else if constexpr (t == 1) { lo = R(slot_of(pz), max(row - 1, 0), lane); hi = R(slot_of(pz), min(row + 1, RY - 1), lane); }
+        else { lo = R(slot_of(pz - 1), row, lane); hi = R(slot_of(pz + 1), row, lane); }
+        moment_diff<t>(lo + Q, hi + Q, dM);
+    };
+    constexpr std::integral_constant<int, 0> AX{};
+    constexpr std::integral_constant<int, 1> AY{};
+    constexpr std::integral_constant<int, 2> AZ{};
+
     // ---------------- prologue: planes z0-1, z0, z0+1 ----------------
-    Mom mc, mn;  // moments of fbar+ at the current and the next plane
-    {
-        for (int pz = z0 - 1; pz <= z0 + 1; pz++) {
-            if (!perz && (pz < 0 || pz >= nz)) continue;
-            const Mom t = make_phi(pz);
-            if (pz == z0) mc = t;
-            if (pz == z0 + 1) mn = t;
-        }
-        for (int pz = z0 - 1; pz <= z0 + 1; pz++) {
-            if (!perz && (pz < 0 || pz >= nz)) continue;
-            ghosts_xy(pz);
-        }
-        __syncthreads();
-        for (int pz = z0 - 1; pz <= z0 + 1; pz++)
-            if (!perz && (pz < 0 || pz >= nz)) ghost_z(pz);
-        __syncthreads();
-        // ghost columns and ghost planes: moments from the ring
-        if (!load) mc = ring_moments(z0);
-        if (!load || (!perz && z0 + 1 >= nz)) mn = ring_moments(z0 + 1);
+    for (int pz = z0 - 1; pz <= z0 + 1; pz++) {
+        if (!perz && (pz < 0 || pz >= nz)) continue;
+        make_phi(pz, US(pz));  // (plane z0+1 overwrites the u0 of plane z0-1: same parity)
     }
+    for (int pz = z0 - 1; pz <= z0 + 1; pz++) {
+        if (!perz && (pz < 0 || pz >= nz)) continue;
+        ghosts_xy(pz);
+    }
+    __syncthreads();
+    for (int pz = z0 - 1; pz <= z0 + 1; pz++)
+        if (!perz && (pz < 0 || pz >= nz)) ghost_z(pz);
+    __syncthreads();
+
     // carried: alpha_z, A_z of the current plane and f at its -z interface
     float alz[NF], Az[4], fzm[NF];
+#pragma unroll
+    for (int i = 0; i < NF; i++) alz[i] = fzm[i] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; i++) Az[i] = 0.0f;
     if (upd) {
-        float C1[Q], C2[Q], E01, E11[3], E02, E12[3], bz[NF], Bz[4];
-        cdiff_x(z0, C1);
-        cdiff_y(z0, C2);
-        diff_moments<Q, 0>(C1, E01, E11);
-        diff_moments<Q, 1>(C2, E02, E12);
-        face_parts<Q, 2>(P(slot_of(z0), row, lane), C1, C2, E01, E11, E02, E12, mc.M0, mc.M1, mc.M2, cf.kappa, alz,
-                         bz, Az, Bz);
+        float C1[Q], C2[Q], d1[4], d2[4], bz[NF], Bz[4];
+        cdiff(z0, AX, C1);
+        cdiff(z0, AY, C2);
+        mdiff(z0, AX, d1);
+        mdiff(z0, AY, d2);
+        const float *c = R(slot_of(z0), row, lane);
+        face_parts<Q, 2>(c, c + Q, C1, C2, d1, d2, cf.kappa, alz, bz, Az, Bz);
         float t[NF];
         direct_face(2, z0 - 1, z0, t);
 #pragma unroll
         for (int i = 0; i < NF; i++) fzm[i] = t[i];
     }
 
-    const bool xrow = row >= 1 && row <= K::TYI && gy >= 0 && gy < ny;       // needs x parts
-    const bool ycol = lane >= 1 && lane <= K::TXI && gx >= 0 && gx < nx;     // needs y parts
-    const bool need_x = xrow && lane <= K::TXI && gx >= -1 && gx < nx;       // owns its +x interface
-    const bool need_y = ycol && row <= K::TYI && gy >= -1 && gy < ny;        // owns its +y interface
-
     for (int kz = z0; kz < z1; kz++) {
-        // ---- P2a: z parts of plane kz+1 and the z interface kz+1/2 ----
+        // ---- P1: fbar+ of plane kz+1 (planes z0 .. z0+1 were made in the prologue) ----
+        if (kz > z0) {
+            const int pn = kz + 1;
+            if (perz || pn < nz) {
+                make_phi(pn, US(pn));
+                ghosts_xy(pn);
+            } else if (pn == nz) {
+                ghost_z(pn);
+            }
+            __syncthreads();
+        }
+        const float *cur = R(slot_of(kz), row, lane);
+
+        // ---- P3: x interfaces of plane kz (beta parts exchanged by shuffles) ----
+        float Cz[Q], dz[4];
+        cdiff(kz, AZ, Cz);
+        mdiff(kz, AZ, dz);
+        float fxp[NF];
+#pragma unroll
+        for (int i = 0; i < NF; i++) fxp[i] = 0.0f;
+        if (row >= 1 && row <= K::TYI) {  // warp-uniform: halo rows own no x interface
+            float alx[NF], bex[NF], Ax[4], Bx[4];
+            float Cy[Q], dy[4];
+            cdiff(kz, AY, Cy);
+            mdiff(kz, AY, dy);
+            face_parts<Q, 0>(cur, cur + Q, Cy, Cz, dy, dz, cf.kappa, alx, bex, Ax, Bx);
+            float F[NF], jb[3];
+#pragma unroll
+            for (int i = 0; i < NF; i++) F[i] = alx[i] + __shfl_down_sync(0xffffffffu, bex[i], 1);
+            const float drb = Ax[0] + __shfl_down_sync(0xffffffffu, Bx[0], 1);
+#pragma unroll
+            for (int a = 0; a < 3; a++) jb[a] = Ax[1 + a] + __shfl_down_sync(0xffffffffu, Bx[1 + a], 1);
+            if (need_x) {
+                if (!perx && (gx == -1 || gx == nx - 1)) {
+                    float t[NF];
+                    direct_face(0, kz, gx + 1, t);
+#pragma unroll
+                    for (int i = 0; i < NF; i++) fxp[i] = t[i];
+                } else {
+                    float Gb[3] = {0.0f, 0.0f, 0.0f};
+                    if (FORCE) faceG(0, gx + 1, gy, kz, Gb);
+                    face_relax<Q, 0, FORCE>(cf, F, drb, jb, Gb, fxp);
+                }
+            }
+        }
+        // ---- P4: y parts of plane kz; publish beta_y, B_y; y interfaces ----
+        float aly[NF], Ay[4];
+        if (ycol) {
+            float bey[NF], By[4], Cx[Q], dx[4];
+            cdiff(kz, AX, Cx);
+            mdiff(kz, AX, dx);
+            face_parts<Q, 1>(cur, cur + Q, Cx, Cz, dx, dz, cf.kappa, aly, bey, Ay, By);
+            float *b = xb + (row * 32 + lane) * K::BS;
+#pragma unroll
+            for (int i = 0; i < NF; i++) b[i] = bey[i];
+#pragma unroll
+            for (int i = 0; i < 4; i++) b[NF + i] = By[i];
+        }
+        __syncthreads();
+        float fyp[NF];
+        if (need_y) {
+            if (!pery && (gy == -1 || gy == ny - 1)) {
+                float t[NF];
+                direct_face(1, kz, gy + 1, t);
+#pragma unroll
+                for (int i = 0; i < NF; i++) fyp[i] = t[i];
+            } else {
+                const float *nb = xb + ((row + 1) * 32 + lane) * K::BS;
+                float F[NF], jb[3];
+#pragma unroll
+                for (int i = 0; i < NF; i++) F[i] = aly[i] + nb[i];
+#pragma unroll
+                for (int a = 0; a < 3; a++) jb[a] = Ay[1 + a] + nb[NF + 1 + a];
+                float Gb[3] = {0.0f, 0.0f, 0.0f};
+                if (FORCE) faceG(1, gx, gy + 1, kz, Gb);
+                face_relax<Q, 1, FORCE>(cf, F, Ay[0] + nb[NF], jb, Gb, fyp);
+            }
+            float *o = xf + (row * 32 + lane) * K::FS;
+#pragma unroll
+            for (int i = 0; i < NF; i++) o[i] = fyp[i];
+        }
+        __syncthreads();
+
+        // ---- P2: z parts of plane kz+1 and the z interface kz+1/2 ----
         float alzn[NF], Azn[4], fzp[NF];
         if (upd) {
-            float Cxn[Q], Cyn[Q], Exn0, Exn1[3], Eyn0, Eyn1[3], bezn[NF], Bzn[4];
-            cdiff_x(kz + 1, Cxn);
-            cdiff_y(kz + 1, Cyn);
-            diff_moments<Q, 0>(Cxn, Exn0, Exn1);
-            diff_moments<Q, 1>(Cyn, Eyn0, Eyn1);
-            face_parts<Q, 2>(P(slot_of(kz + 1), row, lane), Cxn, Cyn, Exn0, Exn1, Eyn0, Eyn1, mn.M0, mn.M1, mn.M2,
-                             cf.kappa, alzn, bezn, Azn, Bzn);
+            float C1[Q], C2[Q], d1[4], d2[4], bezn[NF], Bzn[4];
+            cdiff(kz + 1, AX, C1);
+            cdiff(kz + 1, AY, C2);
+            mdiff(kz + 1, AX, d1);
+            mdiff(kz + 1, AY, d2);
+            const float *nxt = R(slot_of(kz + 1), row, lane);
+            face_parts<Q, 2>(nxt, nxt + Q, C1, C2, d1, d2, cf.kappa, alzn, bezn, Azn, Bzn);
             if (!perz && kz + 1 == nz) {
                 float t[NF];
                 direct_face(2, kz, kz + 1, t);
@@ -450,98 +546,23 @@ __global__ void __launch_bounds__(32 * RY, 1) fused_step3d(const __grid_constant
                 face_relax<Q, 2, FORCE>(cf, F, Az[0] + Bzn[0], jb, Gb, fzp);
             }
         }
-        // ---- P2b: x and y parts of plane kz; publish the beta parts ----
-        float alx[NF], Ax[4], aly[NF], Ay[4];
-        {
-            float Cz[Q], Ez0, Ez1[3];
-            cdiff_z(kz, Cz);
-            diff_moments<Q, 2>(Cz, Ez0, Ez1);
-            const float *phk = P(slot_of(kz), row, lane);
-            float *x = X(row, lane);
-            if (xrow) {
-                float Cy[Q], Ey0, Ey1[3], bex[NF], Bx[4];
-                cdiff_y(kz, Cy);
-                diff_moments<Q, 1>(Cy, Ey0, Ey1);
-                face_parts<Q, 0>(phk, Cy, Cz, Ey0, Ey1, Ez0, Ez1, mc.M0, mc.M1, mc.M2, cf.kappa, alx, bex, Ax, Bx);
-#pragma unroll
-                for (int i = 0; i < NF; i++) x[i] = bex[i];
-#pragma unroll
-                for (int i = 0; i < 4; i++) x[NF + i] = Bx[i];
-            }
-            if (ycol) {
-                float Cx[Q], Ex0, Ex1[3], bey[NF], By[4];
-                cdiff_x(kz, Cx);
-                diff_moments<Q, 0>(Cx, Ex0, Ex1);
-                face_parts<Q, 1>(phk, Cx, Cz, Ex0, Ex1, Ez0, Ez1, mc.M0, mc.M1, mc.M2, cf.kappa, aly, bey, Ay, By);
-#pragma unroll
-                for (int i = 0; i < NF; i++) x[NF + 4 + i] = bey[i];
-#pragma unroll
-                for (int i = 0; i < 4; i++) x[2 * NF + 4 + i] = By[i];
-            }
-        }
-        __syncthreads();
 
-        // ---- P3: +x and +y interfaces of the own cell ----
-        float fxp[NF], fyp[NF];
-        if (need_x) {
-            if (!perx && (gx == -1 || gx == nx - 1)) {
-                float t[NF];
-                direct_face(0, kz, gx + 1, t);
+        // ---- P5: steps 8-9, update of cell (gx, gy, kz) ----
+        float fxm[NF];
+        if (row >= 1 && row <= K::TYI) {
 #pragma unroll
-                for (int i = 0; i < NF; i++) fxp[i] = t[i];
-            } else {
-                const float *nb = X(row, lane + 1);
-                float F[NF], jb[3];
-#pragma unroll
-                for (int i = 0; i < NF; i++) F[i] = alx[i] + nb[i];
-#pragma unroll
-                for (int a = 0; a < 3; a++) jb[a] = Ax[1 + a] + nb[NF + 1 + a];
-                float Gb[3] = {0.0f, 0.0f, 0.0f};
-                if (FORCE) faceG(0, gx + 1, gy, kz, Gb);
-                face_relax<Q, 0, FORCE>(cf, F, Ax[0] + nb[NF], jb, Gb, fxp);
-            }
+            for (int i = 0; i < NF; i++) fxm[i] = __shfl_up_sync(0xffffffffu, fxp[i], 1);
         }
-        if (need_y) {
-            if (!pery && (gy == -1 || gy == ny - 1)) {
-                float t[NF];
-                direct_face(1, kz, gy + 1, t);
-#pragma unroll
-                for (int i = 0; i < NF; i++) fyp[i] = t[i];
-            } else {
-                const float *nb = X(row + 1, lane) + NF + 4;
-                float F[NF], jb[3];
-#pragma unroll
-                for (int i = 0; i < NF; i++) F[i] = aly[i] + nb[i];
-#pragma unroll
-                for (int a = 0; a < 3; a++) jb[a] = Ay[1 + a] + nb[NF + 1 + a];
-                float Gb[3] = {0.0f, 0.0f, 0.0f};
-                if (FORCE) faceG(1, gx, gy + 1, kz, Gb);
-                face_relax<Q, 1, FORCE>(cf, F, Ay[0] + nb[NF], jb, Gb, fyp);
-            }
-        }
-        __syncthreads();
-        {
-            float *x = X(row, lane);
-            if (need_x)
-#pragma unroll
-                for (int i = 0; i < NF; i++) x[i] = fxp[i];
-            if (need_y)
-#pragma unroll
-                for (int i = 0; i < NF; i++) x[NF + 4 + i] = fyp[i];
-        }
-        __syncthreads();
-
-        // ---- P4: steps 8-9, update of cell (gx, gy, kz) ----
         if (upd) {
-            const float *xm = X(row, lane - 1), *ym = X(row - 1, lane) + NF + 4;
-            const float *ph = P(slot_of(kz), row, lane);
+            const float *ym = xf + ((row - 1) * 32 + lane) * K::FS;
+            const float *u0 = US(kz);
             const int64_t off = (int64_t)kz * p.plane + (int64_t)gy * p.px + gx;
             sfor<Q>([&](auto kc) {
                 constexpr int k = kc;
                 float acc = 0.0f;
                 if constexpr (Lat<Q>::e(k, 0) != 0) {
                     constexpr int i = flux_index<Q>(0, k);
-                    acc = fmaf((float)Lat<Q>::e(k, 0), fxp[i] - xm[i], acc);
+                    acc = fmaf((float)Lat<Q>::e(k, 0), fxp[i] - fxm[i], acc);
                 }
                 if constexpr (Lat<Q>::e(k, 1) != 0) {
                     constexpr int i = flux_index<Q>(1, k);
@@ -551,32 +572,16 @@ __global__ void __launch_bounds__(32 * RY, 1) fused_step3d(const __grid_constant
                     constexpr int i = flux_index<Q>(2, k);
                     acc = fmaf((float)Lat<Q>::e(k, 2), fzp[i] - fzm[i], acc);
                 }
-                // eq. f_tilde_+ in increment form, then eq. evolution_equation
-                const float gold = (float)Store<S>::ld(src + k * p.dstride + off);
-                const float u0 = fmaf(1.0f / 3.0f, ph[k] - gold, ph[k]);
-                Store<S>::st(dst + k * p.dstride + off, fmaf(-cf.two_kappa, acc, u0));
+                // eq. evolution_equation: f~(t+dt) = f~+ - dt/|V| flux
+                Store<S>::st(dst + k * p.dstride + off, fmaf(-cf.two_kappa, acc, u0[k]));
             });
 #pragma unroll
             for (int i = 0; i < NF; i++) { fzm[i] = fzp[i]; alz[i] = alzn[i]; }
 #pragma unroll
             for (int i = 0; i < 4; i++) Az[i] = Azn[i];
         }
-        // ---- P1: fbar+ of plane kz+2 into the ring slot of plane kz-1 ----
-        mc = mn;
-        if (kz + 1 < z1) {
-            const int pn = kz + 2;
-            __syncthreads();  // every thread is done with the ring slot of kz-1
-            if (perz || pn < nz) {
-                mn = make_phi(pn);
-                ghosts_xy(pn);
-                __syncthreads();
-                if (!load) mn = ring_moments(pn);
-            } else if (pn == nz) {
-                ghost_z(pn);
-                __syncthreads();
-                mn = ring_moments(pn);
-            }
-        }
+        // the next P1 overwrites the ring slot of plane kz-1, last read in P3/P4 above and
+        // separated from it by the barrier before P5
     }
 }
 
