@@ -164,6 +164,36 @@ int64_t dugks_launch_count(dugks_t h);
 const char *dugks_last_error(dugks_t h);
 void dugks_destroy(dugks_t h);
 
+/* Allocation-free FP64 residual and conservation totals (the paper has no counterpart; this
+ * is a library facility). Same reduction and the same outputs as dugks_residual, for callers
+ * that cannot call cudaMalloc: code running while a CUDA graph is being captured, hosts whose
+ * own allocator already owns the device memory, and loops that must not take cudaMalloc's
+ * implicit device synchronisation. Nothing is allocated: the partial sums go to a fixed
+ * 512 KB array in device memory that the library reserves on every GPU that loads it, held
+ * until the process exits.
+ *   state:  DEVICE pointer to g~ = f~ - W rho0 in the storage type `store`, unpadded layout
+ *           [Q][nz][ny][nx] (what dugks_get_state writes with buf_is_device = 1).
+ *   nx, ny, nz, lattice: the mesh and velocity set (nz = 1 and DUGKS_D2Q9 in 2D).
+ *   rt, rho0: RT and rho0 of the simulation.
+ *   shift:  HOST [3] doubles or NULL: the uniform part of the velocity shift of eq.
+ *           macro_values, G(t) dt/2 (u = c/rho0 sum_k e_k g~_k + shift).
+ *   shift_field: DEVICE [dim][ncell] floats or NULL: the per-cell part of that shift.
+ *   uprev:  DEVICE [dim][ncell] doubles owned by the caller: the velocity of the previous
+ *           call, read when have_prev != 0 and overwritten with the current velocity.
+ *   out:    HOST [dim+2] doubles: out[0] = ||u - uprev||/||u|| (+inf when have_prev == 0),
+ *           out[1] = sum rho, out[2+a] = sum rho0 u_a.
+ *   stream: cudaStream_t (NULL: legacy stream); the call synchronises it before returning.
+ * Limit: at most 16,777,216 cells (256^3); larger meshes return DUGKS_E_INVAL with the
+ * limit in dugks_last_error(NULL). The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ * capture. Every call on a device shares the one array: calls that overlap on the GPU (from
+ * several streams or threads) race and give wrong sums. Each call rewrites every partial it
+ * reads, so nothing has to be cleared between calls. Errors: DUGKS_E_INVAL, DUGKS_E_CUDA,
+ * DUGKS_E_UNSTABLE (non-finite sums); the reason is in dugks_last_error(NULL). */
+int dugks_residual_static(int32_t lattice, int32_t store, const void *state, int64_t nx, int64_t ny, int64_t nz,
+                          double rt, double rho0, const double *shift, const float *shift_field, double *uprev,
+                          int32_t have_prev, double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -50,6 +50,10 @@ struct dugks_s {
 
 static thread_local std::string g_create_error;
 
+namespace dugks {
+void set_null_handle_error(const char *msg) { g_create_error = msg; }
+}  // namespace dugks
+
 static int fail(dugks_t h, int code, const char *fmt, ...) {
     char buf[512];
     va_list ap;

@@ -29,4 +29,7 @@ cudaError_t launch_residual(int q, int store, const StepParams &p, double t, dou
 int residual_blocks(int64_t ncell);
 cudaError_t launch_advance(long long *ctr, long long n, cudaStream_t stream);
 
+// Sets the message that dugks_last_error(NULL) returns in this thread (api.cu).
+void set_null_handle_error(const char *msg);
+
 }  // namespace dugks

@@ -29,7 +29,7 @@ EXPORTS = [
     "dugks_opts_default", "dugks_create", "dugks_init", "dugks_step", "dugks_moments",
     "dugks_residual", "dugks_state_bytes", "dugks_get_state", "dugks_set_state",
     "dugks_get_clock", "dugks_set_clock", "dugks_set_force_field", "dugks_sync",
-    "dugks_launch_count", "dugks_last_error", "dugks_destroy",
+    "dugks_launch_count", "dugks_last_error", "dugks_destroy", "dugks_residual_static",
 ]
 
 
@@ -94,6 +94,7 @@ def load(path=None):
     lib.dugks_last_error.restype = C.c_char_p
     lib.dugks_destroy.argtypes = [P]
     lib.dugks_destroy.restype = None
+    lib.dugks_residual_static.argtypes = [I32, I32, P, I64, I64, I64, C.c_double, C.c_double, D, P, P, I32, D, P]
     _lib = lib
     return lib
 
