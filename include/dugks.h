@@ -164,6 +164,36 @@ int64_t dugks_launch_count(dugks_t h);
 const char *dugks_last_error(dugks_t h);
 void dugks_destroy(dugks_t h);
 
+/* ---- batched form: many independent 2D instances ---------------------------------------
+ * A batch advances `count` independent D2Q9 instances (each its own mesh, viscosity,
+ * acceleration and boundaries; shared dt, RT, rho0 and storage from opts) together: one time
+ * step of the whole batch is one persistent kernel launch over a work list of (instance,
+ * tile) items, largest instances first, and dugks_batch_step replays n such launches as one
+ * captured CUDA graph. The per-instance scheme is exactly that of dugks_step (Appendix
+ * steps 1-10 of the paper). meshes/nu/forces/bcs: HOST arrays of `count` records (a force
+ * field pointer, if any, is a DEVICE [2][ncell] float array read at every step). opts may
+ * be NULL; opts->tile_x/tile_y pick the tile (32x8, 16x8, 32x4 or 64x4), else 32x8.
+ * Errors as for the single-instance calls; dugks_batch_last_error(b) gives the reason
+ * (NULL b: the last failed dugks_batch_create in this thread). */
+typedef struct dugks_batch_s *dugks_batch_t;
+int dugks_batch_create(int32_t count, const dugks_mesh *meshes, const double *nu, double dt,
+                       const dugks_force *forces, const dugks_boundaries *bcs, const dugks_opts *opts,
+                       dugks_batch_t *out);
+/* Initial state of instance i (as dugks_init: f~ = f_eq(rho0 + p/RT, u), HOST fields or NULL). */
+int dugks_batch_init(dugks_batch_t b, int32_t i, const double *p, const double *u);
+/* Advance every instance by n steps (asynchronous). */
+int dugks_batch_step(dugks_batch_t b, int64_t n);
+/* Moments of instance i: [3][ncell_i] floats (p, u_x, u_y); synchronous. */
+int dugks_batch_moments(dugks_batch_t b, int32_t i, float *out, int32_t out_is_device);
+/* Autotuner: times each built tile shape on a copy of the batch state (the state and clock
+ * are restored), keeps the fastest and caches the choice per (instance sizes, storage, SM
+ * count) for the process. Writes the chosen tile to tile_x/tile_y (may be NULL). */
+int dugks_batch_tune(dugks_batch_t b, int32_t *tile_x, int32_t *tile_y);
+int dugks_batch_sync(dugks_batch_t b);
+int64_t dugks_batch_launch_count(dugks_batch_t b);
+const char *dugks_batch_last_error(dugks_batch_t b);
+void dugks_batch_destroy(dugks_batch_t b);
+
 /* Allocation-free FP64 residual and conservation totals (the paper has no counterpart; this
  * is a library facility). Same reduction and the same outputs as dugks_residual, for callers
  * that cannot call cudaMalloc: code running while a CUDA graph is being captured, hosts whose

@@ -121,13 +121,15 @@ __device__ __forceinline__ void cell_G(const StepParams &p, int64_t cell, int64_
     }
 }
 
+// One tile of the fused step: cells [x0, x0+TX) x [y0, y0+TY) x [z0, z1) of the instance
+// described by p, with the CTA's TX*TY threads and its dynamic shared memory.
 template <int Q, class S, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) fused_step(const __grid_constant__ StepParams p, int zchunk) {
+__device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, int z0, int z1,
+                                          unsigned char *smem_raw) {
     using T = typename Arith<S>::T;
     using K = StepShape<Q, TX, TY, T>;
     constexpr int D = K::D;
     constexpr int RX = K::RX, RY = K::RY, NT = K::NT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T *smem = reinterpret_cast<T *>(smem_raw);
     T *phi = smem;                                       // [NP][RY][RX][Q]
     T *xf = phi + K::NP * K::PLANE;                      // [TY][TX+1][SX]
@@ -136,10 +138,7 @@ __global__ void __launch_bounds__(TX *TY) fused_step(const __grid_constant__ Ste
 
     const int tid = threadIdx.x;
     const int lx = tid % TX, ly = tid / TX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const int z0 = blockIdx.z * zchunk;
-    const int z1 = min(nz, z0 + zchunk);
     const int64_t ncell = (int64_t)nx * ny * nz;
     const bool perx = p.bc[0] == 0, pery = p.bc[2] == 0, perz = D == 3 ? p.bc[4] == 0 : true;
     const S *src = reinterpret_cast<const S *>(p.src);
@@ -393,6 +392,30 @@ __global__ void __launch_bounds__(TX *TY) fused_step(const __grid_constant__ Ste
                 }
             }
         }
+    }
+}
+
+template <int Q, class S, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY) fused_step(const __grid_constant__ StepParams p, int zchunk) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int z0 = blockIdx.z * zchunk;
+    const int z1 = min(p.nz, z0 + zchunk);
+    step_tile<Q, S, TX, TY>(p, blockIdx.x * TX, blockIdx.y * TY, z0, z1, smem_raw);
+}
+
+// Batched form: many independent 2D instances in one persistent launch. params holds two
+// descriptors per instance (source/destination buffers swapped: index 2 i + parity); items
+// is the work list of (instance, x0, y0) tiles, largest instances first; CTA b takes items
+// b, b + gridDim.x, ...
+template <int Q, class S, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY) fused_step_batch(const StepParams *__restrict__ params,
+                                                           const int4 *__restrict__ items, int nitems, int parity) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int4 w = items[it];
+        const StepParams &p = params[2 * w.x + parity];
+        step_tile<Q, S, TX, TY>(p, w.y, w.z, 0, 1, smem_raw);
+        __syncthreads();  // the next item reuses the shared buffers
     }
 }
 

@@ -30,6 +30,8 @@ EXPORTS = [
     "dugks_residual", "dugks_state_bytes", "dugks_get_state", "dugks_set_state",
     "dugks_get_clock", "dugks_set_clock", "dugks_set_force_field", "dugks_sync",
     "dugks_launch_count", "dugks_last_error", "dugks_destroy", "dugks_residual_static",
+    "dugks_batch_create", "dugks_batch_init", "dugks_batch_step", "dugks_batch_moments", "dugks_batch_tune",
+    "dugks_batch_sync", "dugks_batch_launch_count", "dugks_batch_last_error", "dugks_batch_destroy",
 ]
 
 
@@ -95,6 +97,19 @@ def load(path=None):
     lib.dugks_destroy.argtypes = [P]
     lib.dugks_destroy.restype = None
     lib.dugks_residual_static.argtypes = [I32, I32, P, I64, I64, I64, C.c_double, C.c_double, D, P, P, I32, D, P]
+    lib.dugks_batch_create.argtypes = [I32, C.POINTER(Mesh), D, C.c_double, C.POINTER(Force), C.POINTER(Boundaries),
+                                       C.POINTER(Opts), C.POINTER(P)]
+    lib.dugks_batch_init.argtypes = [P, I32, D, D]
+    lib.dugks_batch_step.argtypes = [P, I64]
+    lib.dugks_batch_moments.argtypes = [P, I32, P, I32]
+    lib.dugks_batch_tune.argtypes = [P, C.POINTER(I32), C.POINTER(I32)]
+    lib.dugks_batch_sync.argtypes = [P]
+    lib.dugks_batch_launch_count.argtypes = [P]
+    lib.dugks_batch_launch_count.restype = I64
+    lib.dugks_batch_last_error.argtypes = [P]
+    lib.dugks_batch_last_error.restype = C.c_char_p
+    lib.dugks_batch_destroy.argtypes = [P]
+    lib.dugks_batch_destroy.restype = None
     _lib = lib
     return lib
 
@@ -238,3 +253,86 @@ class Sim:
 
     def launch_count(self):
         return self.lib.dugks_launch_count(self.h)
+
+
+class Batch:
+    """Many independent D2Q9 instances advanced together (see ``dugks_batch_*``).
+
+    ``instances``: list of dicts with ``shape`` (nx, ny), ``nu``, optional ``g``, ``omega``,
+    ``field`` (CUDA float tensor [2][ncell]), ``bcs`` and ``dx``; shared ``dt``, ``rt``,
+    ``rho0``, ``store``.
+    """
+
+    def __init__(self, instances, dt, rt=1.0 / 3.0, rho0=1.0, store=STORE_F32, stream=None, tile=None):
+        lib = load()
+        self.lib = lib
+        n = len(instances)
+        self.count = n
+        meshes = (Mesh * n)()
+        nus = (C.c_double * n)()
+        forces = (Force * n)()
+        bcs = (Boundaries * n)()
+        self._fields = []
+        self.shapes = []
+        for i, ins in enumerate(instances):
+            nx, ny = int(ins["shape"][0]), int(ins["shape"][1])
+            self.shapes.append((nx, ny))
+            meshes[i] = Mesh(2, nx, ny, 1, float(ins.get("dx", 1.0)))
+            nus[i] = float(ins["nu"])
+            g = ins.get("g", (0.0, 0.0, 0.0))
+            for a in range(3):
+                forces[i].g[a] = float(g[a]) if a < len(g) else 0.0
+            forces[i].omega = float(ins.get("omega", 0.0))
+            fld = ins.get("field")
+            self._fields.append(fld)
+            forces[i].field = None if fld is None else int(fld.data_ptr())
+            bcs[i] = make_bcs(ins.get("bcs"))
+        o = Opts()
+        lib.dugks_opts_default(C.byref(o))
+        o.rt, o.rho0, o.store = float(rt), float(rho0), int(store)
+        o.stream = None if stream is None else int(stream)
+        if tile:
+            o.tile_x, o.tile_y = int(tile[0]), int(tile[1])
+        h = C.c_void_p()
+        rc = lib.dugks_batch_create(n, meshes, C.cast(nus, C.POINTER(C.c_double)), float(dt), forces, bcs,
+                                    C.byref(o), C.byref(h))
+        if rc != DUGKS_OK:
+            raise DugksError(rc, lib.dugks_batch_last_error(None).decode(errors="replace"))
+        self.h = h
+
+    def _check(self, rc):
+        if rc != DUGKS_OK:
+            raise DugksError(rc, self.lib.dugks_batch_last_error(self.h).decode(errors="replace"))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dugks_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def init(self, i, p=None, u=None):
+        p = None if p is None else np.ascontiguousarray(p, dtype=np.float64).ravel()
+        u = None if u is None else np.ascontiguousarray(u, dtype=np.float64).ravel()
+        self._check(self.lib.dugks_batch_init(self.h, int(i), _dp(p), _dp(u)))
+
+    def step(self, n=1):
+        self._check(self.lib.dugks_batch_step(self.h, int(n)))
+
+    def sync(self):
+        self._check(self.lib.dugks_batch_sync(self.h))
+
+    def moments(self, i):
+        nx, ny = self.shapes[i]
+        a = np.zeros((3, nx * ny), dtype=np.float32)
+        self._check(self.lib.dugks_batch_moments(self.h, int(i), a.ctypes.data_as(C.c_void_p), 0))
+        return a
+
+    def tune(self):
+        tx, ty = C.c_int32(), C.c_int32()
+        self._check(self.lib.dugks_batch_tune(self.h, C.byref(tx), C.byref(ty)))
+        return tx.value, ty.value
+
+    def launch_count(self):
+        return self.lib.dugks_batch_launch_count(self.h)
