@@ -154,6 +154,10 @@ int dugks_set_clock(dugks_t h, int64_t step);
 /* Replace the per-cell acceleration field (device [dim][ncell] floats, or NULL). */
 int dugks_set_force_field(dugks_t h, const float *field);
 
+/* Replace the wall velocities u and wall pressures p of the boundaries given at creation.
+ * The face types must be unchanged (DUGKS_E_INVAL otherwise). Takes effect at the next step. */
+int dugks_set_boundaries(dugks_t h, const dugks_boundaries *bcs);
+
 /* Wait for the handle's stream, polling for at most timeout_s seconds (<= 0: no limit).
  * DUGKS_E_TIMEOUT if the work has not finished by then (the work keeps running). */
 int dugks_sync(dugks_t h, double timeout_s);
@@ -163,6 +167,34 @@ int64_t dugks_launch_count(dugks_t h);
 
 const char *dugks_last_error(dugks_t h);
 void dugks_destroy(dugks_t h);
+
+/* ---- differentiation: checkpointed adjoint of the step (D2Q9, F32 or F64 storage) -------
+ * The paper has no adjoint; these two calls give the gradient of a loss of the final
+ * moments with respect to the acceleration field, the wall velocities and the initial state,
+ * through the exact discrete adjoint of the step (Appendix steps 1-10, transposed step by
+ * step in the handle's arithmetic type).
+ *
+ * dugks_record runs nsteps steps from the current state, exactly as dugks_step does, and
+ * keeps a device copy of the state every `every` steps (ceil(nsteps/every) state buffers plus
+ * every-1 buffers for the reverse sweep, owned by the handle and reused by later calls). The
+ * handle's clock advances by nsteps. A new record replaces the previous one.
+ *
+ * dugks_adjoint takes dL_dmom = dL/d(moments at the end of the recorded rollout), a DEVICE
+ * [3][ncell] float array in the layout of dugks_moments (p, u_x, u_y), and runs the reverse
+ * sweep: for each checkpoint segment, last first, it recomputes the segment's states from its
+ * checkpoint and applies the transposed step to them in reverse order. Outputs (each may be
+ * NULL when not wanted):
+ *   dL_dfield  DEVICE [2][ncell] floats: dL/d(acceleration field) (the per-cell G of
+ *              dugks_force, whether or not a field is set), overwritten;
+ *   dL_dwall   HOST [6][3] doubles: dL/d(u of each face) for velocity walls, zero elsewhere;
+ *   dL_dstate0 DEVICE [Q][ncell] values of the storage type: dL/d(state at the start of the
+ *              rollout), unpadded layout as dugks_get_state.
+ * The acceleration, wall velocities and viscosity must be those of the recorded rollout.
+ * Synchronous. DUGKS_E_UNSUPPORTED for 3D lattices or BF16/F16 storage; DUGKS_E_INVAL
+ * without a recorded rollout. Memory: (ceil(nsteps/every) + every - 1) x the state size plus
+ * about 7 state sizes of work buffers. */
+int dugks_record(dugks_t h, int64_t nsteps, int32_t every);
+int dugks_adjoint(dugks_t h, const float *dL_dmom, float *dL_dfield, double *dL_dwall, void *dL_dstate0);
 
 /* ---- batched form: many independent 2D instances ---------------------------------------
  * A batch advances `count` independent D2Q9 instances (each its own mesh, viscosity,

@@ -6,4 +6,4 @@ The compute path is the C-ABI library ``libdugks.so`` (hand-written CUDA kernels
 synthetic inputs. Importing the package does not load the library; ``dugks.load()`` does,
 and fails loudly when the library has not been built.
 """
-__all__ = ["dugks", "workloads"]
+__all__ = ["dugks", "autograd", "workloads"]

@@ -1,0 +1,767 @@
+// adjoint2d.cu -- hand-written discrete adjoint of the 2D (D2Q9) DUGKS step, and the
+// checkpointed reverse sweep behind dugks_record / dugks_adjoint.
+//
+// One step Phi: g~^n -> g~^{n+1} (Appendix steps 1-10 of arXiv 1411.6121 in deviation form,
+// as dugks_step.cuh computes it) depends on the acceleration field G(x) and on the wall
+// velocities u_w. For lambda' = dL/dg~^{n+1} one reverse step forms
+//     lambda = (dPhi/dg~^n)^T lambda',  dL/dG += (dPhi/dG)^T lambda',  dL/du_w += (dPhi/du_w)^T lambda'
+// by running the sub-steps backwards in three gather-form kernels:
+//   adj_cells_fwd (per cell)       recomputes the cell moments (eq. macro_values) and
+//                                  fbar+ (step 1, eq. f_bar_+);
+//   adj_faces     (per interface)  recomputes steps 3-7 and pulls lambda' back through the
+//                                  flux (steps 8-9), the interface relaxation (step 7,
+//                                  eq. original_f), the interface moments (step 6) and the NEQ
+//                                  wall condition (step 5, eq. NEQ), down to the adjoint of
+//                                  the step-4 values and of the interface acceleration;
+//   adj_cells     (per cell)       transposes the reconstruction (steps 3-4, eq. gradient)
+//                                  and the ghost extrapolation (step 2), then pulls the
+//                                  adjoint of fbar+ back through step 1 and the cell moments
+//                                  to g~^n and G.
+// Every output element is a gather written by one thread (no atomics), so the sweep is
+// bitwise reproducible. Arithmetic in the storage type of the handle (float or double).
+//
+// Interfaces: normal to x, (i, j) with i in [0, nx], j in [0, ny), between cells (i-1, j)
+// and (i, j), index i + (nx+1) j; normal to y, (i, j) with i in [0, nx), j in [0, ny],
+// between (i, j-1) and (i, j), index i + nx j. The forward step evaluates interface 0 and
+// interface n of a periodic axis separately (equal values): the first feeds cell 0, the
+// second cell n-1, and so they are two interfaces here as well.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/dugks.h"
+#include "dugks_internal.h"
+#include "handle.h"
+
+namespace dugks {
+
+namespace {
+
+constexpr int Q = 9;
+using L9 = Lat<9>;
+
+template <class T>
+struct AdjParams {
+    int n[2];                // nx, ny
+    int per[2];              // periodic along x / y
+    int64_t px, dstride;     // layout of the stored state (row pitch, direction stride)
+    int bc[4];               // DUGKS_BC_* of the faces -x, +x, -y, +y
+    T mw[4][2];              // wall momentum rho0 u_w / c of a velocity condition
+    T drw[4];                // rho_a - rho0 = p_w / RT of a pressure condition
+    T rho0, inv_rho0, dmw;   // dmw = d m_w / d u_w = rho0 / c
+    T b1, c1, b7, c7, kappa, two_kappa, wcell, wface;
+    T g[2];                  // uniform acceleration
+    const float *field;      // [2][ncell] acceleration field or null
+    T ctc, cthc;             // cos(omega t_n) / c and cos(omega (t_n + h)) / c
+    const T *state;          // g~^n (padded layout)
+    T *phi;                  // [Q][ncell] fbar+ of the cells
+    T *mom;                  // [3][ncell] drho, m_x, m_y of the cells (m in units of c)
+    const T *lam1;           // lambda' [Q][ncell]
+    T *fb[2];                // adjoint of the step-4 values [Q][nface_d]
+    T *gb[2];                // adjoint of the interface acceleration Gh [2][nface_d]
+    T *lam0;                 // lambda [Q][ncell]
+    double *dG;              // [2][ncell] dL/dfield accumulator (null: not wanted)
+    double *dW;              // [2 (ny + nx)][2] dL/du_w accumulator per wall interface
+};
+
+template <class T>
+__device__ __forceinline__ int64_t ncell(const AdjParams<T> &a) {
+    return (int64_t)a.n[0] * a.n[1];
+}
+template <class T>
+__device__ __forceinline__ int64_t nface(const AdjParams<T> &a, int d) {
+    return d == 0 ? (int64_t)(a.n[0] + 1) * a.n[1] : (int64_t)a.n[0] * (a.n[1] + 1);
+}
+template <class T>
+__device__ __forceinline__ int64_t fidx(const AdjParams<T> &a, int d, int i, int j) {
+    return d == 0 ? i + (int64_t)(a.n[0] + 1) * j : i + (int64_t)a.n[0] * j;
+}
+
+// ---- step 2: extended positions -1 .. n along one axis ----
+// Cells that make up position x (reading R3: ghost = 2 f(0) - f(1) at a wall, the periodic
+// image otherwise) and their weights; returns the count.
+template <class T>
+__device__ __forceinline__ int ext_parts(int x, int n, int per, int c[2], T w[2]) {
+    if (x >= 0 && x < n) { c[0] = x; w[0] = T(1); return 1; }
+    if (per) { c[0] = x < 0 ? x + n : x - n; w[0] = T(1); return 1; }
+    c[0] = x < 0 ? 0 : n - 1;
+    c[1] = x < 0 ? 1 : n - 2;
+    w[0] = T(2);
+    w[1] = T(-1);
+    return 2;
+}
+// The transpose: positions that cell x contributes to and the weights (at most 3).
+template <class T>
+__device__ __forceinline__ int ext_users(int x, int n, int per, int c[3], T w[3]) {
+    int k = 0;
+    c[k] = x; w[k++] = T(1);
+    if (per) {
+        if (x == n - 1) { c[k] = -1; w[k++] = T(1); }
+        if (x == 0) { c[k] = n; w[k++] = T(1); }
+    } else {
+        if (x == 0) { c[k] = -1; w[k++] = T(2); }
+        if (x == 1) { c[k] = -1; w[k++] = T(-1); }
+        if (x == n - 1) { c[k] = n; w[k++] = T(2); }
+        if (x == n - 2) { c[k] = n; w[k++] = T(-1); }
+    }
+    return k;
+}
+
+template <class T>
+__device__ __forceinline__ T phi_ext(const AdjParams<T> &a, int k, int x, int y) {
+    int cx[2], cy[2];
+    T wx[2], wy[2];
+    const int nxp = ext_parts<T>(x, a.n[0], a.per[0], cx, wx);
+    const int nyp = ext_parts<T>(y, a.n[1], a.per[1], cy, wy);
+    const T *ph = a.phi + k * ncell(a);
+    T v = T(0);
+    for (int p = 0; p < nxp; p++)
+        for (int q = 0; q < nyp; q++) v += wx[p] * wy[q] * ph[cx[p] + (int64_t)a.n[0] * cy[q]];
+    return v;
+}
+
+// ---- steps 3-4: step-4 value of velocity k at interface (d, i, j) (eq. gradient with the
+// step-3 cross points): 1/2 (L + R) - kappa e_d (R - L) - kappa/4 e_t [(L+R)_{t+1} - (L+R)_{t-1}] ----
+template <class T>
+__device__ __forceinline__ T recon(const AdjParams<T> &a, int d, int i, int j, int k) {
+    const int ed = L9::e(k, d), et = L9::e(k, 1 - d);
+    const int lx = d == 0 ? i - 1 : i, ly = d == 1 ? j - 1 : j;
+    const T l = phi_ext(a, k, lx, ly), r = phi_ext(a, k, i, j);
+    T v = T(0.5) * (l + r) - a.kappa * (T)ed * (r - l);
+    if (et) {
+        const int tx = d == 0 ? 0 : 1, ty = d == 0 ? 1 : 0;
+        const T pp = phi_ext(a, k, lx + tx, ly + ty) + phi_ext(a, k, i + tx, j + ty);
+        const T pm = phi_ext(a, k, lx - tx, ly - ty) + phi_ext(a, k, i - tx, j - ty);
+        v -= T(0.25) * a.kappa * (T)et * (pp - pm);
+    }
+    return v;
+}
+
+// Transpose of recon: d/d fbar+(x, y) of sum over interfaces of fb . F (velocity k).
+template <class T>
+__device__ __forceinline__ T recon_T(const AdjParams<T> &a, int k, int x, int y) {
+    const int ex = L9::e(k, 0), ey = L9::e(k, 1);
+    const int64_t n0 = nface(a, 0), n1 = nface(a, 1);
+    const T *f0 = a.fb[0] + k * n0, *f1 = a.fb[1] + k * n1;
+    auto fx = [&](int i, int j) -> T {
+        return (i < 0 || i > a.n[0] || j < 0 || j >= a.n[1]) ? T(0) : f0[fidx(a, 0, i, j)];
+    };
+    auto fy = [&](int i, int j) -> T {
+        return (i < 0 || i >= a.n[0] || j < 0 || j > a.n[1]) ? T(0) : f1[fidx(a, 1, i, j)];
+    };
+    const T h = T(0.5), q = T(0.25) * a.kappa;
+    // as L of x interface (x+1, y), R of (x, y); as a tangential neighbour of the x
+    // interfaces of rows y-1 (their t+1 pair) and y+1 (their t-1 pair)
+    T v = (h + a.kappa * ex) * fx(x + 1, y) + (h - a.kappa * ex) * fx(x, y);
+    if (ey) v += q * (T)ey * ((fx(x + 1, y + 1) + fx(x, y + 1)) - (fx(x + 1, y - 1) + fx(x, y - 1)));
+    // the same for the y interfaces, tangential along x
+    v += (h + a.kappa * ey) * fy(x, y + 1) + (h - a.kappa * ey) * fy(x, y);
+    if (ex) v += q * (T)ex * ((fy(x + 1, y + 1) + fy(x + 1, y)) - (fy(x - 1, y + 1) + fy(x - 1, y)));
+    return v;
+}
+
+// ---- equilibrium (eq. icfeq, deviation form, m = rho0 u / c) and its derivative ----
+template <class T>
+__device__ __forceinline__ T geq(const AdjParams<T> &a, int k, T dr, const T m[2]) {
+    const T em = (T)L9::e(k, 0) * m[0] + (T)L9::e(k, 1) * m[1];
+    const T mm = m[0] * m[0] + m[1] * m[1];
+    return L9::wt<T>(k) * (dr + T(3) * em + (T(4.5) * em * em - T(1.5) * mm) * a.inv_rho0);
+}
+template <class T>
+__device__ __forceinline__ void geq_dm(const AdjParams<T> &a, int k, const T m[2], T out[2]) {
+    const T e0 = (T)L9::e(k, 0), e1 = (T)L9::e(k, 1);
+    const T em = e0 * m[0] + e1 * m[1];
+    const T W = L9::wt<T>(k);
+    out[0] = W * (T(3) * e0 + (T(9) * em * e0 - T(3) * m[0]) * a.inv_rho0);
+    out[1] = W * (T(3) * e1 + (T(9) * em * e1 - T(3) * m[1]) * a.inv_rho0);
+}
+
+// Moments of a distribution with the force weight w (dt/2 at cells, h/2 at interfaces).
+template <class T>
+__device__ __forceinline__ void moments2(const AdjParams<T> &a, const T f[Q], const T Gh[2], T w, T &dr, T m[2]) {
+    dr = T(0);
+    m[0] = m[1] = T(0);
+    for (int k = 0; k < Q; k++) {
+        dr += f[k];
+        m[0] += (T)L9::e(k, 0) * f[k];
+        m[1] += (T)L9::e(k, 1) * f[k];
+    }
+    m[0] += a.rho0 * Gh[0] * w;
+    m[1] += a.rho0 * Gh[1] * w;
+}
+
+// Relaxation P_k = f_k + b (geq_k - f_k) + c S_k with S_k = 3 (Gh.e_k - Gh.m/rho0) f_eq,k
+// (steps 1 and 7). Given weights wk = dL/dP_k, adds dL/d(drho), dL/dm and dL/dGh through
+// the moment dependence (the direct part (1 - b) wk is left to the caller).
+template <class T>
+__device__ __forceinline__ void relax_T(const AdjParams<T> &a, const T wk[Q], T dr, const T m[2], const T Gh[2],
+                                        T b, T c, T &bdr, T bm[2], T bG[2]) {
+    const T gm = (Gh[0] * m[0] + Gh[1] * m[1]) * a.inv_rho0;
+    for (int k = 0; k < Q; k++) {
+        const T w = wk[k];
+        if (w == T(0)) continue;
+        const T e0 = (T)L9::e(k, 0), e1 = (T)L9::e(k, 1);
+        const T W = L9::wt<T>(k);
+        const T s = T(3) * (Gh[0] * e0 + Gh[1] * e1 - gm);
+        const T feq = W * a.rho0 + geq(a, k, dr, m);
+        T dg[2];
+        geq_dm(a, k, m, dg);
+        const T coef = b + c * s;  // dP/dgeq
+        bdr += w * coef * W;
+        bm[0] += w * (coef * dg[0] - c * T(3) * Gh[0] * a.inv_rho0 * feq);
+        bm[1] += w * (coef * dg[1] - c * T(3) * Gh[1] * a.inv_rho0 * feq);
+        bG[0] += w * c * T(3) * (e0 - m[0] * a.inv_rho0) * feq;
+        bG[1] += w * c * T(3) * (e1 - m[1] * a.inv_rho0) * feq;
+    }
+}
+
+// ---- acceleration at cells and interfaces (reading R2) ----
+template <class T>
+__device__ __forceinline__ T field_at(const AdjParams<T> &a, int comp, int x, int y) {
+    return a.field ? (T)a.field[comp * ncell(a) + x + (int64_t)a.n[0] * y] : T(0);
+}
+template <class T>
+__device__ __forceinline__ void cell_Gh(const AdjParams<T> &a, int x, int y, T Gh[2]) {
+    for (int c = 0; c < 2; c++) Gh[c] = (a.g[c] + field_at(a, c, x, y)) * a.ctc;
+}
+// Cells whose field the interface at position pos along d averages: wrapped on a periodic
+// axis, clamped at a wall (the one boundary cell).
+template <class T>
+__device__ __forceinline__ void face_cells(const AdjParams<T> &a, int d, int pos, int &lo, int &hi) {
+    const int nd = a.n[d];
+    lo = pos - 1;
+    hi = pos;
+    if (a.per[d]) {
+        if (lo < 0) lo += nd;
+        if (hi >= nd) hi -= nd;
+    } else {
+        if (lo < 0) lo = 0;
+        if (hi >= nd) hi = nd - 1;
+    }
+}
+template <class T>
+__device__ __forceinline__ void face_Gh(const AdjParams<T> &a, int d, int i, int j, T Gh[2]) {
+    int lo, hi;
+    face_cells(a, d, d == 0 ? i : j, lo, hi);
+    const int lx = d == 0 ? lo : i, ly = d == 1 ? lo : j, hx = d == 0 ? hi : i, hy = d == 1 ? hi : j;
+    for (int c = 0; c < 2; c++)
+        Gh[c] = (a.g[c] + T(0.5) * (field_at(a, c, lx, ly) + field_at(a, c, hx, hy))) * a.cthc;
+}
+
+// ---- forward state of one interface (steps 3-6) ----
+template <class T>
+struct FaceState {
+    T F[Q];                // step-4 values, incoming velocities replaced at a wall (step 5)
+    T dr, m[2], Gh[2];     // step-6 moments and the interface acceleration
+    int wall, side;
+    T drc, mc[2];          // moments at x_c (wall only)
+    T ma[2];               // m_a of step 5 (wall only)
+};
+
+template <class T>
+__device__ __forceinline__ void face_forward(const AdjParams<T> &a, int d, int i, int j, FaceState<T> &s) {
+    for (int k = 0; k < Q; k++) s.F[k] = recon(a, d, i, j, k);
+    const int pos = d == 0 ? i : j;
+    s.wall = !a.per[d] && (pos == 0 || pos == a.n[d]);
+    s.side = pos == 0 ? 0 : 1;
+    face_Gh(a, d, i, j, s.Gh);
+    if (s.wall) {
+        // x_c: the boundary cell's opposite interface (reading R4)
+        const int sh = s.side == 0 ? 1 : -1;
+        const int ci = d == 0 ? i + sh : i, cj = d == 1 ? j + sh : j;
+        T Fc[Q], Ghc[2];
+        for (int k = 0; k < Q; k++) Fc[k] = recon(a, d, ci, cj, k);
+        face_Gh(a, d, ci, cj, Ghc);
+        moments2(a, Fc, Ghc, a.wface, s.drc, s.mc);
+        const int wid = 2 * d + s.side;
+        const bool vel = a.bc[wid] == DUGKS_BC_NEQ_VELOCITY;
+        const T dra = vel ? s.drc : a.drw[wid];
+        s.ma[0] = vel ? a.mw[wid][0] : s.mc[0];
+        s.ma[1] = vel ? a.mw[wid][1] : s.mc[1];
+        const int sgn = s.side == 0 ? -1 : 1;
+        for (int k = 0; k < Q; k++)
+            if (sgn * L9::e(k, d) < 0) s.F[k] = geq(a, k, dra, s.ma) + Fc[k] - geq(a, k, s.drc, s.mc);
+    }
+    moments2(a, s.F, s.Gh, a.wface, s.dr, s.m);
+}
+
+// Adjoint of steps 5-9 at interface (d, i, j) for lambda'. Fb: dL/d(step-4 values), zero
+// for the velocities a wall replaces; Gb: dL/dGh of the interface. At a wall also what
+// flows to the step-4 values and Gh of x_c (Fcb, Gcb) and to the wall velocity (Wb).
+template <class T>
+__device__ __forceinline__ void face_adjoint(const AdjParams<T> &a, int d, int i, int j, T Fb[Q], T Gb[2],
+                                             T Fcb[Q], T Gcb[2], T Wb[2], int &wall) {
+    FaceState<T> s;
+    face_forward(a, d, i, j, s);
+    wall = s.wall;
+    const int64_t nc = ncell(a);
+    const int pos = d == 0 ? i : j, nd = a.n[d];
+    // steps 8-9: velocity k of this interface enters the update of its low cell with
+    // -2 kappa e_d and of its high cell with +2 kappa e_d
+    const bool haslo = pos > 0, hashi = pos < nd;
+    const int plo = pos > 0 ? pos - 1 : nd - 1, phi_c = pos < nd ? pos : 0;
+    const int64_t clo = d == 0 ? plo + (int64_t)a.n[0] * j : i + (int64_t)a.n[0] * plo;
+    const int64_t chi = d == 0 ? phi_c + (int64_t)a.n[0] * j : i + (int64_t)a.n[0] * phi_c;
+    T fbar[Q];
+    for (int k = 0; k < Q; k++) {
+        const int ed = L9::e(k, d);
+        T v = T(0);
+        if (ed) {
+            if (haslo) v -= a.lam1[k * nc + clo];
+            if (hashi) v += a.lam1[k * nc + chi];
+        }
+        fbar[k] = a.two_kappa * (T)ed * v;
+    }
+    // step 7 (eq. original_f) at the step-6 moments, then step 6
+    T bdr = T(0), bm[2] = {T(0), T(0)};
+    Gb[0] = Gb[1] = T(0);
+    relax_T(a, fbar, s.dr, s.m, s.Gh, a.b7, a.c7, bdr, bm, Gb);
+    Gb[0] += a.rho0 * a.wface * bm[0];
+    Gb[1] += a.rho0 * a.wface * bm[1];
+    for (int k = 0; k < Q; k++)
+        Fb[k] = (T(1) - a.b7) * fbar[k] + bdr + (T)L9::e(k, 0) * bm[0] + (T)L9::e(k, 1) * bm[1];
+    for (int k = 0; k < Q; k++) Fcb[k] = T(0);
+    Gcb[0] = Gcb[1] = T(0);
+    Wb[0] = Wb[1] = T(0);
+    if (!wall) return;
+    // step 5 (eq. NEQ): F_k = geq_k(drho_a, m_a) + Fc_k - geq_k(drho_c, m_c), incoming k.
+    // Velocity condition: drho_a = drho_c (the W_k terms cancel), m_a from u_w.
+    // Pressure condition: m_a = m_c (the m terms cancel), drho_a fixed.
+    const int wid = 2 * d + s.side;
+    const bool vel = a.bc[wid] == DUGKS_BC_NEQ_VELOCITY;
+    const int sgn = s.side == 0 ? -1 : 1;
+    T bdrc = T(0), bmc[2] = {T(0), T(0)};
+    for (int k = 0; k < Q; k++) {
+        if (!(sgn * L9::e(k, d) < 0)) continue;
+        const T w = Fb[k];
+        Fb[k] = T(0);
+        Fcb[k] += w;
+        if (vel) {
+            T da[2], dc[2];
+            geq_dm(a, k, s.ma, da);
+            geq_dm(a, k, s.mc, dc);
+            Wb[0] += w * da[0] * a.dmw;
+            Wb[1] += w * da[1] * a.dmw;
+            bmc[0] -= w * dc[0];
+            bmc[1] -= w * dc[1];
+        } else {
+            bdrc -= w * L9::wt<T>(k);
+        }
+    }
+    // step 6 at x_c
+    for (int k = 0; k < Q; k++) Fcb[k] += bdrc + (T)L9::e(k, 0) * bmc[0] + (T)L9::e(k, 1) * bmc[1];
+    Gcb[0] = a.rho0 * a.wface * bmc[0];
+    Gcb[1] = a.rho0 * a.wface * bmc[1];
+}
+
+// ---- kernels ----
+template <class T>
+__global__ void __launch_bounds__(256) adj_cells_fwd(const AdjParams<T> a) {
+    const int64_t nc = ncell(a);
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(c % a.n[0]), y = (int)(c / a.n[0]);
+        T g[Q], Gh[2], dr, m[2];
+        for (int k = 0; k < Q; k++) g[k] = a.state[k * a.dstride + (int64_t)y * a.px + x];
+        cell_Gh(a, x, y, Gh);
+        moments2(a, g, Gh, a.wcell, dr, m);
+        const T gm = (Gh[0] * m[0] + Gh[1] * m[1]) * a.inv_rho0;
+        for (int k = 0; k < Q; k++) {
+            const T q = geq(a, k, dr, m);
+            const T s = T(3) * (Gh[0] * (T)L9::e(k, 0) + Gh[1] * (T)L9::e(k, 1) - gm);
+            a.phi[k * nc + c] = g[k] + a.b1 * (q - g[k]) + a.c1 * s * (L9::wt<T>(k) * a.rho0 + q);
+        }
+        a.mom[c] = dr;
+        a.mom[nc + c] = m[0];
+        a.mom[2 * nc + c] = m[1];
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) adj_faces(const AdjParams<T> a) {
+    const int64_t n0 = nface(a, 0), ntot = n0 + nface(a, 1);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntot; t += (int64_t)gridDim.x * blockDim.x) {
+        const int d = t < n0 ? 0 : 1;
+        const int64_t f = d == 0 ? t : t - n0;
+        const int w = d == 0 ? a.n[0] + 1 : a.n[0];
+        const int i = (int)(f % w), j = (int)(f / w);
+        const int pos = d == 0 ? i : j, nd = a.n[d];
+        T Fb[Q], Gb[2], Fcb[Q], Gcb[2], Wb[2];
+        int wall;
+        face_adjoint(a, d, i, j, Fb, Gb, Fcb, Gcb, Wb, wall);
+        if (wall && a.dW && a.bc[2 * d + (pos == 0 ? 0 : 1)] == DUGKS_BC_NEQ_VELOCITY) {
+            const int64_t slot =
+                d == 0 ? (pos == 0 ? 0 : a.n[1]) + j : 2 * (int64_t)a.n[1] + (pos == 0 ? 0 : a.n[0]) + i;
+            a.dW[2 * slot] += (double)Wb[0];
+            a.dW[2 * slot + 1] += (double)Wb[1];
+        }
+        // this interface is x_c of the wall interface at 0 (pos == 1) and/or at nd (pos == nd - 1)
+        if (!a.per[d]) {
+            for (int sd = 0; sd < 2; sd++) {
+                if (pos != (sd == 0 ? 1 : nd - 1)) continue;
+                const int wp = sd == 0 ? 0 : nd;
+                T wFb[Q], wGb[2], wFcb[Q], wGcb[2], wWb[2];
+                int ww;
+                face_adjoint(a, d, d == 0 ? wp : i, d == 1 ? wp : j, wFb, wGb, wFcb, wGcb, wWb, ww);
+                for (int k = 0; k < Q; k++) Fb[k] += wFcb[k];
+                Gb[0] += wGcb[0];
+                Gb[1] += wGcb[1];
+            }
+        }
+        T *fb = a.fb[d], *gb = a.gb[d];
+        const int64_t nf = d == 0 ? n0 : ntot - n0;
+        for (int k = 0; k < Q; k++) fb[k * nf + f] = Fb[k];
+        gb[f] = Gb[0];
+        gb[nf + f] = Gb[1];
+    }
+}
+
+// dL/dGh summed over the interfaces whose acceleration averages cell (x, y), with the
+// averaging weights (1/2 per side; the clamped wall interface takes the cell twice).
+template <class T>
+__device__ __forceinline__ T face_G_T(const AdjParams<T> &a, int comp, int x, int y) {
+    T s = T(0);
+    for (int d = 0; d < 2; d++) {
+        const int pc = d == 0 ? x : y, nd = a.n[d];
+        int cand[4], nc = 0;
+        cand[nc++] = pc;
+        cand[nc++] = pc + 1;
+        if (a.per[d] && nd > 1) {  // the interfaces across the periodic seam
+            if (pc == nd - 1) cand[nc++] = 0;
+            if (pc == 0) cand[nc++] = nd;
+        }
+        const int64_t nf = nface(a, d);
+        for (int u = 0; u < nc; u++) {
+            int lo, hi;
+            face_cells(a, d, cand[u], lo, hi);
+            const T w = (lo == pc ? T(0.5) : T(0)) + (hi == pc ? T(0.5) : T(0));
+            if (w != T(0)) {
+                const int i = d == 0 ? cand[u] : x, j = d == 1 ? cand[u] : y;
+                s += w * a.gb[d][comp * nf + fidx(a, d, i, j)];
+            }
+        }
+    }
+    return s;
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) adj_cells(const AdjParams<T> a) {
+    const int64_t nc = ncell(a);
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(c % a.n[0]), y = (int)(c / a.n[0]);
+        int ux[3], uy[3];
+        T wx[3], wy[3];
+        const int nux = ext_users<T>(x, a.n[0], a.per[0], ux, wx);
+        const int nuy = ext_users<T>(y, a.n[1], a.per[1], uy, wy);
+        // adjoint of fbar+ of this cell: eq. f_tilde_+ (4/3 fbar+) and every interface
+        // value reconstructed from it, directly or through a ghost / periodic image
+        T pb[Q];
+        for (int k = 0; k < Q; k++) {
+            T v = T(4) / T(3) * a.lam1[k * nc + c];
+            for (int p = 0; p < nux; p++)
+                for (int q = 0; q < nuy; q++) v += wx[p] * wy[q] * recon_T(a, k, ux[p], uy[q]);
+            pb[k] = v;
+        }
+        // step 1 (eq. f_bar_+) and the cell moments (eq. macro_values)
+        const T dr = a.mom[c];
+        const T m[2] = {a.mom[nc + c], a.mom[2 * nc + c]};
+        T Gh[2];
+        cell_Gh(a, x, y, Gh);
+        T bdr = T(0), bm[2] = {T(0), T(0)}, bG[2] = {T(0), T(0)};
+        relax_T(a, pb, dr, m, Gh, a.b1, a.c1, bdr, bm, bG);
+        for (int k = 0; k < Q; k++)
+            a.lam0[k * nc + c] = -a.lam1[k * nc + c] / T(3) + (T(1) - a.b1) * pb[k] + bdr +
+                                 (T)L9::e(k, 0) * bm[0] + (T)L9::e(k, 1) * bm[1];
+        if (a.dG) {
+            for (int comp = 0; comp < 2; comp++) {
+                const T s = (bG[comp] + a.rho0 * a.wcell * bm[comp]) * a.ctc + face_G_T(a, comp, x, y) * a.cthc;
+                a.dG[comp * nc + c] += (double)s;
+            }
+        }
+    }
+}
+
+// Loss seed from dL/d(moments) [3][ncell] (p, u_x, u_y as dugks_moments returns them):
+// p = RT sum g~, u = c/rho0 sum e g~ + G cos(omega t) dt/2 (eq. macro_values).
+template <class T>
+__global__ void adj_seed(const AdjParams<T> a, const float *dLdm, T rt, T c_over_rho0, double gdt) {
+    const int64_t nc = ncell(a);
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        const T gp = (T)dLdm[c], gu0 = (T)dLdm[nc + c], gu1 = (T)dLdm[2 * nc + c];
+        for (int k = 0; k < Q; k++)
+            a.lam0[k * nc + c] = rt * gp + c_over_rho0 * ((T)L9::e(k, 0) * gu0 + (T)L9::e(k, 1) * gu1);
+        if (a.dG) {
+            a.dG[c] += (double)gu0 * gdt;
+            a.dG[nc + c] += (double)gu1 * gdt;
+        }
+    }
+}
+
+__global__ void adj_to_float(const double *src, float *dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+
+int blocks_for(int64_t n, int threads) {
+    const int64_t b = (n + threads - 1) / threads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 1 << 20));
+}
+
+// Work buffers carved from one allocation (element size es, 256-byte aligned pieces).
+struct AdjBufs {
+    void *phi, *mom, *fb[2], *gb[2], *lam[2];
+};
+
+size_t al256(size_t b) { return (b + 255) / 256 * 256; }
+
+size_t scratch_bytes(int64_t nx, int64_t ny, size_t es) {
+    const int64_t nc = nx * ny, n0 = (nx + 1) * ny, n1 = nx * (ny + 1);
+    return al256(es * Q * nc) + al256(es * 3 * nc) + al256(es * Q * n0) + al256(es * Q * n1) + al256(es * 2 * n0) +
+           al256(es * 2 * n1) + 2 * al256(es * Q * nc);
+}
+
+AdjBufs carve(void *base, int64_t nx, int64_t ny, size_t es) {
+    const int64_t nc = nx * ny, n0 = (nx + 1) * ny, n1 = nx * (ny + 1);
+    char *p = (char *)base;
+    AdjBufs B;
+    B.phi = p; p += al256(es * Q * nc);
+    B.mom = p; p += al256(es * 3 * nc);
+    B.fb[0] = p; p += al256(es * Q * n0);
+    B.fb[1] = p; p += al256(es * Q * n1);
+    B.gb[0] = p; p += al256(es * 2 * n0);
+    B.gb[1] = p; p += al256(es * 2 * n1);
+    B.lam[0] = p; p += al256(es * Q * nc);
+    B.lam[1] = p;
+    return B;
+}
+
+template <class T>
+AdjParams<T> base_params(const dugks_t h, const AdjBufs &B) {
+    AdjParams<T> a;
+    memset(&a, 0, sizeof a);
+    const StepParams p = handle_params(h);
+    a.n[0] = (int)h->nx;
+    a.n[1] = (int)h->ny;
+    a.per[0] = h->bcs.face[0].type == DUGKS_BC_PERIODIC;
+    a.per[1] = h->bcs.face[2].type == DUGKS_BC_PERIODIC;
+    a.px = p.px;
+    a.dstride = p.dstride;
+    for (int w = 0; w < 4; w++) {
+        a.bc[w] = p.bc[w];
+        a.mw[w][0] = (T)(p.bc_u[w][0] * p.rho0 * p.inv_c);
+        a.mw[w][1] = (T)(p.bc_u[w][1] * p.rho0 * p.inv_c);
+        a.drw[w] = (T)p.bc_drho[w];
+    }
+    a.rho0 = (T)p.rho0;
+    a.inv_rho0 = (T)(1.0 / p.rho0);
+    a.dmw = (T)(p.rho0 * p.inv_c);
+    a.b1 = (T)p.b1;
+    a.c1 = (T)p.c1;
+    a.b7 = (T)p.b7;
+    a.c7 = (T)p.c7;
+    a.kappa = (T)p.kappa;
+    a.two_kappa = (T)p.two_kappa;
+    a.wcell = (T)p.wcell;
+    a.wface = (T)p.wface;
+    a.g[0] = (T)p.g[0];
+    a.g[1] = (T)p.g[1];
+    a.field = p.field;
+    a.phi = (T *)B.phi;
+    a.mom = (T *)B.mom;
+    for (int d = 0; d < 2; d++) {
+        a.fb[d] = (T *)B.fb[d];
+        a.gb[d] = (T *)B.gb[d];
+    }
+    a.dG = h->tape.dG;
+    a.dW = h->tape.dW;
+    return a;
+}
+
+// One reverse step at the state g~^n held in `state` (t_n = tn): lambda' in lam1 -> lam0.
+template <class T>
+cudaError_t reverse_step(AdjParams<T> a, const dugks_t h, const void *state, double tn, const void *lam1,
+                         void *lam0) {
+    const double om = h->force.omega, inv_c = 1.0 / h->c;
+    a.ctc = (T)(cos(om * tn) * inv_c);
+    a.cthc = (T)(cos(om * (tn + 0.5 * h->dt)) * inv_c);
+    a.state = (const T *)state;
+    a.lam1 = (const T *)lam1;
+    a.lam0 = (T *)lam0;
+    const int64_t nc = h->ncell, nf = (h->nx + 1) * h->ny + h->nx * (h->ny + 1);
+    adj_cells_fwd<T><<<blocks_for(nc, 256), 256, 0, h->stream>>>(a);
+    adj_faces<T><<<blocks_for(nf, 128), 128, 0, h->stream>>>(a);
+    adj_cells<T><<<blocks_for(nc, 128), 128, 0, h->stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <class T>
+int run_adjoint(dugks_t h, const float *dL_dmom, float *dL_dfield, double *dL_dwall, void *dL_dstate0) {
+    AdjointTape &t = h->tape;
+    const size_t es = sizeof(T);
+    const AdjBufs B = carve(t.scratch, h->nx, h->ny, es);
+    const int64_t nc = h->ncell;
+    const int64_t nwall = 2 * (h->nx + h->ny);
+    cudaStream_t st = h->stream;
+    cudaError_t e = cudaMemsetAsync(t.dG, 0, sizeof(double) * 2 * nc, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(t.dW, 0, sizeof(double) * 2 * nwall, st);
+    if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "adjoint: %s", cudaGetErrorString(e));
+    AdjParams<T> a = base_params<T>(h, B);
+    {  // seed at the end of the rollout
+        const double tend = (double)(t.step0 + t.steps) * h->dt;
+        AdjParams<T> s = a;
+        s.lam0 = (T *)B.lam[0];
+        adj_seed<T><<<blocks_for(nc, 256), 256, 0, st>>>(s, dL_dmom, (T)h->rt, (T)(h->c / h->rho0),
+                                                          cos(h->force.omega * tend) * 0.5 * h->dt);
+        h->launches++;
+    }
+    int cur = 0;
+    const int64_t every = t.every;
+    const int64_t nseg = (t.steps + every - 1) / every;
+    std::vector<const void *> states((size_t)every);
+    for (int64_t sg = nseg - 1; sg >= 0; sg--) {
+        const int64_t start = sg * every;
+        const int64_t len = std::min<int64_t>(every, t.steps - start);
+        states[0] = t.ckpt[(size_t)sg];
+        // recompute the segment's states from its checkpoint
+        for (int64_t j = 1; j < len; j++) {
+            StepParams p = handle_params(h);
+            p.src = states[(size_t)j - 1];
+            p.dst = t.seg[(size_t)j - 1];
+            p.step_ctr = t.zero;
+            p.step_off = (int)(t.step0 + start + j - 1);
+            e = handle_launch_step(h, p);
+            if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "adjoint recompute: %s", cudaGetErrorString(e));
+            states[(size_t)j] = t.seg[(size_t)j - 1];
+            h->launches++;
+        }
+        for (int64_t j = len - 1; j >= 0; j--) {
+            const double tn = (double)(t.step0 + start + j) * h->dt;
+            e = reverse_step<T>(a, h, states[(size_t)j], tn, B.lam[cur], B.lam[cur ^ 1]);
+            if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "adjoint step: %s", cudaGetErrorString(e));
+            h->launches += 3;
+            cur ^= 1;
+        }
+    }
+    if (dL_dfield) {
+        adj_to_float<<<blocks_for(2 * nc, 256), 256, 0, st>>>(t.dG, dL_dfield, 2 * nc);
+        h->launches++;
+    }
+    if (dL_dstate0) {
+        e = cudaMemcpyAsync(dL_dstate0, B.lam[cur], es * Q * nc, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "adjoint: %s", cudaGetErrorString(e));
+    }
+    std::vector<double> w((size_t)(2 * nwall));
+    if (dL_dwall) e = cudaMemcpyAsync(w.data(), t.dW, sizeof(double) * 2 * nwall, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "adjoint: %s", cudaGetErrorString(e));
+    if (dL_dwall) {
+        // wall interface slots: -x (ny), +x (ny), -y (nx), +y (nx); fixed summation order
+        for (int i = 0; i < 18; i++) dL_dwall[i] = 0.0;
+        const int64_t first[4] = {0, h->ny, 2 * h->ny, 2 * h->ny + h->nx};
+        const int64_t count[4] = {h->ny, h->ny, h->nx, h->nx};
+        for (int f = 0; f < 4; f++) {
+            if (h->bcs.face[f].type != DUGKS_BC_NEQ_VELOCITY) continue;
+            for (int64_t s = 0; s < count[f]; s++) {
+                dL_dwall[3 * f + 0] += w[(size_t)(2 * (first[f] + s))];
+                dL_dwall[3 * f + 1] += w[(size_t)(2 * (first[f] + s) + 1)];
+            }
+        }
+    }
+    return DUGKS_OK;
+}
+
+}  // namespace
+
+void adjoint_release(dugks_t h) {
+    AdjointTape &t = h->tape;
+    for (void *p : t.ckpt) cudaFree(p);
+    for (void *p : t.seg) cudaFree(p);
+    t.ckpt.clear();
+    t.seg.clear();
+    cudaFree(t.scratch);
+    cudaFree(t.dG);
+    cudaFree(t.dW);
+    cudaFree(t.zero);
+    t.scratch = nullptr;
+    t.dG = t.dW = nullptr;
+    t.zero = nullptr;
+    t.steps = 0;
+}
+
+}  // namespace dugks
+
+using namespace dugks;
+
+static int check_adjoint_support(dugks_t h) {
+    if (h->q != DUGKS_D2Q9 || h->dim != 2)
+        return handle_fail(h, DUGKS_E_UNSUPPORTED, "record/adjoint: built for D2Q9 only");
+    if (h->store != DUGKS_STORE_F32 && h->store != DUGKS_STORE_F64)
+        return handle_fail(h, DUGKS_E_UNSUPPORTED, "record/adjoint: F32 or F64 storage only");
+    return DUGKS_OK;
+}
+
+extern "C" int dugks_record(dugks_t h, int64_t nsteps, int32_t every) {
+    if (!h) return DUGKS_E_INVAL;
+    if (nsteps < 1 || every < 1) return handle_fail(h, DUGKS_E_INVAL, "record: nsteps and every must be >= 1");
+    int rc = check_adjoint_support(h);
+    if (rc != DUGKS_OK) return rc;
+    if (h->step + nsteps > 2147483647LL) return handle_fail(h, DUGKS_E_INVAL, "record: step index past 2^31 - 1");
+    AdjointTape &t = h->tape;
+    t.steps = 0;
+    const int64_t nseg = (nsteps + every - 1) / every;
+    const int64_t nbuf = std::min<int64_t>(every, nsteps) - 1;
+    cudaError_t e = cudaSuccess;
+    auto resize = [&](std::vector<void *> &v, int64_t count) {
+        while ((int64_t)v.size() > count) {
+            cudaFree(v.back());
+            v.pop_back();
+        }
+        while (e == cudaSuccess && (int64_t)v.size() < count) {
+            void *p = nullptr;
+            e = cudaMalloc(&p, h->state_bytes);
+            if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, h->state_bytes, h->stream);  // zero padding columns
+            if (e == cudaSuccess) v.push_back(p);
+            else cudaFree(p);
+        }
+    };
+    resize(t.ckpt, nseg);
+    resize(t.seg, nbuf);
+    const size_t es = h->store == DUGKS_STORE_F64 ? 8 : 4;
+    if (e == cudaSuccess && !t.scratch) {
+        t.scratch_bytes = scratch_bytes(h->nx, h->ny, es);
+        e = cudaMalloc(&t.scratch, t.scratch_bytes);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&t.dG, sizeof(double) * 2 * h->ncell);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&t.dW, sizeof(double) * 4 * (h->nx + h->ny));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&t.zero, sizeof(long long));
+        if (e == cudaSuccess) e = cudaMemsetAsync(t.zero, 0, sizeof(long long), h->stream);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        adjoint_release(h);
+        return handle_fail(h, e == cudaErrorMemoryAllocation ? DUGKS_E_NOMEM : DUGKS_E_CUDA, "record: %s",
+                           cudaGetErrorString(e));
+    }
+    t.step0 = h->step;
+    t.every = every;
+    for (int64_t s = 0; s < nseg; s++) {
+        e = cudaMemcpyAsync(t.ckpt[(size_t)s], h->buf[h->cur], h->state_bytes, cudaMemcpyDeviceToDevice, h->stream);
+        if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "record: %s", cudaGetErrorString(e));
+        rc = dugks_step(h, std::min<int64_t>(every, nsteps - s * every));
+        if (rc != DUGKS_OK) return rc;
+    }
+    t.steps = nsteps;
+    return DUGKS_OK;
+}
+
+extern "C" int dugks_adjoint(dugks_t h, const float *dL_dmom, float *dL_dfield, double *dL_dwall,
+                             void *dL_dstate0) {
+    if (!h || !dL_dmom) return DUGKS_E_INVAL;
+    int rc = check_adjoint_support(h);
+    if (rc != DUGKS_OK) return rc;
+    if (h->tape.steps < 1) return handle_fail(h, DUGKS_E_INVAL, "adjoint: no recorded rollout (call dugks_record)");
+    return h->store == DUGKS_STORE_F64 ? run_adjoint<double>(h, dL_dmom, dL_dfield, dL_dwall, dL_dstate0)
+                                       : run_adjoint<float>(h, dL_dmom, dL_dfield, dL_dwall, dL_dstate0);
+}

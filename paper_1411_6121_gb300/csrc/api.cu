@@ -16,37 +16,9 @@
 
 #include "../../include/dugks.h"
 #include "dugks_internal.h"
+#include "handle.h"
 
 using namespace dugks;
-
-struct dugks_s {
-    int dim, q, store;
-    int64_t nx, ny, nz, px, ncell;
-    double dx, nu, dt, rt, rho0, c, tau;
-    dugks_force force;
-    dugks_boundaries bcs;
-    cudaStream_t stream;
-    int use_graph, tile_x, tile_y;
-    int kernel;            // 0: throughput kernel where built, 1: reference kernel
-    int ry3d;              // CTA rows of the 3D throughput kernel
-    int own_stream;
-    size_t esize;          // bytes per stored element
-    size_t state_bytes;    // padded device bytes of one buffer
-    void *buf[2];
-    int cur;               // index of the buffer that holds the current state
-    long long *d_step;     // device step counter
-    int64_t step;          // host mirror of the step counter
-    double *d_uprev;       // [dim][ncell] velocity at the previous residual
-    int have_prev;
-    double *d_partials;
-    int res_blocks;
-    double *d_res;         // 8 doubles
-    float *d_mom;          // moments staging for host outputs (allocated on first use)
-    double *h_res;         // pinned 8 doubles
-    int64_t launches;
-    std::map<std::pair<int64_t, int>, cudaGraphExec_t> graphs;
-    std::string err;
-};
 
 static thread_local std::string g_create_error;
 
@@ -54,7 +26,7 @@ namespace dugks {
 void set_null_handle_error(const char *msg) { g_create_error = msg; }
 }  // namespace dugks
 
-static int fail(dugks_t h, int code, const char *fmt, ...) {
+int dugks::handle_fail(dugks_t h, int code, const char *fmt, ...) {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
@@ -69,11 +41,11 @@ static int fail(dugks_t h, int code, const char *fmt, ...) {
     do {                                                                                          \
         cudaError_t e_ = (call);                                                                  \
         if (e_ != cudaSuccess)                                                                    \
-            return fail((h), DUGKS_E_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+            return handle_fail((h), DUGKS_E_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
                         __LINE__);                                                                \
     } while (0)
 
-static StepParams make_params(const dugks_t h) {
+StepParams dugks::handle_params(const dugks_t h) {
     StepParams p;
     memset(&p, 0, sizeof p);
     p.nx = (int)h->nx;
@@ -114,7 +86,7 @@ static StepParams make_params(const dugks_t h) {
     return p;
 }
 
-static cudaError_t launch_one_step(dugks_t h, StepParams &p) {
+cudaError_t dugks::handle_launch_step(dugks_t h, StepParams &p) {
     if (h->kernel == 0 && h->q == 19 && h->store != DUGKS_STORE_F64)
         return launch_step3d_q19(p, h->store, h->ry3d, h->stream);
     switch (h->q) {
@@ -144,36 +116,36 @@ const char *dugks_last_error(dugks_t h) { return h ? h->err.c_str() : g_create_e
 
 int dugks_create(const dugks_mesh *mesh, int32_t lattice, double nu, double dt, const dugks_force *force,
                  const dugks_boundaries *bcs, const dugks_opts *opts, dugks_t *out) {
-    if (!out) return fail(NULL, DUGKS_E_INVAL, "out is NULL");
+    if (!out) return handle_fail(NULL, DUGKS_E_INVAL, "out is NULL");
     *out = NULL;
-    if (!mesh || !force || !bcs) return fail(NULL, DUGKS_E_INVAL, "mesh, force and bcs are required");
+    if (!mesh || !force || !bcs) return handle_fail(NULL, DUGKS_E_INVAL, "mesh, force and bcs are required");
     dugks_opts o;
     dugks_opts_default(&o);
     if (opts) o = *opts;
     const int dim = mesh->dim;
-    if (!(dim == 2 || dim == 3)) return fail(NULL, DUGKS_E_INVAL, "dim must be 2 or 3");
-    if (dim == 2 && lattice != DUGKS_D2Q9) return fail(NULL, DUGKS_E_UNSUPPORTED, "2D needs DUGKS_D2Q9");
+    if (!(dim == 2 || dim == 3)) return handle_fail(NULL, DUGKS_E_INVAL, "dim must be 2 or 3");
+    if (dim == 2 && lattice != DUGKS_D2Q9) return handle_fail(NULL, DUGKS_E_UNSUPPORTED, "2D needs DUGKS_D2Q9");
     if (dim == 3 && lattice != DUGKS_D3Q19 && lattice != DUGKS_D3Q27)
-        return fail(NULL, DUGKS_E_UNSUPPORTED, "3D needs DUGKS_D3Q19 or DUGKS_D3Q27");
+        return handle_fail(NULL, DUGKS_E_UNSUPPORTED, "3D needs DUGKS_D3Q19 or DUGKS_D3Q27");
     if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || (dim == 2 && mesh->nz != 1))
-        return fail(NULL, DUGKS_E_INVAL, "bad mesh extents");
+        return handle_fail(NULL, DUGKS_E_INVAL, "bad mesh extents");
     if (mesh->nx > (1 << 30) || mesh->ny > (1 << 30) || mesh->nz > (1 << 30))
-        return fail(NULL, DUGKS_E_INVAL, "mesh extent too large");
+        return handle_fail(NULL, DUGKS_E_INVAL, "mesh extent too large");
     if (!(mesh->dx > 0) || !(nu > 0) || !(dt > 0) || !(o.rt > 0) || !(o.rho0 > 0))
-        return fail(NULL, DUGKS_E_INVAL, "dx, nu, dt, RT and rho0 must be positive");
-    if (o.store < 0 || o.store > 3) return fail(NULL, DUGKS_E_INVAL, "bad storage type");
-    if (o.kernel < 0 || o.kernel > 1) return fail(NULL, DUGKS_E_INVAL, "bad kernel selector");
+        return handle_fail(NULL, DUGKS_E_INVAL, "dx, nu, dt, RT and rho0 must be positive");
+    if (o.store < 0 || o.store > 3) return handle_fail(NULL, DUGKS_E_INVAL, "bad storage type");
+    if (o.kernel < 0 || o.kernel > 1) return handle_fail(NULL, DUGKS_E_INVAL, "bad kernel selector");
     const double c = sqrt(3.0 * o.rt);
     if (dt > mesh->dx / c * (1.0 + 1e-12))
-        return fail(NULL, DUGKS_E_CFL, "dt = %g exceeds dx/sqrt(3RT) = %g (CFL number > 1)", dt, mesh->dx / c);
+        return handle_fail(NULL, DUGKS_E_CFL, "dt = %g exceeds dx/sqrt(3RT) = %g (CFL number > 1)", dt, mesh->dx / c);
     const int64_t n[3] = {mesh->nx, mesh->ny, mesh->nz};
     for (int d = 0; d < 3; d++) {
         const int lo = bcs->face[2 * d].type, hi = bcs->face[2 * d + 1].type;
         if (d >= dim) continue;
-        if (lo < 0 || lo > 2 || hi < 0 || hi > 2) return fail(NULL, DUGKS_E_INVAL, "bad boundary type");
+        if (lo < 0 || lo > 2 || hi < 0 || hi > 2) return handle_fail(NULL, DUGKS_E_INVAL, "bad boundary type");
         if ((lo == DUGKS_BC_PERIODIC) != (hi == DUGKS_BC_PERIODIC))
-            return fail(NULL, DUGKS_E_INVAL, "periodic faces must be paired (axis %d)", d);
-        if (lo != DUGKS_BC_PERIODIC && n[d] < 2) return fail(NULL, DUGKS_E_INVAL, "a wall axis needs >= 2 cells");
+            return handle_fail(NULL, DUGKS_E_INVAL, "periodic faces must be paired (axis %d)", d);
+        if (lo != DUGKS_BC_PERIODIC && n[d] < 2) return handle_fail(NULL, DUGKS_E_INVAL, "a wall axis needs >= 2 cells");
     }
     // tile of the reference kernel (tile_x x tile_y cells), or, for the D3Q19 throughput
     // kernel, tile_y = rows of its 32 x tile_y thread block
@@ -182,7 +154,7 @@ int dugks_create(const dugks_mesh *mesh, int32_t lattice, double nu, double dt, 
     int ry3d = 8;
     if (thr3d) {
         if (ty != 0) ry3d = ty;
-        if (!(ry3d == 8 || ry3d == 10)) return fail(NULL, DUGKS_E_UNSUPPORTED, "3D kernel rows %d not built", ry3d);
+        if (!(ry3d == 8 || ry3d == 10)) return handle_fail(NULL, DUGKS_E_UNSUPPORTED, "3D kernel rows %d not built", ry3d);
         tx = 32;
         ty = 8;
     } else {
@@ -191,11 +163,11 @@ int dugks_create(const dugks_mesh *mesh, int32_t lattice, double nu, double dt, 
             ty = 8;
         }
         if (!((tx == 32 && ty == 8) || (tx == 16 && ty == 8)))
-            return fail(NULL, DUGKS_E_UNSUPPORTED, "tile %dx%d not built", tx, ty);
+            return handle_fail(NULL, DUGKS_E_UNSUPPORTED, "tile %dx%d not built", tx, ty);
     }
 
     dugks_t h = new (std::nothrow) dugks_s();
-    if (!h) return fail(NULL, DUGKS_E_NOMEM, "host allocation failed");
+    if (!h) return handle_fail(NULL, DUGKS_E_NOMEM, "host allocation failed");
     h->dim = dim;
     h->q = lattice;
     h->store = o.store;
@@ -218,7 +190,7 @@ int dugks_create(const dugks_mesh *mesh, int32_t lattice, double nu, double dt, 
         if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
             cudaGetLastError();
             delete h;
-            return fail(NULL, DUGKS_E_CUDA, "stream creation failed");
+            return handle_fail(NULL, DUGKS_E_CUDA, "stream creation failed");
         }
         h->own_stream = 1;
     }
@@ -245,7 +217,7 @@ int dugks_create(const dugks_mesh *mesh, int32_t lattice, double nu, double dt, 
 #undef ALLOC
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_res, sizeof(double) * 8);
     if (e != cudaSuccess) {
-        rc = fail(NULL, e == cudaErrorMemoryAllocation ? DUGKS_E_NOMEM : DUGKS_E_CUDA, "allocation: %s",
+        rc = handle_fail(NULL, e == cudaErrorMemoryAllocation ? DUGKS_E_NOMEM : DUGKS_E_CUDA, "allocation: %s",
                   cudaGetErrorString(e));
         cudaGetLastError();
         dugks_destroy(h);
@@ -256,7 +228,7 @@ int dugks_create(const dugks_mesh *mesh, int32_t lattice, double nu, double dt, 
         (e = cudaMemsetAsync(h->buf[1], 0, h->state_bytes, h->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(h->d_step, 0, sizeof(long long), h->stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
-        rc = fail(NULL, DUGKS_E_CUDA, "initial clear: %s", cudaGetErrorString(e));
+        rc = handle_fail(NULL, DUGKS_E_CUDA, "initial clear: %s", cudaGetErrorString(e));
         dugks_destroy(h);
         return rc;
     }
@@ -267,6 +239,7 @@ int dugks_create(const dugks_mesh *mesh, int32_t lattice, double nu, double dt, 
 void dugks_destroy(dugks_t h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
+    adjoint_release(h);
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
     cudaFree(h->buf[0]);
     cudaFree(h->buf[1]);
@@ -291,12 +264,12 @@ int dugks_init(dugks_t h, const double *pres, const double *vel) {
         cudaError_t e = cudaMalloc((void **)&du, sizeof(double) * h->dim * h->ncell);
         if (e != cudaSuccess) {
             cudaFree(dp);
-            return fail(h, DUGKS_E_NOMEM, "init: %s", cudaGetErrorString(e));
+            return handle_fail(h, DUGKS_E_NOMEM, "init: %s", cudaGetErrorString(e));
         }
         CUDA_TRY(h, cudaMemcpyAsync(du, vel, sizeof(double) * h->dim * h->ncell, cudaMemcpyHostToDevice, h->stream));
     }
     h->cur = 0;
-    StepParams p = make_params(h);
+    StepParams p = handle_params(h);
     p.dst = h->buf[0];
     cudaError_t e = launch_init(h->q, h->store, p, dp, du, h->rt, h->stream);
     h->launches++;
@@ -304,7 +277,7 @@ int dugks_init(dugks_t h, const double *pres, const double *vel) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(dp);
     cudaFree(du);
-    if (e != cudaSuccess) return fail(h, DUGKS_E_CUDA, "init: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "init: %s", cudaGetErrorString(e));
     h->step = 0;
     h->have_prev = 0;
     return DUGKS_OK;
@@ -312,19 +285,19 @@ int dugks_init(dugks_t h, const double *pres, const double *vel) {
 
 // Enqueue n steps starting from the current buffer (no graph).
 static int enqueue_steps(dugks_t h, int64_t n) {
-    StepParams p = make_params(h);
+    StepParams p = handle_params(h);
     int cur = h->cur;
     for (int64_t i = 0; i < n; i++) {
         p.src = h->buf[cur];
         p.dst = h->buf[cur ^ 1];
         p.step_off = (int)i;
-        cudaError_t e = launch_one_step(h, p);
-        if (e != cudaSuccess) return fail(h, DUGKS_E_CUDA, "step launch: %s", cudaGetErrorString(e));
+        cudaError_t e = handle_launch_step(h, p);
+        if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "step launch: %s", cudaGetErrorString(e));
         cur ^= 1;
     }
     if (h->force.omega != 0.0) {  // the device clock only feeds G(t)
         cudaError_t e = launch_advance(h->d_step, (long long)n, h->stream);
-        if (e != cudaSuccess) return fail(h, DUGKS_E_CUDA, "advance: %s", cudaGetErrorString(e));
+        if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "advance: %s", cudaGetErrorString(e));
     }
     return DUGKS_OK;
 }
@@ -345,11 +318,11 @@ int dugks_step(dugks_t h, int64_t n) {
                 int rc = enqueue_steps(h, m);
                 cudaError_t e = cudaStreamEndCapture(h->stream, &g);
                 if (rc != DUGKS_OK) return rc;
-                if (e != cudaSuccess) return fail(h, DUGKS_E_CUDA, "capture: %s", cudaGetErrorString(e));
+                if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "capture: %s", cudaGetErrorString(e));
                 cudaGraphExec_t ge;
                 e = cudaGraphInstantiate(&ge, g, 0);
                 cudaGraphDestroy(g);
-                if (e != cudaSuccess) return fail(h, DUGKS_E_CUDA, "instantiate: %s", cudaGetErrorString(e));
+                if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "instantiate: %s", cudaGetErrorString(e));
                 it = h->graphs.emplace(key, ge).first;
             }
             CUDA_TRY(h, cudaGraphLaunch(it->second, h->stream));
@@ -373,31 +346,31 @@ int dugks_moments(dugks_t h, float *out, int32_t out_is_device) {
         if (!h->d_mom) CUDA_TRY(h, cudaMalloc((void **)&h->d_mom, bytes));
         d = h->d_mom;
     }
-    StepParams p = make_params(h);
+    StepParams p = handle_params(h);
     cudaError_t e = launch_moments(h->q, h->store, p, h->step * h->dt, h->rt, d, h->stream);
     h->launches++;
     if (e == cudaSuccess && !out_is_device) e = cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return fail(h, DUGKS_E_CUDA, "moments: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "moments: %s", cudaGetErrorString(e));
     return DUGKS_OK;
 }
 
 int dugks_residual(dugks_t h, double *out) {
     if (!h || !out) return DUGKS_E_INVAL;
-    StepParams p = make_params(h);
+    StepParams p = handle_params(h);
     cudaError_t e = launch_residual(h->q, h->store, p, h->step * h->dt, h->rt, h->d_uprev, h->have_prev,
                                     h->d_partials, h->res_blocks, h->d_res, h->stream);
     h->launches += 2;
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_res, h->d_res, sizeof(double) * 8, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return fail(h, DUGKS_E_CUDA, "residual: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "residual: %s", cudaGetErrorString(e));
     const double *s = h->h_res;
     out[0] = h->have_prev ? (s[1] > 0 ? sqrt(s[0]) / sqrt(s[1]) : (s[0] > 0 ? INFINITY : 0.0)) : INFINITY;
     out[1] = s[2];
     for (int a = 0; a < h->dim; a++) out[2 + a] = s[3 + a];
     h->have_prev = 1;
     for (int i = 0; i < 3 + h->dim; i++)
-        if (!isfinite(s[i])) return fail(h, DUGKS_E_UNSTABLE, "non-finite moments (slot %d)", i);
+        if (!isfinite(s[i])) return handle_fail(h, DUGKS_E_UNSTABLE, "non-finite moments (slot %d)", i);
     return DUGKS_OK;
 }
 
@@ -451,6 +424,17 @@ int dugks_set_force_field(dugks_t h, const float *field) {
     return DUGKS_OK;
 }
 
+int dugks_set_boundaries(dugks_t h, const dugks_boundaries *bcs) {
+    if (!h || !bcs) return DUGKS_E_INVAL;
+    for (int w = 0; w < 2 * h->dim; w++)
+        if (bcs->face[w].type != h->bcs.face[w].type)
+            return handle_fail(h, DUGKS_E_INVAL, "set_boundaries: face %d changes type", w);
+    h->bcs = *bcs;
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);  // parameters are baked into graphs
+    h->graphs.clear();
+    return DUGKS_OK;
+}
+
 int dugks_sync(dugks_t h, double timeout_s) {
     if (!h) return DUGKS_E_INVAL;
     struct timespec t0, t1;
@@ -458,10 +442,10 @@ int dugks_sync(dugks_t h, double timeout_s) {
     for (;;) {
         cudaError_t e = cudaStreamQuery(h->stream);
         if (e == cudaSuccess) return DUGKS_OK;
-        if (e != cudaErrorNotReady) return fail(h, DUGKS_E_CUDA, "sync: %s", cudaGetErrorString(e));
+        if (e != cudaErrorNotReady) return handle_fail(h, DUGKS_E_CUDA, "sync: %s", cudaGetErrorString(e));
         clock_gettime(CLOCK_MONOTONIC, &t1);
         const double el = (t1.tv_sec - t0.tv_sec) + 1e-9 * (t1.tv_nsec - t0.tv_nsec);
-        if (timeout_s > 0 && el > timeout_s) return fail(h, DUGKS_E_TIMEOUT, "sync: not done after %.3f s", el);
+        if (timeout_s > 0 && el > timeout_s) return handle_fail(h, DUGKS_E_TIMEOUT, "sync: not done after %.3f s", el);
         struct timespec ns = {0, 20000};
         nanosleep(&ns, NULL);
     }

@@ -30,6 +30,7 @@ EXPORTS = [
     "dugks_residual", "dugks_state_bytes", "dugks_get_state", "dugks_set_state",
     "dugks_get_clock", "dugks_set_clock", "dugks_set_force_field", "dugks_sync",
     "dugks_launch_count", "dugks_last_error", "dugks_destroy", "dugks_residual_static",
+    "dugks_set_boundaries", "dugks_record", "dugks_adjoint",
     "dugks_batch_create", "dugks_batch_init", "dugks_batch_step", "dugks_batch_moments", "dugks_batch_tune",
     "dugks_batch_sync", "dugks_batch_launch_count", "dugks_batch_last_error", "dugks_batch_destroy",
 ]
@@ -96,6 +97,9 @@ def load(path=None):
     lib.dugks_last_error.restype = C.c_char_p
     lib.dugks_destroy.argtypes = [P]
     lib.dugks_destroy.restype = None
+    lib.dugks_set_boundaries.argtypes = [P, C.POINTER(Boundaries)]
+    lib.dugks_record.argtypes = [P, I64, I32]
+    lib.dugks_adjoint.argtypes = [P, P, P, D, P]
     lib.dugks_residual_static.argtypes = [I32, I32, P, I64, I64, I64, C.c_double, C.c_double, D, P, P, I32, D, P]
     lib.dugks_batch_create.argtypes = [I32, C.POINTER(Mesh), D, C.c_double, C.POINTER(Force), C.POINTER(Boundaries),
                                        C.POINTER(Opts), C.POINTER(P)]
@@ -247,6 +251,37 @@ class Sim:
     def set_force_field(self, field):
         self._field = field
         _check(self.lib.dugks_set_force_field(self.h, None if field is None else C.c_void_p(field.data_ptr())), self.h)
+
+    def set_boundaries(self, bcs):
+        """Replace wall velocities / pressures (same face types as at creation)."""
+        b = make_bcs(bcs)
+        _check(self.lib.dugks_set_boundaries(self.h, C.byref(b)), self.h)
+        self.bcs = b
+
+    def record(self, nsteps, every):
+        """Run ``nsteps`` steps keeping a checkpoint every ``every`` steps (for ``adjoint``)."""
+        _check(self.lib.dugks_record(self.h, int(nsteps), int(every)), self.h)
+
+    def adjoint(self, dL_dmom, field_grad=True, state_grad=False):
+        """Reverse sweep of the recorded rollout. ``dL_dmom``: CUDA float32 tensor
+        [dim+1][ncell] (the gradient of the loss w.r.t. the final moments). Returns
+        ``(dL/dfield CUDA [2][ncell] float32 or None, dL/du_wall numpy [6][3],
+        dL/dstate0 CUDA [Q][ncell] or None)``."""
+        import torch
+        assert dL_dmom.is_cuda and dL_dmom.dtype == torch.float32 and dL_dmom.is_contiguous()
+        assert dL_dmom.numel() == (self.dim + 1) * self.ncell
+        dev = dL_dmom.device
+        dfield = torch.empty((self.dim, self.ncell), dtype=torch.float32, device=dev) if field_grad else None
+        dwall = np.zeros((6, 3), dtype=np.float64)
+        dstate = None
+        if state_grad:
+            dt = torch.float64 if self.store == STORE_F64 else torch.float32
+            dstate = torch.empty((self.q, self.ncell), dtype=dt, device=dev)
+        rc = self.lib.dugks_adjoint(self.h, C.c_void_p(dL_dmom.data_ptr()),
+                                    None if dfield is None else C.c_void_p(dfield.data_ptr()), _dp(dwall),
+                                    None if dstate is None else C.c_void_p(dstate.data_ptr()))
+        _check(rc, self.h)
+        return dfield, dwall, dstate
 
     def sync(self, timeout_s=0.0):
         _check(self.lib.dugks_sync(self.h, float(timeout_s)), self.h)
