@@ -256,6 +256,76 @@ def run_batched(torch, steps, warmup, dev):
             "note": "64 D2Q9 channels, one persistent launch per step replayed as a CUDA graph"}
 
 
+ADJ_STEPS, ADJ_EVERY = 2000, 100
+ADJ_BYTES = 132  # algorithmic bytes per adjoint cell update (FP32 D2Q9): 3 x 36 state/adjoint + 8 G + 16 dL/dG
+
+
+def run_adjoint(torch, dev, count=64):
+    """Differentiable form: for each of the 64 uneven channels (FP32), loss ||u(T) - u_target||^2
+    over T = 2000 steps with a checkpoint every 100 steps; gradient w.r.t. the per-cell
+    acceleration field through dugks_record + dugks_adjoint. Timed with CUDA events on the
+    handle's stream: the forward rollout with checkpoints, and the reverse sweep (segment
+    recompute + transposed steps)."""
+    import numpy as np
+    from paper_1411_6121_gb300 import dugks
+    from paper_1411_6121_gb300 import workloads as W
+    specs = W.batched_channels(64, seed=0x1411)[:count]
+    stream = torch.cuda.Stream(device=dev)
+    fwd_ms = bwd_ms = 0.0
+    cells_total = 0
+    launches = 0
+    largest = None
+    for i, sp in enumerate(specs):
+        nx, ny = sp["shape"]
+        n = nx * ny
+        fld = torch.tensor(W.force_field(sp["shape"], sp["g"][0], seed=1000 + i, rel=0.1), dtype=torch.float32,
+                           device=dev)
+        ut = torch.tensor(0.5 * W.random_state_fields(sp["shape"], seed=i, u_amp=0.05)[1].reshape(2, n),
+                          dtype=torch.float32, device=dev)
+        sim = dugks.Sim(shape=sp["shape"], q=9, nu=sp["nu"], dt=sp["dt"], g=sp["g"], bcs=sp["bcs"], field=fld,
+                        store=dugks.STORE_F32, stream=stream.cuda_stream)
+        sim.init()
+        if i == 0:  # warm-up of the code paths (graphs, allocations)
+            sim.record(ADJ_EVERY * 2, ADJ_EVERY)
+            sim.adjoint(torch.zeros((3, n), dtype=torch.float32, device=dev))
+            sim.init()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        l0 = sim.launch_count()
+        torch.cuda.synchronize(dev)
+        e[0].record(stream)
+        sim.record(ADJ_STEPS, ADJ_EVERY)
+        e[1].record(stream)
+        m = torch.empty((3, n), dtype=torch.float32, device=dev)
+        sim.moments(m)
+        seed = torch.zeros_like(m)
+        seed[1:] = 2.0 * (m[1:] - ut)
+        torch.cuda.synchronize(dev)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        sim.adjoint(seed)
+        e[2].record(stream)
+        torch.cuda.synchronize(dev)
+        f_ms, b_ms = e[0].elapsed_time(e[1]), e2.elapsed_time(e[2])
+        fwd_ms += f_ms
+        bwd_ms += b_ms
+        cells_total += n
+        launches += sim.launch_count() - l0
+        if largest is None or n > largest[0]:
+            largest = (n, b_ms, sp["shape"])
+        sim.close()
+    upd = cells_total * ADJ_STEPS
+    n_l, b_l, shape_l = largest
+    return {"value": upd / (bwd_ms * 1e-3) / 1e6, "unit": "MLUPS",
+            "forward_with_checkpoints_mlups": upd / (fwd_ms * 1e-3) / 1e6,
+            "forward_plus_adjoint_mlups": upd / ((fwd_ms + bwd_ms) * 1e-3) / 1e6,
+            "reverse_ms": bwd_ms, "forward_ms": fwd_ms, "instances": len(specs), "cells": cells_total,
+            "steps": ADJ_STEPS, "checkpoint_every": ADJ_EVERY, "dtype": "f32", "gpu_launches": launches,
+            "largest_instance": {"shape": list(shape_l), "adjoint_mlups": n_l * ADJ_STEPS / (b_l * 1e-3) / 1e6,
+                                 "bytes_per_cell_update": ADJ_BYTES},
+            "note": "reverse sweep = recompute of each 100-step segment from its checkpoint + 2000 "
+                    "transposed steps; loss ||u(T) - u_target||^2 w.r.t. the per-cell force field"}
+
+
 def cpu_baseline(seconds=12.0):
     """The FP64 oracle as it stands on a bounded sample of the same workload: a 40^3 cube
     at the same Reynolds number (same lid speed, nu scaled with the size), single thread."""
@@ -373,6 +443,11 @@ def main():
             extras["batched"] = run_batched(torch, max(50, args.steps), warmup, dev)
         except Exception as ex:
             extras["batched"] = {"error": str(ex)}
+    if not args.no_extras and rank == 0:
+        try:
+            extras["adjoint"] = run_adjoint(torch, dev)
+        except Exception as ex:
+            extras["adjoint"] = {"error": str(ex)}
     e2e = None
     if rank == 0 and not args.no_extras:
         sec, bi, bo = run_e2e(torch, max(3, min(10, args.steps // 20)), dev)
