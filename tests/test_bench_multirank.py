@@ -1,0 +1,53 @@
+"""Multi-rank logic of bench.py on CPU: two gloo ranks (one process each) agree on the
+slowest rank's step time and on the whole-job throughput, as the GPU ranks do over NCCL."""
+import os
+import socket
+
+import pytest
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    ws, r, _ = bench.dist_env()
+    ms = bench.max_over_ranks(torch, dist, 10.0 + 5.0 * rank, torch.device("cpu"))
+    out.put((r, ws, ms, bench.whole_job_mlups(ws, 1000000, ms)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_take_the_slowest_time():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [r[0] for r in res] == [0, 1]
+    for _, ws, ms, v in res:
+        assert ws == 2
+        assert ms == 15.0                      # max over ranks
+        assert v == pytest.approx(2 * 1e6 / 15e-3 / 1e6)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1"])
+    assert bench.main() == 0
+    assert capsys.readouterr().out == ""
