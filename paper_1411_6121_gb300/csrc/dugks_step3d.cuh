@@ -32,7 +32,7 @@
 
 namespace dugks {
 
-template <int Q, int RY>
+template <int Q, int RY, class S = float>
 struct Shape3 {
     static constexpr int RX = 32;
     static constexpr int NT = RX * RY;
@@ -44,7 +44,12 @@ struct Shape3 {
     static constexpr int FS = NF | 1;                 // y exchange: f at +y
     static constexpr int PLANE = RY * RX * CS;
     static constexpr int US = Q | 1;                  // u0 of a plane (own column), two planes
-    static constexpr size_t smem_floats = 3 * (size_t)PLANE + (size_t)NT * (BS + FS + 2 * US);
+    // FP32 storage: the next plane's state is staged in shared memory by cp.async while the
+    // current plane is computed (two buffers, [Q][NT] each: conflict-free per direction)
+    static constexpr size_t BASE_FLOATS = 3 * (size_t)PLANE + (size_t)NT * (BS + FS + 2 * US);
+    static constexpr bool STAGE = sizeof(S) == 4 && (BASE_FLOATS + 2 * (size_t)Q * NT) * 4 <= 227 * 1024;
+    static constexpr size_t STAGE_FLOATS = STAGE ? 2 * (size_t)Q * NT : 0;
+    static constexpr size_t smem_floats = BASE_FLOATS + STAGE_FLOATS;
     static constexpr size_t smem_bytes = smem_floats * sizeof(float);
 };
 
@@ -187,7 +192,7 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
 // planes of neighbouring tiles together, so the halo columns they share hit in L2.
 template <int Q, class S, int RY, bool FORCE>
 __global__ void __launch_bounds__(32 * RY, 1) fused_step3d(const __grid_constant__ StepParams p, int zchunk) {
-    using K = Shape3<Q, RY>;
+    using K = Shape3<Q, RY, S>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int z0 = blockIdx.z * zchunk;
     const int z1 = min(p.nz, z0 + zchunk);
@@ -197,7 +202,7 @@ __global__ void __launch_bounds__(32 * RY, 1) fused_step3d(const __grid_constant
 template <int Q, class S, int RY, bool FORCE>
 __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned char *smem_raw, int x0, int y0, int z0,
                                                int z1) {
-    using K = Shape3<Q, RY>;
+    using K = Shape3<Q, RY, S>;
     constexpr int NF = K::NF;
     constexpr int CS = K::CS;
     float *ring = reinterpret_cast<float *>(smem_raw);  // [3][RY][32][CS]: fbar+ then moments
@@ -265,9 +270,31 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
         }
     };
 
+    // ---- staging of plane pz's state (FP32 storage): one 4-byte cp.async per direction
+    //      into the buffer of pz's parity, completed by the cp.async.wait_group in
+    //      make_phi; each thread reads back only what it copied itself ----
+    float *stg = reinterpret_cast<float *>(smem_raw) + (K::smem_floats - K::STAGE_FLOATS);
+    const int tid = row * 32 + lane;
+    auto prefetch = [&](int pz) __attribute__((always_inline)) {
+        if constexpr (K::STAGE) {
+            if (load) {
+                const int64_t off = (int64_t)wrap_idx(pz, nz) * p.plane + (int64_t)cy * p.px + cx;
+                float *sb = stg + (pz & 1) * Q * K::NT + tid;
+#pragma unroll
+                for (int k = 0; k < Q; k++) {
+                    const unsigned sa = (unsigned)__cvta_generic_to_shared(sb + k * K::NT);
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src + k * p.dstride + off)
+                                 : "memory");
+                }
+            }
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+        }
+    };
+
     // ---- step 1 for the own column at plane pz into the ring; u0 = fbar+ + (fbar+ - f~)/3
-    //      (the cell's part of eq. f_tilde_+, applied in increment form) is returned ----
-    auto make_phi = [&](int pz, float *u0) __attribute__((always_inline)) {
+    //      (the cell's part of eq. f_tilde_+, applied in increment form) is returned.
+    //      staged: the state was prefetched into the staging buffer ----
+    auto make_phi = [&](int pz, float *u0, bool staged) __attribute__((always_inline)) {
         float *o = R(slot_of(pz), row, lane);
         if (!load) {
 #pragma unroll
@@ -277,8 +304,15 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
         const int gz = wrap_idx(pz, nz);
         const int64_t off = (int64_t)gz * p.plane + (int64_t)cy * p.px + cx;
         float g[Q];
+        if (K::STAGE && staged) {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            const float *sb = stg + (pz & 1) * Q * K::NT + tid;
 #pragma unroll
-        for (int k = 0; k < Q; k++) g[k] = (float)Store<S>::ld(src + k * p.dstride + off);
+            for (int k = 0; k < Q; k++) g[k] = sb[k * K::NT];
+        } else {
+#pragma unroll
+            for (int k = 0; k < Q; k++) g[k] = (float)Store<S>::ld(src + k * p.dstride + off);
+        }
         float Gh[3] = {0.0f, 0.0f, 0.0f}, drho, m[3];
         if (FORCE) {
             const int64_t c = (int64_t)cx + (int64_t)nx * ((int64_t)cy + (int64_t)ny * gz);
@@ -403,9 +437,12 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
     constexpr std::integral_constant<int, 2> AZ{};
 
     // ---------------- prologue: planes z0-1, z0, z0+1 ----------------
+    // plane z0+2 is made at the first iteration of the loop below, if there is one
+    const bool need_next0 = z0 + 1 < z1 && (perz || z0 + 2 < nz);
+    if (need_next0) prefetch(z0 + 2);
     for (int pz = z0 - 1; pz <= z0 + 1; pz++) {
         if (!perz && (pz < 0 || pz >= nz)) continue;
-        make_phi(pz, US(pz));  // (plane z0+1 overwrites the u0 of plane z0-1: same parity)
+        make_phi(pz, US(pz), false);  // (plane z0+1 overwrites the u0 of plane z0-1: same parity)
     }
     for (int pz = z0 - 1; pz <= z0 + 1; pz++) {
         if (!perz && (pz < 0 || pz >= nz)) continue;
@@ -441,7 +478,8 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
         if (kz > z0) {
             const int pn = kz + 1;
             if (perz || pn < nz) {
-                make_phi(pn, US(pn));
+                make_phi(pn, US(pn), true);  // prefetched at the previous iteration
+                if (kz + 1 < z1 && (perz || kz + 2 < nz)) prefetch(kz + 2);
                 ghosts_xy(pn);
             } else if (pn == nz) {
                 ghost_z(pn);

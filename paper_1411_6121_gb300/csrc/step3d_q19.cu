@@ -6,7 +6,7 @@ namespace dugks {
 
 template <int RY, class S, bool FORCE>
 static cudaError_t launch_ry(const StepParams &p, cudaStream_t stream) {
-    using K = Shape3<19, RY>;
+    using K = Shape3<19, RY, S>;
     static int configured_dev = -1;
     static int sms = 0;
     int dev = 0;
