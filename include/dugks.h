@@ -176,7 +176,7 @@ void dugks_destroy(dugks_t h);
  *
  * dugks_record runs nsteps steps from the current state, exactly as dugks_step does, and
  * keeps a device copy of the state every `every` steps (ceil(nsteps/every) state buffers plus
- * every-1 buffers for the reverse sweep, owned by the handle and reused by later calls). The
+ * `every` buffers for the reverse sweep, owned by the handle and reused by later calls). The
  * handle's clock advances by nsteps. A new record replaces the previous one.
  *
  * dugks_adjoint takes dL_dmom = dL/d(moments at the end of the recorded rollout), a DEVICE
@@ -191,10 +191,17 @@ void dugks_destroy(dugks_t h);
  *              rollout), unpadded layout as dugks_get_state.
  * The acceleration, wall velocities and viscosity must be those of the recorded rollout.
  * Synchronous. DUGKS_E_UNSUPPORTED for 3D lattices or BF16/F16 storage; DUGKS_E_INVAL
- * without a recorded rollout. Memory: (ceil(nsteps/every) + every - 1) x the state size plus
+ * without a recorded rollout. Memory: (ceil(nsteps/every) + every) x the state size plus
  * about 7 state sizes of work buffers. */
 int dugks_record(dugks_t h, int64_t nsteps, int32_t every);
 int dugks_adjoint(dugks_t h, const float *dL_dmom, float *dL_dfield, double *dL_dwall, void *dL_dstate0);
+/* Asynchronous form of dugks_adjoint for running the reverse sweeps of several handles
+ * concurrently on their streams: enqueues the same work and returns; dL_dfield and
+ * dL_dstate0 are complete once the handle's stream is (dugks_sync). dugks_adjoint_wall waits
+ * for the stream and writes the wall-velocity gradient [6][3] of the last adjoint to HOST
+ * memory. dugks_adjoint_async first waits for any earlier work of the handle. */
+int dugks_adjoint_async(dugks_t h, const float *dL_dmom, float *dL_dfield, void *dL_dstate0);
+int dugks_adjoint_wall(dugks_t h, double *dL_dwall);
 
 /* ---- batched form: many independent 2D instances ---------------------------------------
  * A batch advances `count` independent D2Q9 instances (each its own mesh, viscosity,

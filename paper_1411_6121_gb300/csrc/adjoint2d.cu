@@ -30,6 +30,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <vector>
 
 #include "../../include/dugks.h"
@@ -357,6 +358,172 @@ __device__ __forceinline__ void face_adjoint(const AdjParams<T> &a, int d, int i
     Gcb[1] = a.rho0 * a.wface * bmc[1];
 }
 
+// ---- fast paths: interfaces and cells whose stencils lie inside the domain, away from
+// walls and periodic seams (no ghosts, images, NEQ or x_c coupling). Same arithmetic as the
+// general path, with compile-time velocities and direct neighbour reads. ----
+
+// relax_T with a compile-time velocity loop; D >= 0 restricts it to the velocities that
+// cross an interface normal to axis D (the others have zero weight there).
+template <class T, int D>
+__device__ __forceinline__ void relax_T_c(const AdjParams<T> &a, const T wk[Q], T dr, const T m[2], const T Gh[2],
+                                          T b, T c, T &bdr, T bm[2], T bG[2]) {
+    const T gm = (Gh[0] * m[0] + Gh[1] * m[1]) * a.inv_rho0;
+    const T mm = m[0] * m[0] + m[1] * m[1];
+    sfor<Q>([&](auto kc) {
+        constexpr int k = kc;
+        constexpr int e0 = L9::e(k, 0), e1 = L9::e(k, 1);
+        if constexpr (D < 0 || L9::e(k, D < 0 ? 0 : D) != 0) {
+            const T W = L9::wt<T>(k);
+            const T em = T(e0) * m[0] + T(e1) * m[1];
+            const T s = T(3) * (Gh[0] * T(e0) + Gh[1] * T(e1) - gm);
+            const T feq = W * a.rho0 + W * (dr + T(3) * em + (T(4.5) * em * em - T(1.5) * mm) * a.inv_rho0);
+            const T w = wk[k];
+            const T cw = w * (b + c * s) * W;  // w dP/dgeq times W
+            const T fq = w * c * T(3) * feq;
+            bdr += cw;
+            bm[0] += cw * (T(3) * T(e0) + (T(9) * em * T(e0) - T(3) * m[0]) * a.inv_rho0) - fq * Gh[0] * a.inv_rho0;
+            bm[1] += cw * (T(3) * T(e1) + (T(9) * em * T(e1) - T(3) * m[1]) * a.inv_rho0) - fq * Gh[1] * a.inv_rho0;
+            bG[0] += fq * (T(e0) - m[0] * a.inv_rho0);
+            bG[1] += fq * (T(e1) - m[1] * a.inv_rho0);
+        }
+    });
+}
+
+// The fast regions. Interfaces normal to d: both cells, their tangential neighbours and
+// the cells' own interfaces are in the domain without wrapping, and the interface is neither
+// a wall nor the x_c of one. Cells: every interface of the stencil transposed in adj_cells
+// is in the domain and the cell feeds no ghost or periodic image. Everything else (a frame
+// along the boundary) takes the general path.
+struct Rect {
+    int W, H;            // index space W x H
+    int x0, x1, y0, y1;  // fast rectangle, inclusive (empty when x0 > x1 or y0 > y1)
+};
+__host__ __device__ inline Rect face_rect(int d, int nx, int ny, int perx, int pery) {
+    if (d == 0) {
+        const int m = perx ? 1 : 2;
+        return Rect{nx + 1, ny, m, nx - m, 1, ny - 2};
+    }
+    const int m = pery ? 1 : 2;
+    return Rect{nx, ny + 1, 1, nx - 2, m, ny - m};
+}
+__host__ __device__ inline Rect cell_rect(int nx, int ny, int perx, int pery) {
+    const int mx = perx ? 1 : 2, my = pery ? 1 : 2;
+    return Rect{nx, ny, mx, nx - 1 - mx, my, ny - 1 - my};
+}
+__host__ __device__ inline bool rect_empty(const Rect &r) { return r.x0 > r.x1 || r.y0 > r.y1; }
+__host__ __device__ inline int64_t rect_count(const Rect &r) {
+    return rect_empty(r) ? 0 : (int64_t)(r.x1 - r.x0 + 1) * (r.y1 - r.y0 + 1);
+}
+__host__ __device__ inline int64_t frame_count(const Rect &r) { return (int64_t)r.W * r.H - rect_count(r); }
+// The t-th element (row-major) of the index space outside the fast rectangle.
+__device__ inline void frame_at(const Rect &r, int64_t t, int &x, int &y) {
+    if (rect_empty(r)) {
+        x = (int)(t % r.W);
+        y = (int)(t / r.W);
+        return;
+    }
+    const int64_t below = (int64_t)r.y0 * r.W, above = (int64_t)(r.H - 1 - r.y1) * r.W;
+    if (t < below) {
+        x = (int)(t % r.W);
+        y = (int)(t / r.W);
+    } else if (t < below + above) {
+        t -= below;
+        x = (int)(t % r.W);
+        y = r.y1 + 1 + (int)(t / r.W);
+    } else {
+        t -= below + above;
+        const int side = r.x0 + (r.W - 1 - r.x1);  // frame columns of a middle row
+        y = r.y0 + (int)(t / side);
+        const int c = (int)(t % side);
+        x = c < r.x0 ? c : r.x1 + 1 + (c - r.x0);
+    }
+}
+
+template <class T, int d>
+__device__ __forceinline__ void face_fast(const AdjParams<T> &a, int i, int j, int64_t f, int64_t nf) {
+    const int nx = a.n[0];
+    const int64_t nc = ncell(a);
+    const int64_t cR = i + (int64_t)nx * j;
+    const int64_t cL = d == 0 ? cR - 1 : cR - nx;
+    const int64_t ts = d == 0 ? nx : 1;  // step to the tangential neighbour
+    T F[Q];
+    sfor<Q>([&](auto kc) {
+        constexpr int k = kc;
+        constexpr int ed = L9::e(k, d), et = L9::e(k, 1 - d);
+        const T *ph = a.phi + k * nc;
+        const T l = ph[cL], r = ph[cR];
+        T v = T(0.5) * (l + r);
+        if constexpr (ed != 0) v -= a.kappa * T(ed) * (r - l);
+        if constexpr (et != 0) v -= T(0.25) * a.kappa * T(et) * ((ph[cL + ts] + ph[cR + ts]) - (ph[cL - ts] + ph[cR - ts]));
+        F[k] = v;
+    });
+    T Gh[2];
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        const T fl = a.field ? T(0.5) * ((T)a.field[c * nc + cL] + (T)a.field[c * nc + cR]) : T(0);
+        Gh[c] = (a.g[c] + fl) * a.cthc;
+    }
+    T dr, m[2];
+    moments2(a, F, Gh, a.wface, dr, m);
+    T fbar[Q];
+    sfor<Q>([&](auto kc) {
+        constexpr int k = kc;
+        constexpr int ed = L9::e(k, d);
+        if constexpr (ed != 0) fbar[k] = a.two_kappa * T(ed) * (a.lam1[k * nc + cR] - a.lam1[k * nc + cL]);
+        else fbar[k] = T(0);
+    });
+    T bdr = T(0), bm[2] = {T(0), T(0)}, Gb[2] = {T(0), T(0)};
+    relax_T_c<T, d>(a, fbar, dr, m, Gh, a.b7, a.c7, bdr, bm, Gb);
+    T *fb = a.fb[d];
+    sfor<Q>([&](auto kc) {
+        constexpr int k = kc;
+        fb[k * nf + f] = (T(1) - a.b7) * fbar[k] + bdr + T(L9::e(k, 0)) * bm[0] + T(L9::e(k, 1)) * bm[1];
+    });
+    a.gb[d][f] = Gb[0] + a.rho0 * a.wface * bm[0];
+    a.gb[d][nf + f] = Gb[1] + a.rho0 * a.wface * bm[1];
+}
+
+template <class T>
+__device__ __forceinline__ void cell_fast(const AdjParams<T> &a, int x, int y, int64_t c) {
+    const int nx = a.n[0];
+    const int64_t nc = ncell(a), n0 = nface(a, 0), n1 = nface(a, 1);
+    const int64_t ix = x + (int64_t)(nx + 1) * y;  // x interface (x, y): the cell's -x interface
+    const int64_t iy = x + (int64_t)nx * y;        // y interface (x, y): the cell's -y interface
+    const int64_t sx = nx + 1, sy = nx;            // row strides of the interface arrays
+    const T h = T(0.5), q = T(0.25) * a.kappa;
+    T pb[Q];
+    sfor<Q>([&](auto kc) {
+        constexpr int k = kc;
+        constexpr int ex = L9::e(k, 0), ey = L9::e(k, 1);
+        const T *f0 = a.fb[0] + k * n0, *f1 = a.fb[1] + k * n1;
+        T v = T(4) / T(3) * a.lam1[k * nc + c];
+        v += (h + a.kappa * T(ex)) * f0[ix + 1] + (h - a.kappa * T(ex)) * f0[ix];
+        if constexpr (ey != 0) v += q * T(ey) * ((f0[ix + 1 + sx] + f0[ix + sx]) - (f0[ix + 1 - sx] + f0[ix - sx]));
+        v += (h + a.kappa * T(ey)) * f1[iy + sy] + (h - a.kappa * T(ey)) * f1[iy];
+        if constexpr (ex != 0) v += q * T(ex) * ((f1[iy + 1 + sy] + f1[iy + 1]) - (f1[iy - 1 + sy] + f1[iy - 1]));
+        pb[k] = v;
+    });
+    const T dr = a.mom[c];
+    const T m[2] = {a.mom[nc + c], a.mom[2 * nc + c]};
+    T Gh[2];
+    cell_Gh(a, x, y, Gh);
+    T bdr = T(0), bm[2] = {T(0), T(0)}, bG[2] = {T(0), T(0)};
+    relax_T_c<T, -1>(a, pb, dr, m, Gh, a.b1, a.c1, bdr, bm, bG);
+    sfor<Q>([&](auto kc) {
+        constexpr int k = kc;
+        a.lam0[k * nc + c] = -a.lam1[k * nc + c] / T(3) + (T(1) - a.b1) * pb[k] + bdr + T(L9::e(k, 0)) * bm[0] +
+                             T(L9::e(k, 1)) * bm[1];
+    });
+    if (a.dG) {
+#pragma unroll
+        for (int comp = 0; comp < 2; comp++) {
+            const T fs = T(0.5) * (a.gb[0][comp * n0 + ix] + a.gb[0][comp * n0 + ix + 1]) +
+                         T(0.5) * (a.gb[1][comp * n1 + iy] + a.gb[1][comp * n1 + iy + sy]);
+            a.dG[comp * nc + c] += (double)((bG[comp] + a.rho0 * a.wcell * bm[comp]) * a.ctc + fs * a.cthc);
+        }
+    }
+}
+
 // ---- kernels ----
 template <class T>
 __global__ void __launch_bounds__(256) adj_cells_fwd(const AdjParams<T> a) {
@@ -379,14 +546,30 @@ __global__ void __launch_bounds__(256) adj_cells_fwd(const AdjParams<T> a) {
     }
 }
 
+// Interior interfaces of both axes (blockIdx.z = axis), 2D blocks over the fast rectangle.
 template <class T>
-__global__ void __launch_bounds__(128) adj_faces(const AdjParams<T> a) {
-    const int64_t n0 = nface(a, 0), ntot = n0 + nface(a, 1);
+__global__ void __launch_bounds__(128, 4) adj_faces_fast(const AdjParams<T> a) {
+    const int d = blockIdx.z;
+    const Rect r = face_rect(d, a.n[0], a.n[1], a.per[0], a.per[1]);
+    const int i = r.x0 + blockIdx.x * blockDim.x + threadIdx.x, j = r.y0 + blockIdx.y * blockDim.y + threadIdx.y;
+    if (i > r.x1 || j > r.y1) return;
+    const int64_t f = fidx(a, d, i, j);
+    if (d == 0) face_fast<T, 0>(a, i, j, f, nface(a, 0));
+    else face_fast<T, 1>(a, i, j, f, nface(a, 1));
+}
+
+// The frame of both axes: walls (NEQ, dL/du_w), x_c interfaces, periodic seams.
+template <class T>
+__global__ void __launch_bounds__(128) adj_faces_frame(const AdjParams<T> a) {
+    const Rect r0 = face_rect(0, a.n[0], a.n[1], a.per[0], a.per[1]);
+    const Rect r1 = face_rect(1, a.n[0], a.n[1], a.per[0], a.per[1]);
+    const int64_t c0 = frame_count(r0), ntot = c0 + frame_count(r1);
+    const int64_t n0 = nface(a, 0);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntot; t += (int64_t)gridDim.x * blockDim.x) {
-        const int d = t < n0 ? 0 : 1;
-        const int64_t f = d == 0 ? t : t - n0;
-        const int w = d == 0 ? a.n[0] + 1 : a.n[0];
-        const int i = (int)(f % w), j = (int)(f / w);
+        const int d = t < c0 ? 0 : 1;
+        int i, j;
+        frame_at(d == 0 ? r0 : r1, d == 0 ? t : t - c0, i, j);
+        const int64_t f = fidx(a, d, i, j);
         const int pos = d == 0 ? i : j, nd = a.n[d];
         T Fb[Q], Gb[2], Fcb[Q], Gcb[2], Wb[2];
         int wall;
@@ -411,7 +594,7 @@ __global__ void __launch_bounds__(128) adj_faces(const AdjParams<T> a) {
             }
         }
         T *fb = a.fb[d], *gb = a.gb[d];
-        const int64_t nf = d == 0 ? n0 : ntot - n0;
+        const int64_t nf = d == 0 ? n0 : nface(a, 1);
         for (int k = 0; k < Q; k++) fb[k * nf + f] = Fb[k];
         gb[f] = Gb[0];
         gb[nf + f] = Gb[1];
@@ -447,10 +630,22 @@ __device__ __forceinline__ T face_G_T(const AdjParams<T> &a, int comp, int x, in
 }
 
 template <class T>
-__global__ void __launch_bounds__(128) adj_cells(const AdjParams<T> a) {
+__global__ void __launch_bounds__(128, 4) adj_cells_fast(const AdjParams<T> a) {
+    const Rect r = cell_rect(a.n[0], a.n[1], a.per[0], a.per[1]);
+    const int x = r.x0 + blockIdx.x * blockDim.x + threadIdx.x, y = r.y0 + blockIdx.y * blockDim.y + threadIdx.y;
+    if (x > r.x1 || y > r.y1) return;
+    cell_fast(a, x, y, x + (int64_t)a.n[0] * y);
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) adj_cells_frame(const AdjParams<T> a) {
     const int64_t nc = ncell(a);
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(c % a.n[0]), y = (int)(c / a.n[0]);
+    const Rect r = cell_rect(a.n[0], a.n[1], a.per[0], a.per[1]);
+    const int64_t ntot = frame_count(r);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntot; t += (int64_t)gridDim.x * blockDim.x) {
+        int x, y;
+        frame_at(r, t, x, y);
+        const int64_t c = x + (int64_t)a.n[0] * y;
         int ux[3], uy[3];
         T wx[3], wy[3];
         const int nux = ext_users<T>(x, a.n[0], a.per[0], ux, wx);
@@ -476,8 +671,8 @@ __global__ void __launch_bounds__(128) adj_cells(const AdjParams<T> a) {
                                  (T)L9::e(k, 0) * bm[0] + (T)L9::e(k, 1) * bm[1];
         if (a.dG) {
             for (int comp = 0; comp < 2; comp++) {
-                const T s = (bG[comp] + a.rho0 * a.wcell * bm[comp]) * a.ctc + face_G_T(a, comp, x, y) * a.cthc;
-                a.dG[comp * nc + c] += (double)s;
+                const T sv = (bG[comp] + a.rho0 * a.wcell * bm[comp]) * a.ctc + face_G_T(a, comp, x, y) * a.cthc;
+                a.dG[comp * nc + c] += (double)sv;
             }
         }
     }
@@ -497,6 +692,23 @@ __global__ void adj_seed(const AdjParams<T> a, const float *dLdm, T rt, T c_over
             a.dG[nc + c] += (double)gu1 * gdt;
         }
     }
+}
+
+// dL/du_w per face [6][3] from the per-wall-interface slots (-x: ny, +x: ny, -y: nx, +y: nx
+// slots of 2 components), each sum in slot order (deterministic); zero for the faces that
+// are not velocity walls.
+__global__ void adj_wall_sum(const double *slots, double *out, int nx, int ny, int vx0, int vx1, int vy0, int vy1) {
+    const int t = threadIdx.x;  // face * 3 + component
+    if (t >= 18) return;
+    const int f = t / 3, comp = t % 3;
+    const int vel[4] = {vx0, vx1, vy0, vy1};
+    double s = 0.0;
+    if (f < 4 && comp < 2 && vel[f]) {
+        const int first = f == 0 ? 0 : f == 1 ? ny : f == 2 ? 2 * ny : 2 * ny + nx;
+        const int count = f < 2 ? ny : nx;
+        for (int i = 0; i < count; i++) s += slots[2 * (first + i) + comp];
+    }
+    out[t] = s;
 }
 
 __global__ void adj_to_float(const double *src, float *dst, int64_t n) {
@@ -580,24 +792,76 @@ AdjParams<T> base_params(const dugks_t h, const AdjBufs &B) {
 }
 
 // One reverse step at the state g~^n held in `state` (t_n = tn): lambda' in lam1 -> lam0.
+// Five launches: cell recompute, interior and frame interfaces, interior and frame cells.
 template <class T>
 cudaError_t reverse_step(AdjParams<T> a, const dugks_t h, const void *state, double tn, const void *lam1,
-                         void *lam0) {
+                         void *lam0, int64_t *launches) {
     const double om = h->force.omega, inv_c = 1.0 / h->c;
     a.ctc = (T)(cos(om * tn) * inv_c);
     a.cthc = (T)(cos(om * (tn + 0.5 * h->dt)) * inv_c);
     a.state = (const T *)state;
     a.lam1 = (const T *)lam1;
     a.lam0 = (T *)lam0;
-    const int64_t nc = h->ncell, nf = (h->nx + 1) * h->ny + h->nx * (h->ny + 1);
-    adj_cells_fwd<T><<<blocks_for(nc, 256), 256, 0, h->stream>>>(a);
-    adj_faces<T><<<blocks_for(nf, 128), 128, 0, h->stream>>>(a);
-    adj_cells<T><<<blocks_for(nc, 128), 128, 0, h->stream>>>(a);
+    cudaStream_t st = h->stream;
+    const int nx = (int)h->nx, ny = (int)h->ny;
+    const int64_t nc = h->ncell;
+    adj_cells_fwd<T><<<blocks_for(nc, 256), 256, 0, st>>>(a);
+    const Rect r0 = face_rect(0, nx, ny, a.per[0], a.per[1]), r1 = face_rect(1, nx, ny, a.per[0], a.per[1]);
+    int64_t n = 1;
+    if (rect_count(r0) + rect_count(r1) > 0) {
+        const int w = std::max(rect_empty(r0) ? 0 : r0.x1 - r0.x0 + 1, rect_empty(r1) ? 0 : r1.x1 - r1.x0 + 1);
+        const int hh = std::max(rect_empty(r0) ? 0 : r0.y1 - r0.y0 + 1, rect_empty(r1) ? 0 : r1.y1 - r1.y0 + 1);
+        adj_faces_fast<T><<<dim3((w + 31) / 32, (hh + 3) / 4, 2), dim3(32, 4), 0, st>>>(a);
+        n++;
+    }
+    const int64_t ff = frame_count(r0) + frame_count(r1);
+    if (ff > 0) {
+        adj_faces_frame<T><<<blocks_for(ff, 128), 128, 0, st>>>(a);
+        n++;
+    }
+    const Rect rc = cell_rect(nx, ny, a.per[0], a.per[1]);
+    if (rect_count(rc) > 0) {
+        adj_cells_fast<T><<<dim3((rc.x1 - rc.x0 + 32) / 32, (rc.y1 - rc.y0 + 4) / 4), dim3(32, 4), 0, st>>>(a);
+        n++;
+    }
+    const int64_t cf = frame_count(rc);
+    if (cf > 0) {
+        adj_cells_frame<T><<<blocks_for(cf, 128), 128, 0, st>>>(a);
+        n++;
+    }
+    *launches += n;
     return cudaGetLastError();
 }
 
+// The work of one checkpoint segment of `len` steps whose first state is in seg[0] (copied
+// from the checkpoint) and whose clock starts at `start`: recompute the states into
+// seg[1 .. len-1], then the reverse steps len-1 .. 0 with lambda ping-ponging from
+// lam[cur]. Returns the number of launches through *launches.
 template <class T>
-int run_adjoint(dugks_t h, const float *dL_dmom, float *dL_dfield, double *dL_dwall, void *dL_dstate0) {
+cudaError_t enqueue_segment(dugks_t h, const AdjParams<T> &a, const AdjBufs &B, int64_t start, int64_t len, int cur,
+                            int64_t *launches) {
+    AdjointTape &t = h->tape;
+    for (int64_t j = 1; j < len; j++) {
+        StepParams p = handle_params(h);
+        p.src = t.seg[(size_t)j - 1];
+        p.dst = t.seg[(size_t)j];
+        p.step_ctr = t.zero;
+        p.step_off = (int)(t.step0 + start + j - 1);
+        cudaError_t e = handle_launch_step(h, p);
+        if (e != cudaSuccess) return e;
+        (*launches)++;
+    }
+    for (int64_t j = len - 1; j >= 0; j--) {
+        const double tn = (double)(t.step0 + start + j) * h->dt;
+        cudaError_t e = reverse_step<T>(a, h, t.seg[(size_t)j], tn, B.lam[cur], B.lam[cur ^ 1], launches);
+        if (e != cudaSuccess) return e;
+        cur ^= 1;
+    }
+    return cudaSuccess;
+}
+
+template <class T>
+int enqueue_adjoint(dugks_t h, const float *dL_dmom, float *dL_dfield, void *dL_dstate0) {
     AdjointTape &t = h->tape;
     const size_t es = sizeof(T);
     const AdjBufs B = carve(t.scratch, h->nx, h->ny, es);
@@ -619,30 +883,54 @@ int run_adjoint(dugks_t h, const float *dL_dmom, float *dL_dfield, double *dL_dw
     int cur = 0;
     const int64_t every = t.every;
     const int64_t nseg = (t.steps + every - 1) / every;
-    std::vector<const void *> states((size_t)every);
-    for (int64_t sg = nseg - 1; sg >= 0; sg--) {
+    // With a time-independent acceleration every segment of the same length and starting
+    // parity is the same sequence of launches on the same buffers: capture it once as a
+    // CUDA graph and replay it per segment.
+    const bool graphs = h->use_graph && h->force.omega == 0.0 && nseg >= 3;
+    // graphs of the previous call (its work has completed: the caller synchronised the
+    // handle's stream before this call)
+    for (cudaGraphExec_t g : t.graphs) cudaGraphExecDestroy(g);
+    t.graphs.clear();
+    std::map<std::pair<int64_t, int>, std::pair<cudaGraphExec_t, int64_t>> cache;  // graph, its launches
+    int rc = DUGKS_OK;
+    for (int64_t sg = nseg - 1; sg >= 0 && rc == DUGKS_OK; sg--) {
         const int64_t start = sg * every;
         const int64_t len = std::min<int64_t>(every, t.steps - start);
-        states[0] = t.ckpt[(size_t)sg];
-        // recompute the segment's states from its checkpoint
-        for (int64_t j = 1; j < len; j++) {
-            StepParams p = handle_params(h);
-            p.src = states[(size_t)j - 1];
-            p.dst = t.seg[(size_t)j - 1];
-            p.step_ctr = t.zero;
-            p.step_off = (int)(t.step0 + start + j - 1);
-            e = handle_launch_step(h, p);
-            if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "adjoint recompute: %s", cudaGetErrorString(e));
-            states[(size_t)j] = t.seg[(size_t)j - 1];
-            h->launches++;
+        e = cudaMemcpyAsync(t.seg[0], t.ckpt[(size_t)sg], h->state_bytes, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) { rc = handle_fail(h, DUGKS_E_CUDA, "adjoint: %s", cudaGetErrorString(e)); break; }
+        int64_t nl = 0;
+        if (graphs) {
+            const auto key = std::make_pair(len, cur);
+            auto it = cache.find(key);
+            if (it == cache.end()) {
+                cudaGraph_t g;
+                e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    cudaError_t e2 = enqueue_segment<T>(h, a, B, start, len, cur, &nl);
+                    e = cudaStreamEndCapture(st, &g);
+                    if (e2 != cudaSuccess) e = e2;
+                }
+                cudaGraphExec_t ge = nullptr;
+                if (e == cudaSuccess) {
+                    e = cudaGraphInstantiate(&ge, g, 0);
+                    cudaGraphDestroy(g);
+                }
+                if (e != cudaSuccess) { rc = handle_fail(h, DUGKS_E_CUDA, "adjoint graph: %s", cudaGetErrorString(e)); break; }
+                it = cache.emplace(key, std::make_pair(ge, nl)).first;
+                t.graphs.push_back(ge);
+            }
+            nl = it->second.second;
+            e = cudaGraphLaunch(it->second.first, st);
+        } else {
+            e = enqueue_segment<T>(h, a, B, start, len, cur, &nl);
         }
-        for (int64_t j = len - 1; j >= 0; j--) {
-            const double tn = (double)(t.step0 + start + j) * h->dt;
-            e = reverse_step<T>(a, h, states[(size_t)j], tn, B.lam[cur], B.lam[cur ^ 1]);
-            if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "adjoint step: %s", cudaGetErrorString(e));
-            h->launches += 3;
-            cur ^= 1;
-        }
+        if (e != cudaSuccess) { rc = handle_fail(h, DUGKS_E_CUDA, "adjoint step: %s", cudaGetErrorString(e)); break; }
+        h->launches += nl;
+        if (len & 1) cur ^= 1;
+    }
+    if (rc != DUGKS_OK) {
+        cudaStreamSynchronize(st);
+        return rc;
     }
     if (dL_dfield) {
         adj_to_float<<<blocks_for(2 * nc, 256), 256, 0, st>>>(t.dG, dL_dfield, 2 * nc);
@@ -652,24 +940,13 @@ int run_adjoint(dugks_t h, const float *dL_dmom, float *dL_dfield, double *dL_dw
         e = cudaMemcpyAsync(dL_dstate0, B.lam[cur], es * Q * nc, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "adjoint: %s", cudaGetErrorString(e));
     }
-    std::vector<double> w((size_t)(2 * nwall));
-    if (dL_dwall) e = cudaMemcpyAsync(w.data(), t.dW, sizeof(double) * 2 * nwall, cudaMemcpyDeviceToHost, st);
+    adj_wall_sum<<<1, 32, 0, st>>>(t.dW, t.dW_face, (int)h->nx, (int)h->ny,
+                                   h->bcs.face[0].type == DUGKS_BC_NEQ_VELOCITY, h->bcs.face[1].type == DUGKS_BC_NEQ_VELOCITY,
+                                   h->bcs.face[2].type == DUGKS_BC_NEQ_VELOCITY, h->bcs.face[3].type == DUGKS_BC_NEQ_VELOCITY);
+    h->launches++;
+    e = cudaMemcpyAsync(t.h_wall, t.dW_face, sizeof(double) * 18, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "adjoint: %s", cudaGetErrorString(e));
-    if (dL_dwall) {
-        // wall interface slots: -x (ny), +x (ny), -y (nx), +y (nx); fixed summation order
-        for (int i = 0; i < 18; i++) dL_dwall[i] = 0.0;
-        const int64_t first[4] = {0, h->ny, 2 * h->ny, 2 * h->ny + h->nx};
-        const int64_t count[4] = {h->ny, h->ny, h->nx, h->nx};
-        for (int f = 0; f < 4; f++) {
-            if (h->bcs.face[f].type != DUGKS_BC_NEQ_VELOCITY) continue;
-            for (int64_t s = 0; s < count[f]; s++) {
-                dL_dwall[3 * f + 0] += w[(size_t)(2 * (first[f] + s))];
-                dL_dwall[3 * f + 1] += w[(size_t)(2 * (first[f] + s) + 1)];
-            }
-        }
-    }
     return DUGKS_OK;
 }
 
@@ -685,8 +962,12 @@ void adjoint_release(dugks_t h) {
     cudaFree(t.dG);
     cudaFree(t.dW);
     cudaFree(t.zero);
+    cudaFree(t.dW_face);
+    if (t.h_wall) cudaFreeHost(t.h_wall);
+    for (cudaGraphExec_t g : t.graphs) cudaGraphExecDestroy(g);
+    t.graphs.clear();
     t.scratch = nullptr;
-    t.dG = t.dW = nullptr;
+    t.dG = t.dW = t.dW_face = t.h_wall = nullptr;
     t.zero = nullptr;
     t.steps = 0;
 }
@@ -711,8 +992,11 @@ extern "C" int dugks_record(dugks_t h, int64_t nsteps, int32_t every) {
     if (h->step + nsteps > 2147483647LL) return handle_fail(h, DUGKS_E_INVAL, "record: step index past 2^31 - 1");
     AdjointTape &t = h->tape;
     t.steps = 0;
+    // an earlier asynchronous adjoint may still read the buffers reused below
+    cudaError_t es0 = cudaStreamSynchronize(h->stream);
+    if (es0 != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "record: %s", cudaGetErrorString(es0));
     const int64_t nseg = (nsteps + every - 1) / every;
-    const int64_t nbuf = std::min<int64_t>(every, nsteps) - 1;
+    const int64_t nbuf = std::min<int64_t>(every, nsteps);  // seg[0] receives the checkpoint
     cudaError_t e = cudaSuccess;
     auto resize = [&](std::vector<void *> &v, int64_t count) {
         while ((int64_t)v.size() > count) {
@@ -736,6 +1020,8 @@ extern "C" int dugks_record(dugks_t h, int64_t nsteps, int32_t every) {
         if (e == cudaSuccess) e = cudaMalloc((void **)&t.dG, sizeof(double) * 2 * h->ncell);
         if (e == cudaSuccess) e = cudaMalloc((void **)&t.dW, sizeof(double) * 4 * (h->nx + h->ny));
         if (e == cudaSuccess) e = cudaMalloc((void **)&t.zero, sizeof(long long));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&t.dW_face, sizeof(double) * 18);
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&t.h_wall, sizeof(double) * 18);
         if (e == cudaSuccess) e = cudaMemsetAsync(t.zero, 0, sizeof(long long), h->stream);
     }
     if (e != cudaSuccess) {
@@ -756,12 +1042,38 @@ extern "C" int dugks_record(dugks_t h, int64_t nsteps, int32_t every) {
     return DUGKS_OK;
 }
 
-extern "C" int dugks_adjoint(dugks_t h, const float *dL_dmom, float *dL_dfield, double *dL_dwall,
-                             void *dL_dstate0) {
+static int adjoint_enqueue_checked(dugks_t h, const float *dL_dmom, float *dL_dfield, void *dL_dstate0) {
     if (!h || !dL_dmom) return DUGKS_E_INVAL;
     int rc = check_adjoint_support(h);
     if (rc != DUGKS_OK) return rc;
     if (h->tape.steps < 1) return handle_fail(h, DUGKS_E_INVAL, "adjoint: no recorded rollout (call dugks_record)");
-    return h->store == DUGKS_STORE_F64 ? run_adjoint<double>(h, dL_dmom, dL_dfield, dL_dwall, dL_dstate0)
-                                       : run_adjoint<float>(h, dL_dmom, dL_dfield, dL_dwall, dL_dstate0);
+    // the previous call's graphs and buffers are reused: its work must have completed
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "adjoint: %s", cudaGetErrorString(e));
+    return h->store == DUGKS_STORE_F64 ? enqueue_adjoint<double>(h, dL_dmom, dL_dfield, dL_dstate0)
+                                       : enqueue_adjoint<float>(h, dL_dmom, dL_dfield, dL_dstate0);
+}
+
+extern "C" int dugks_adjoint_async(dugks_t h, const float *dL_dmom, float *dL_dfield, void *dL_dstate0) {
+    return adjoint_enqueue_checked(h, dL_dmom, dL_dfield, dL_dstate0);
+}
+
+extern "C" int dugks_adjoint_wall(dugks_t h, double *dL_dwall) {
+    if (!h || !dL_dwall) return DUGKS_E_INVAL;
+    if (!h->tape.h_wall) return handle_fail(h, DUGKS_E_INVAL, "adjoint_wall: no adjoint has run");
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "adjoint_wall: %s", cudaGetErrorString(e));
+    for (int i = 0; i < 18; i++) dL_dwall[i] = h->tape.h_wall[i];
+    return DUGKS_OK;
+}
+
+extern "C" int dugks_adjoint(dugks_t h, const float *dL_dmom, float *dL_dfield, double *dL_dwall,
+                             void *dL_dstate0) {
+    int rc = adjoint_enqueue_checked(h, dL_dmom, dL_dfield, dL_dstate0);
+    if (rc != DUGKS_OK) return rc;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "adjoint: %s", cudaGetErrorString(e));
+    if (dL_dwall)
+        for (int i = 0; i < 18; i++) dL_dwall[i] = h->tape.h_wall[i];
+    return DUGKS_OK;
 }

@@ -18,12 +18,15 @@ struct AdjointTape {
     int64_t step0 = 0;           // clock step at the start of the rollout
     int every = 0;               // checkpoint interval
     std::vector<void *> ckpt;    // padded state at step0 + s * every, s = 0 .. nseg - 1
-    std::vector<void *> seg;     // every - 1 padded states for the segment recompute
+    std::vector<void *> seg;     // every padded states of the segment being reversed (seg[0]: its checkpoint)
     void *scratch = nullptr;     // adjoint work buffers (adjoint_carve)
     size_t scratch_bytes = 0;
     double *dG = nullptr;        // [2][ncell] dL/dfield accumulator
     double *dW = nullptr;        // [nwall][2] dL/du_w per wall interface
     long long *zero = nullptr;   // device counter fixed at 0 (recompute clock)
+    double *dW_face = nullptr;   // [6][3] dL/du_w per face (device), reduced in fixed order
+    double *h_wall = nullptr;    // [6][3] pinned copy of dW_face
+    std::vector<cudaGraphExec_t> graphs;  // reverse-sweep graphs of the last adjoint call
 };
 
 }  // namespace dugks

@@ -30,7 +30,7 @@ EXPORTS = [
     "dugks_residual", "dugks_state_bytes", "dugks_get_state", "dugks_set_state",
     "dugks_get_clock", "dugks_set_clock", "dugks_set_force_field", "dugks_sync",
     "dugks_launch_count", "dugks_last_error", "dugks_destroy", "dugks_residual_static",
-    "dugks_set_boundaries", "dugks_record", "dugks_adjoint",
+    "dugks_set_boundaries", "dugks_record", "dugks_adjoint", "dugks_adjoint_async", "dugks_adjoint_wall",
     "dugks_batch_create", "dugks_batch_init", "dugks_batch_step", "dugks_batch_moments", "dugks_batch_tune",
     "dugks_batch_sync", "dugks_batch_launch_count", "dugks_batch_last_error", "dugks_batch_destroy",
 ]
@@ -100,6 +100,8 @@ def load(path=None):
     lib.dugks_set_boundaries.argtypes = [P, C.POINTER(Boundaries)]
     lib.dugks_record.argtypes = [P, I64, I32]
     lib.dugks_adjoint.argtypes = [P, P, P, D, P]
+    lib.dugks_adjoint_async.argtypes = [P, P, P, P]
+    lib.dugks_adjoint_wall.argtypes = [P, D]
     lib.dugks_residual_static.argtypes = [I32, I32, P, I64, I64, I64, C.c_double, C.c_double, D, P, P, I32, D, P]
     lib.dugks_batch_create.argtypes = [I32, C.POINTER(Mesh), D, C.c_double, C.POINTER(Force), C.POINTER(Boundaries),
                                        C.POINTER(Opts), C.POINTER(P)]
@@ -282,6 +284,23 @@ class Sim:
                                     None if dstate is None else C.c_void_p(dstate.data_ptr()))
         _check(rc, self.h)
         return dfield, dwall, dstate
+
+    def adjoint_async(self, dL_dmom, dfield=None, dstate=None):
+        """Enqueue the reverse sweep on the handle's stream and return (see
+        ``dugks_adjoint_async``); ``dfield`` / ``dstate`` are CUDA tensors filled once the
+        stream completes (``sync``)."""
+        assert dL_dmom.is_cuda and dL_dmom.is_contiguous() and dL_dmom.numel() == (self.dim + 1) * self.ncell
+        self._async_keep = (dL_dmom, dfield, dstate)  # kept alive until the next call
+        rc = self.lib.dugks_adjoint_async(self.h, C.c_void_p(dL_dmom.data_ptr()),
+                                          None if dfield is None else C.c_void_p(dfield.data_ptr()),
+                                          None if dstate is None else C.c_void_p(dstate.data_ptr()))
+        _check(rc, self.h)
+
+    def adjoint_wall(self):
+        """dL/du_wall [6][3] of the last adjoint (waits for the handle's stream)."""
+        out = np.zeros((6, 3), dtype=np.float64)
+        _check(self.lib.dugks_adjoint_wall(self.h, _dp(out)), self.h)
+        return out
 
     def sync(self, timeout_s=0.0):
         _check(self.lib.dugks_sync(self.h, float(timeout_s)), self.h)
