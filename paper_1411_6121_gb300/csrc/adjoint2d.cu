@@ -81,19 +81,8 @@ __device__ __forceinline__ int64_t fidx(const AdjParams<T> &a, int d, int i, int
     return d == 0 ? i + (int64_t)(a.n[0] + 1) * j : i + (int64_t)a.n[0] * j;
 }
 
-// ---- step 2: extended positions -1 .. n along one axis ----
-// Cells that make up position x (reading R3: ghost = 2 f(0) - f(1) at a wall, the periodic
-// image otherwise) and their weights; returns the count.
-template <class T>
-__device__ __forceinline__ int ext_parts(int x, int n, int per, int c[2], T w[2]) {
-    if (x >= 0 && x < n) { c[0] = x; w[0] = T(1); return 1; }
-    if (per) { c[0] = x < 0 ? x + n : x - n; w[0] = T(1); return 1; }
-    c[0] = x < 0 ? 0 : n - 1;
-    c[1] = x < 0 ? 1 : n - 2;
-    w[0] = T(2);
-    w[1] = T(-1);
-    return 2;
-}
+// ---- step 2: extended positions -1 .. n along one axis (reading R3: ghost = 2 f(0) - f(1)
+// at a wall, the periodic image otherwise) ----
 // The transpose: positions that cell x contributes to and the weights (at most 3).
 template <class T>
 __device__ __forceinline__ int ext_users(int x, int n, int per, int c[3], T w[3]) {
@@ -111,17 +100,25 @@ __device__ __forceinline__ int ext_users(int x, int n, int per, int c[3], T w[3]
     return k;
 }
 
+// fbar+ at an extended position, branch-free: always two cells per axis (the second with
+// weight 0 where the position is a real cell or a periodic image), so every load address is
+// known up front and the loads of a reconstruction can all be in flight together.
+template <class T>
+__device__ __forceinline__ void ext2(int x, int n, int per, int c[2], T w[2]) {
+    if (x >= 0 && x < n) { c[0] = x; c[1] = x; w[0] = T(1); w[1] = T(0); }
+    else if (per) { c[0] = x < 0 ? x + n : x - n; c[1] = c[0]; w[0] = T(1); w[1] = T(0); }
+    else { c[0] = x < 0 ? 0 : n - 1; c[1] = x < 0 ? 1 : n - 2; w[0] = T(2); w[1] = T(-1); }
+}
 template <class T>
 __device__ __forceinline__ T phi_ext(const AdjParams<T> &a, int k, int x, int y) {
     int cx[2], cy[2];
     T wx[2], wy[2];
-    const int nxp = ext_parts<T>(x, a.n[0], a.per[0], cx, wx);
-    const int nyp = ext_parts<T>(y, a.n[1], a.per[1], cy, wy);
+    ext2<T>(x, a.n[0], a.per[0], cx, wx);
+    ext2<T>(y, a.n[1], a.per[1], cy, wy);
     const T *ph = a.phi + k * ncell(a);
-    T v = T(0);
-    for (int p = 0; p < nxp; p++)
-        for (int q = 0; q < nyp; q++) v += wx[p] * wy[q] * ph[cx[p] + (int64_t)a.n[0] * cy[q]];
-    return v;
+    const int64_t r0 = (int64_t)a.n[0] * cy[0], r1 = (int64_t)a.n[0] * cy[1];
+    const T p00 = ph[cx[0] + r0], p10 = ph[cx[1] + r0], p01 = ph[cx[0] + r1], p11 = ph[cx[1] + r1];
+    return wy[0] * (wx[0] * p00 + wx[1] * p10) + wy[1] * (wx[0] * p01 + wx[1] * p11);
 }
 
 // ---- steps 3-4: step-4 value of velocity k at interface (d, i, j) (eq. gradient with the
@@ -147,11 +144,17 @@ __device__ __forceinline__ T recon_T(const AdjParams<T> &a, int k, int x, int y)
     const int ex = L9::e(k, 0), ey = L9::e(k, 1);
     const int64_t n0 = nface(a, 0), n1 = nface(a, 1);
     const T *f0 = a.fb[0] + k * n0, *f1 = a.fb[1] + k * n1;
+    // branch-free: the index is clamped into range and the value masked, so the loads do
+    // not wait on one another
     auto fx = [&](int i, int j) -> T {
-        return (i < 0 || i > a.n[0] || j < 0 || j >= a.n[1]) ? T(0) : f0[fidx(a, 0, i, j)];
+        const bool in = !(i < 0 || i > a.n[0] || j < 0 || j >= a.n[1]);
+        const T v = f0[fidx(a, 0, min(max(i, 0), a.n[0]), min(max(j, 0), a.n[1] - 1))];
+        return in ? v : T(0);
     };
     auto fy = [&](int i, int j) -> T {
-        return (i < 0 || i >= a.n[0] || j < 0 || j > a.n[1]) ? T(0) : f1[fidx(a, 1, i, j)];
+        const bool in = !(i < 0 || i >= a.n[0] || j < 0 || j > a.n[1]);
+        const T v = f1[fidx(a, 1, min(max(i, 0), a.n[0] - 1), min(max(j, 0), a.n[1]))];
+        return in ? v : T(0);
     };
     const T h = T(0.5), q = T(0.25) * a.kappa;
     // as L of x interface (x+1, y), R of (x, y); as a tangential neighbour of the x
@@ -531,10 +534,12 @@ __global__ void __launch_bounds__(256) adj_cells_fwd(const AdjParams<T> a) {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(c % a.n[0]), y = (int)(c / a.n[0]);
         T g[Q], Gh[2], dr, m[2];
+        #pragma unroll
         for (int k = 0; k < Q; k++) g[k] = a.state[k * a.dstride + (int64_t)y * a.px + x];
         cell_Gh(a, x, y, Gh);
         moments2(a, g, Gh, a.wcell, dr, m);
         const T gm = (Gh[0] * m[0] + Gh[1] * m[1]) * a.inv_rho0;
+        #pragma unroll
         for (int k = 0; k < Q; k++) {
             const T q = geq(a, k, dr, m);
             const T s = T(3) * (Gh[0] * (T)L9::e(k, 0) + Gh[1] * (T)L9::e(k, 1) - gm);
@@ -560,7 +565,7 @@ __global__ void __launch_bounds__(128, 4) adj_faces_fast(const AdjParams<T> a) {
 
 // The frame of both axes: walls (NEQ, dL/du_w), x_c interfaces, periodic seams.
 template <class T>
-__global__ void __launch_bounds__(128) adj_faces_frame(const AdjParams<T> a) {
+__global__ void __launch_bounds__(64) adj_faces_frame(const AdjParams<T> a) {
     const Rect r0 = face_rect(0, a.n[0], a.n[1], a.per[0], a.per[1]);
     const Rect r1 = face_rect(1, a.n[0], a.n[1], a.per[0], a.per[1]);
     const int64_t c0 = frame_count(r0), ntot = c0 + frame_count(r1);
@@ -638,7 +643,7 @@ __global__ void __launch_bounds__(128, 4) adj_cells_fast(const AdjParams<T> a) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(128) adj_cells_frame(const AdjParams<T> a) {
+__global__ void __launch_bounds__(64) adj_cells_frame(const AdjParams<T> a) {
     const int64_t nc = ncell(a);
     const Rect r = cell_rect(a.n[0], a.n[1], a.per[0], a.per[1]);
     const int64_t ntot = frame_count(r);
@@ -806,8 +811,8 @@ cudaError_t reverse_step(AdjParams<T> a, const dugks_t h, const void *state, dou
     const int nx = (int)h->nx, ny = (int)h->ny;
     const int64_t nc = h->ncell;
     adj_cells_fwd<T><<<blocks_for(nc, 256), 256, 0, st>>>(a);
-    const Rect r0 = face_rect(0, nx, ny, a.per[0], a.per[1]), r1 = face_rect(1, nx, ny, a.per[0], a.per[1]);
     int64_t n = 1;
+    const Rect r0 = face_rect(0, nx, ny, a.per[0], a.per[1]), r1 = face_rect(1, nx, ny, a.per[0], a.per[1]);
     if (rect_count(r0) + rect_count(r1) > 0) {
         const int w = std::max(rect_empty(r0) ? 0 : r0.x1 - r0.x0 + 1, rect_empty(r1) ? 0 : r1.x1 - r1.x0 + 1);
         const int hh = std::max(rect_empty(r0) ? 0 : r0.y1 - r0.y0 + 1, rect_empty(r1) ? 0 : r1.y1 - r1.y0 + 1);
@@ -816,7 +821,7 @@ cudaError_t reverse_step(AdjParams<T> a, const dugks_t h, const void *state, dou
     }
     const int64_t ff = frame_count(r0) + frame_count(r1);
     if (ff > 0) {
-        adj_faces_frame<T><<<blocks_for(ff, 128), 128, 0, st>>>(a);
+        adj_faces_frame<T><<<blocks_for(ff, 64), 64, 0, st>>>(a);
         n++;
     }
     const Rect rc = cell_rect(nx, ny, a.per[0], a.per[1]);
@@ -826,7 +831,7 @@ cudaError_t reverse_step(AdjParams<T> a, const dugks_t h, const void *state, dou
     }
     const int64_t cf = frame_count(rc);
     if (cf > 0) {
-        adj_cells_frame<T><<<blocks_for(cf, 128), 128, 0, st>>>(a);
+        adj_cells_frame<T><<<blocks_for(cf, 64), 64, 0, st>>>(a);
         n++;
     }
     *launches += n;
