@@ -53,7 +53,11 @@ extern "C" {
 /* Storage of f~ in device memory. The stored quantity is the deviation from the rest
  * equilibrium, g~ = f~ - W_k rho0 (exact algebra: every linear step of the scheme has
  * coefficients summing to one or zero). F32, BF16 and F16 storage use FP32 arithmetic;
- * BF16/F16 round to nearest even on store. F64 storage uses FP64 arithmetic throughout. */
+ * F64 storage uses FP64 arithmetic throughout. BF16 stores g~ and F16 stores g~ * 2^12 (the
+ * exact scale keeps small deviations out of FP16's subnormal range), both with unbiased
+ * stochastic rounding (random bits from a hash of the address and the step), which keeps
+ * slowly varying values from accumulating a rounding bias or losing small increments.
+ * dugks_get_state / dugks_set_state move these raw stored values. */
 #define DUGKS_STORE_F32 0
 #define DUGKS_STORE_BF16 1
 #define DUGKS_STORE_F16 2

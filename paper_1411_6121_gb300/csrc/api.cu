@@ -283,6 +283,12 @@ int dugks_init(dugks_t h, const double *pres, const double *vel) {
     return DUGKS_OK;
 }
 
+// The device step counter is advanced by the kernels' launches when it is read: for a
+// time-dependent force (G(t)) and for 16-bit storage (the stochastic-rounding seed).
+static bool clock_on_device(const dugks_t h) {
+    return h->force.omega != 0.0 || h->store == DUGKS_STORE_BF16 || h->store == DUGKS_STORE_F16;
+}
+
 // Enqueue n steps starting from the current buffer (no graph).
 static int enqueue_steps(dugks_t h, int64_t n) {
     StepParams p = handle_params(h);
@@ -295,7 +301,7 @@ static int enqueue_steps(dugks_t h, int64_t n) {
         if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "step launch: %s", cudaGetErrorString(e));
         cur ^= 1;
     }
-    if (h->force.omega != 0.0) {  // the device clock only feeds G(t)
+    if (clock_on_device(h)) {  // the device clock feeds G(t) and the BF16 rounding seed
         cudaError_t e = launch_advance(h->d_step, (long long)n, h->stream);
         if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "advance: %s", cudaGetErrorString(e));
     }
@@ -330,7 +336,7 @@ int dugks_step(dugks_t h, int64_t n) {
             int rc = enqueue_steps(h, m);
             if (rc != DUGKS_OK) return rc;
         }
-        h->launches += m + (h->force.omega != 0.0 ? 1 : 0);
+        h->launches += m + (clock_on_device(h) ? 1 : 0);
         if (m & 1) h->cur ^= 1;
         h->step += m;
         left -= m;

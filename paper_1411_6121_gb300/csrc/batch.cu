@@ -254,6 +254,8 @@ int dugks_batch_create(int32_t count, const dugks_mesh *meshes, const double *nu
         b->elems += 9 * b->px.back() * meshes[i].ny;
         if (forces[i].omega != 0.0) b->timedep = true;
     }
+    // the device clock also seeds the stochastic rounding of 16-bit stores
+    if (o.store == DUGKS_STORE_BF16 || o.store == DUGKS_STORE_F16) b->timedep = true;
     b->stream = (cudaStream_t)o.stream;
     cudaError_t e = cudaSuccess;
     if (!b->stream) {

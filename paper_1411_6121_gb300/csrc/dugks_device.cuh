@@ -129,11 +129,50 @@ struct Store<double> {
     __device__ static __forceinline__ double ld(const double *p) { return __ldg(p); }
     __device__ static __forceinline__ void st(double *p, double v) { *p = v; }
 };
+// FP16 holds g~ * 2^12: the exact power-of-two scale moves FP16's normal range
+// [6.1e-5, 65504] to [1.5e-8, 16], so slowly developing flows (deviations of 1e-6 and less)
+// stay out of the subnormals while any physical deviation still fits.
+constexpr float F16_SCALE = 4096.0f, F16_UNSCALE = 1.0f / 4096.0f;
 template <>
 struct Store<__half> {
-    __device__ static __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
-    __device__ static __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+    __device__ static __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)) * F16_UNSCALE; }
+    __device__ static __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v * F16_SCALE); }
 };
+
+// BF16 keeps 8 significant bits and FP16 11. Rounded to nearest, a slowly varying stored
+// value makes nearly the same rounding error at every step, and those errors add up like a
+// bias; an increment below half a unit in the last place is lost at every step (a slowly
+// accelerating flow stagnates). The state stores therefore round both stochastically
+// (unbiased: up with probability equal to the discarded fraction), drawing the random bits
+// from a counter-based hash of the destination address and the step. The hash is the 32-bit
+// finalizer of MurmurHash3 (A. Appleby).
+__device__ __forceinline__ uint32_t mix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+// Seed of one step's stores (t: the step index).
+__device__ __forceinline__ uint32_t store_seed(long long t) { return mix32((uint32_t)t * 0x9e3779b9u + 0x7f4a7c15u); }
+
+// Stores a state value: round to nearest for FP32/FP64; stochastic rounding for BF16 and
+// FP16: random bits added below the kept significand of the FP32 pattern, then truncation
+// (BF16: 16 bits dropped; FP16: 13, within its normal range, which the 2^12 scale covers).
+template <class S>
+__device__ __forceinline__ void store_state(S *p, typename std::conditional<sizeof(S) == 8, double, float>::type v,
+                                            uint32_t seed) {
+    if constexpr (std::is_same<S, __nv_bfloat16>::value) {
+        const uint32_t r = mix32(seed ^ (uint32_t)((uintptr_t)p >> 1)) & 0xffffu;
+        *p = __ushort_as_bfloat16((unsigned short)((__float_as_uint(v) + r) >> 16));
+    } else if constexpr (std::is_same<S, __half>::value) {
+        const uint32_t r = mix32(seed ^ (uint32_t)((uintptr_t)p >> 1)) & 0x1fffu;
+        *p = __float2half_rz(__uint_as_float(__float_as_uint(v * F16_SCALE) + r));
+    } else {
+        Store<S>::st(p, v);
+    }
+}
 
 // Arithmetic type for a storage type: FP32 for FP32/BF16/F16 storage, FP64 for FP64.
 template <class S>

@@ -144,6 +144,8 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
     const S *src = reinterpret_cast<const S *>(p.src);
     S *dst = reinterpret_cast<S *>(p.dst);
 
+    uint32_t seed = 0;  // stochastic rounding of 16-bit stores
+    if constexpr (sizeof(S) == 2) seed = store_seed(*p.step_ctr + p.step_off);
     // time factors of G(t) (reading: cells at t_n, interfaces at t_n + h), over c
     T ct = (T)p.inv_c, cth = (T)p.inv_c;
     if (p.omega != 0.0) {
@@ -373,7 +375,7 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
                 const T gold = (T)Store<S>::ld(src + k * p.dstride + off);
                 // eq. f_tilde_+ in increment form: 4/3 fbar+ - 1/3 f~ = fbar+ + (fbar+ - f~)/3
                 const T v = fmaT(T(1) / T(3), ph[k] - gold, ph[k]) - cf.two_kappa * acc;
-                Store<S>::st(dst + k * p.dstride + off, v);
+                store_state<S>(dst + k * p.dstride + off, v, seed);
             });
         }
         if constexpr (D == 3) {

@@ -239,6 +239,8 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
     const bool ycol = lane >= 1 && lane <= K::TXI && gx >= 0 && gx < nx && gy >= -1 && gy <= ny;
     const bool need_y = ycol && row <= K::TYI && gy < ny;
 
+    uint32_t seed = 0;  // stochastic rounding of 16-bit stores
+    if constexpr (sizeof(S) == 2) seed = store_seed(*p.step_ctr + p.step_off);
     float ct = (float)p.inv_c, cth = (float)p.inv_c;
     if (FORCE && p.omega != 0.0) {
         const double tn = ((double)(*p.step_ctr) + (double)p.step_off) * p.dt;
@@ -611,7 +613,7 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
                     acc = fmaf((float)Lat<Q>::e(k, 2), fzp[i] - fzm[i], acc);
                 }
                 // eq. evolution_equation: f~(t+dt) = f~+ - dt/|V| flux
-                Store<S>::st(dst + k * p.dstride + off, fmaf(-cf.two_kappa, acc, u0[k]));
+                store_state<S>(dst + k * p.dstride + off, fmaf(-cf.two_kappa, acc, u0[k]), seed);
             });
 #pragma unroll
             for (int i = 0; i < NF; i++) { fzm[i] = fzp[i]; alz[i] = alzn[i]; }

@@ -223,7 +223,7 @@ class Sim:
 
     def get_state(self, out=None):
         """Raw stored deviation g~ = f~ - W rho0, [Q][ncell] in the storage type (bf16 as
-        uint16 bit patterns on the host)."""
+        uint16 bit patterns on the host; f16 holds g~ * 2^12)."""
         nb = self.state_bytes()
         if out is not None:
             _check(self.lib.dugks_get_state(self.h, C.c_void_p(out.data_ptr()), nb, 1), self.h)

@@ -11,7 +11,8 @@ Tolerances:
     flows round coherently, so the error grows about linearly with the step count:
     n * 2^-24 * (a few) ~ 2e-5 after 1000 steps bounds it (measured 1.6e-6 to 1.3e-5);
     element-wise after 20 steps: 2e-6 of the state's scale.
-  * F16 deviation storage (11 significant bits): velocity within 1e-3 after 1000 steps.
+  * F16 / BF16 deviation storage (11 / 8 significant bits, stochastic rounding): F16 within
+    1e-3 after 1000 steps; BF16 at the level its 8 bits allow (2e-3 to 6e-3, stated per test).
 """
 import numpy as np
 import pytest
@@ -154,21 +155,62 @@ def test_d3q19_cavity_1000_steps():
     o.init()
     o.step(1000)
     ref = o.moments()
-    for store, tol in ((3, 1e-6), (0, 2e-5), (2, 1e-3)):  # F16: pressure to 5e-3 (below)
-        s = _sim(store=store, **cfg)
+    # 16-bit storage (stochastic rounding), both kernels: F16 (measured u 2.2e-4, p 9.9e-4),
+    # BF16 (8 significant bits; measured u 1.8e-3, p 7.7e-3)
+    for store, kernel, tol, ptol in ((3, 0, 1e-6, 1e-6), (0, 0, 2e-5, 2e-5), (2, 0, 1e-3, 2e-3), (2, 1, 1e-3, 2e-3),
+                                     (1, 0, 3e-3, 1.5e-2), (1, 1, 3e-3, 1.5e-2)):
+        s = _sim(store=store, kernel=kernel, **cfg)
         s.init()
         s.step(1000)
         got = s.moments()
-        assert rel_l2(got[1:], ref[1:]) < tol, (store, rel_l2(got[1:], ref[1:]))
-        ptol = 5e-3 if store == 2 else max(tol, 2e-5)  # F16 resolves drho = sum g~ to ~1e-3
-        assert rel_l2(got[0], ref[0]) < ptol, (store, rel_l2(got[0], ref[0]))
+        assert rel_l2(got[1:], ref[1:]) < tol, (store, kernel, rel_l2(got[1:], ref[1:]))
+        assert rel_l2(got[0], ref[0]) < ptol, (store, kernel, rel_l2(got[0], ref[0]))
 
 
-def test_f16_storage():
+def test_16bit_storage_2d_cavity():
+    """F16 within 1e-3 of the oracle after 1000 steps (measured 4.5e-4); BF16 at its
+    8-bit level (measured 3.3e-3)."""
     cfg = dict(shape=(45, 38), q=9, nu=0.05, dt=0.5, bcs=W.cavity_bcs(2, 0.1))
-    o, s = run_pair(cfg, 1000, store=2)
-    ref, got = o.moments(), s.moments()
-    assert rel_l2(got[1:], ref[1:]) < 1e-3
+    o = Oracle(**cfg)
+    o.init()
+    o.step(1000)
+    ref = o.moments()
+    for store, tol in ((2, 1e-3), (1, 6e-3)):
+        s = _sim(store=store, **cfg)
+        s.init()
+        s.step(1000)
+        assert rel_l2(s.moments()[1:], ref[1:]) < tol, store
+
+
+def test_16bit_storage_does_not_stagnate():
+    """A force-driven channel accelerates by ~5e-6 per stored value per step, below half an
+    FP16 unit in the last place of the values around it: rounded to nearest, FP16 storage
+    would lose the increment every step. With stochastic rounding the steady Poiseuille
+    profile is reached: velocity within 1e-3 (F16) / 1e-2 (BF16) of the oracle, and the
+    error against the analytic parabola G y (H - y) / (2 nu) within 10% (F16) / 40% (BF16) of
+    the FP32 run's."""
+    cfg = dict(shape=(8, 32), q=9, nu=0.1, dt=0.5, g=(1e-4, 0.0, 0.0), bcs=W.channel_bcs(2))
+    steps, H = 40000, 32
+    o = Oracle(**cfg)
+    o.init()
+    o.step(steps)
+    ref = o.moments()
+    y = np.arange(H) + 0.5
+    ua = 1e-4 * y * (H - y) / (2 * 0.1)
+
+    def run(store):
+        s = _sim(store=store, **cfg)
+        s.init()
+        s.step(steps)
+        m = s.moments()
+        ux = m[1].reshape(H, 8).mean(axis=1)
+        return m, np.linalg.norm(ux - ua) / np.linalg.norm(ua)
+
+    _, e32 = run(0)
+    for store, tol, band in ((2, 1e-3, 0.10), (1, 1e-2, 0.40)):
+        m, e = run(store)
+        assert rel_l2(m[1:], ref[1:]) < tol, (store, rel_l2(m[1:], ref[1:]))
+        assert abs(e - e32) < band * e32, (store, e, e32)
 
 
 def test_residual_and_totals_fp64():
