@@ -157,18 +157,30 @@ __device__ __forceinline__ uint32_t mix32(uint32_t h) {
 // Seed of one step's stores (t: the step index).
 __device__ __forceinline__ uint32_t store_seed(long long t) { return mix32((uint32_t)t * 0x9e3779b9u + 0x7f4a7c15u); }
 
+// Random bits for the stores of one cell: a 32-bit word per pair of velocities, hashed from
+// the step seed and the cell's element offset; velocity k takes the low (k even) or the
+// high (k odd) half.
+struct CellRandom {
+    uint32_t base;
+    __device__ __forceinline__ CellRandom(uint32_t seed, int64_t cell) : base(mix32(seed ^ (uint32_t)cell)) {}
+    template <int k>
+    __device__ __forceinline__ uint32_t bits() const {
+        const uint32_t h = mix32(base + (uint32_t)(k >> 1));
+        return (k & 1) ? (h >> 16) : h;
+    }
+};
+
 // Stores a state value: round to nearest for FP32/FP64; stochastic rounding for BF16 and
-// FP16: random bits added below the kept significand of the FP32 pattern, then truncation
-// (BF16: 16 bits dropped; FP16: 13, within its normal range, which the 2^12 scale covers).
+// FP16 with the random bits r: they are added below the kept significand of the FP32
+// pattern, then the pattern is truncated (BF16: 16 bits dropped; FP16: 13, within its
+// normal range, which the 2^12 scale covers).
 template <class S>
 __device__ __forceinline__ void store_state(S *p, typename std::conditional<sizeof(S) == 8, double, float>::type v,
-                                            uint32_t seed) {
+                                            uint32_t r) {
     if constexpr (std::is_same<S, __nv_bfloat16>::value) {
-        const uint32_t r = mix32(seed ^ (uint32_t)((uintptr_t)p >> 1)) & 0xffffu;
-        *p = __ushort_as_bfloat16((unsigned short)((__float_as_uint(v) + r) >> 16));
+        *p = __ushort_as_bfloat16((unsigned short)((__float_as_uint(v) + (r & 0xffffu)) >> 16));
     } else if constexpr (std::is_same<S, __half>::value) {
-        const uint32_t r = mix32(seed ^ (uint32_t)((uintptr_t)p >> 1)) & 0x1fffu;
-        *p = __float2half_rz(__uint_as_float(__float_as_uint(v * F16_SCALE) + r));
+        *p = __float2half_rz(__uint_as_float(__float_as_uint(v * F16_SCALE) + (r & 0x1fffu)));
     } else {
         Store<S>::st(p, v);
     }

@@ -357,6 +357,7 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
             const T *ph = cellp(s, ly + 1, lx + 1);
             const T *xm = xf + (ly * (TX + 1) + lx) * K::SX, *xp = xm + K::SX;
             const T *ym = yf + (ly * TX + lx) * K::SY, *yp = ym + TX * K::SY;
+            const CellRandom rnd(seed, off);
             sfor<Q>([&](auto kc) {
                 constexpr int k = kc;
                 T acc = T(0);
@@ -375,7 +376,7 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
                 const T gold = (T)Store<S>::ld(src + k * p.dstride + off);
                 // eq. f_tilde_+ in increment form: 4/3 fbar+ - 1/3 f~ = fbar+ + (fbar+ - f~)/3
                 const T v = fmaT(T(1) / T(3), ph[k] - gold, ph[k]) - cf.two_kappa * acc;
-                store_state<S>(dst + k * p.dstride + off, v, seed);
+                store_state<S>(dst + k * p.dstride + off, v, sizeof(S) == 2 ? rnd.bits<k>() : 0u);
             });
         }
         if constexpr (D == 3) {

@@ -597,6 +597,7 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
             const float *ym = xf + ((row - 1) * 32 + lane) * K::FS;
             const float *u0 = US(kz);
             const int64_t off = (int64_t)kz * p.plane + (int64_t)gy * p.px + gx;
+            const CellRandom rnd(seed, off);
             sfor<Q>([&](auto kc) {
                 constexpr int k = kc;
                 float acc = 0.0f;
@@ -613,7 +614,8 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
                     acc = fmaf((float)Lat<Q>::e(k, 2), fzp[i] - fzm[i], acc);
                 }
                 // eq. evolution_equation: f~(t+dt) = f~+ - dt/|V| flux
-                store_state<S>(dst + k * p.dstride + off, fmaf(-cf.two_kappa, acc, u0[k]), seed);
+                store_state<S>(dst + k * p.dstride + off, fmaf(-cf.two_kappa, acc, u0[k]),
+                               sizeof(S) == 2 ? rnd.bits<k>() : 0u);
             });
 #pragma unroll
             for (int i = 0; i < NF; i++) { fzm[i] = fzp[i]; alz[i] = alzn[i]; }
