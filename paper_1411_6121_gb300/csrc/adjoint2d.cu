@@ -634,20 +634,13 @@ __device__ __forceinline__ T face_G_T(const AdjParams<T> &a, int comp, int x, in
     return s;
 }
 
+// The t-th frame cell (cells whose stencil meets a wall ghost, a periodic image or a
+// wall-clamped interface acceleration).
 template <class T>
-__global__ void __launch_bounds__(128, 4) adj_cells_fast(const AdjParams<T> a) {
-    const Rect r = cell_rect(a.n[0], a.n[1], a.per[0], a.per[1]);
-    const int x = r.x0 + blockIdx.x * blockDim.x + threadIdx.x, y = r.y0 + blockIdx.y * blockDim.y + threadIdx.y;
-    if (x > r.x1 || y > r.y1) return;
-    cell_fast(a, x, y, x + (int64_t)a.n[0] * y);
-}
-
-template <class T>
-__global__ void __launch_bounds__(64) adj_cells_frame(const AdjParams<T> a) {
+__device__ __noinline__ void cells_frame_item(const AdjParams<T> &a, int64_t t) {
     const int64_t nc = ncell(a);
     const Rect r = cell_rect(a.n[0], a.n[1], a.per[0], a.per[1]);
-    const int64_t ntot = frame_count(r);
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntot; t += (int64_t)gridDim.x * blockDim.x) {
+    {
         int x, y;
         frame_at(r, t, x, y);
         const int64_t c = x + (int64_t)a.n[0] * y;
@@ -681,6 +674,23 @@ __global__ void __launch_bounds__(64) adj_cells_frame(const AdjParams<T> a) {
             }
         }
     }
+}
+
+// All cells in one launch of 128-thread blocks: frame blocks first, then 32 x 4 tiles of the
+// fast rectangle (tx x ty blocks).
+template <class T>
+__global__ void __launch_bounds__(128) adj_cells_all(const AdjParams<T> a, int nfb, int tx, int ty) {
+    if ((int)blockIdx.x < nfb) {
+        const Rect r = cell_rect(a.n[0], a.n[1], a.per[0], a.per[1]);
+        const int64_t t = (int64_t)blockIdx.x * 128 + threadIdx.x;
+        if (t < frame_count(r)) cells_frame_item(a, t);
+        return;
+    }
+    const int b = blockIdx.x - nfb;
+    const Rect r = cell_rect(a.n[0], a.n[1], a.per[0], a.per[1]);
+    const int x = r.x0 + (b % tx) * 32 + (threadIdx.x & 31), y = r.y0 + (b / tx) * 4 + (threadIdx.x >> 5);
+    if (x > r.x1 || y > r.y1) return;
+    cell_fast(a, x, y, x + (int64_t)a.n[0] * y);
 }
 
 // Loss seed from dL/d(moments) [3][ncell] (p, u_x, u_y as dugks_moments returns them):
@@ -797,7 +807,7 @@ AdjParams<T> base_params(const dugks_t h, const AdjBufs &B) {
 }
 
 // One reverse step at the state g~^n held in `state` (t_n = tn): lambda' in lam1 -> lam0.
-// Five launches: cell recompute, interior and frame interfaces, interior and frame cells.
+// Four launches: cell recompute, interior and frame interfaces, all cells (frame blocks first).
 template <class T>
 cudaError_t reverse_step(AdjParams<T> a, const dugks_t h, const void *state, double tn, const void *lam1,
                          void *lam0, int64_t *launches) {
@@ -824,15 +834,15 @@ cudaError_t reverse_step(AdjParams<T> a, const dugks_t h, const void *state, dou
         adj_faces_frame<T><<<blocks_for(ff, 64), 64, 0, st>>>(a);
         n++;
     }
-    const Rect rc = cell_rect(nx, ny, a.per[0], a.per[1]);
-    if (rect_count(rc) > 0) {
-        adj_cells_fast<T><<<dim3((rc.x1 - rc.x0 + 32) / 32, (rc.y1 - rc.y0 + 4) / 4), dim3(32, 4), 0, st>>>(a);
-        n++;
-    }
-    const int64_t cf = frame_count(rc);
-    if (cf > 0) {
-        adj_cells_frame<T><<<blocks_for(cf, 64), 64, 0, st>>>(a);
-        n++;
+    {
+        const Rect rc = cell_rect(nx, ny, a.per[0], a.per[1]);
+        const int tx = rect_empty(rc) ? 0 : (rc.x1 - rc.x0 + 32) / 32, ty = rect_empty(rc) ? 0 : (rc.y1 - rc.y0 + 4) / 4;
+        const int nfb = (int)((frame_count(rc) + 127) / 128);
+        const int nb = nfb + tx * ty;
+        if (nb > 0) {
+            adj_cells_all<T><<<nb, 128, 0, st>>>(a, nfb, tx, ty);
+            n++;
+        }
     }
     *launches += n;
     return cudaGetLastError();
