@@ -102,7 +102,10 @@ typedef struct {
     int32_t store;          /* DUGKS_STORE_* (default F32)                           */
     void *stream;           /* cudaStream_t to run on (default NULL: own stream)     */
     int32_t use_graph;      /* 1: dugks_step replays a captured CUDA graph (default) */
-    int32_t tile_x, tile_y; /* 0: autotuned/default tile; else the fused kernel tile */
+    int32_t tile_x, tile_y; /* 0: default tile. Throughput kernels (kernel 0, F32/BF16/F16
+                               storage): tile_y = thread-block rows (D2Q9: 4, 8 or 16;
+                               D3Q19: 8 or 10; default 8), tile_x ignored. Reference
+                               kernel: tile_x x tile_y = 32x8 or 16x8                   */
     int32_t kernel;         /* 0: fastest kernel built for the case (default);
                                1: the reference fused kernel (any lattice/storage)     */
 } dugks_opts;
@@ -215,7 +218,9 @@ int dugks_adjoint_wall(dugks_t h, double *dL_dwall);
  * captured CUDA graph. The per-instance scheme is exactly that of dugks_step (Appendix
  * steps 1-10 of the paper). meshes/nu/forces/bcs: HOST arrays of `count` records (a force
  * field pointer, if any, is a DEVICE [2][ncell] float array read at every step). opts may
- * be NULL; opts->tile_x/tile_y pick the tile (32x8, 16x8, 32x4 or 64x4), else 32x8.
+ * be NULL; opts->tile_x/tile_y pick the tile: 30x2, 30x6 or 30x14 inner cells of the throughput
+ * kernel (32 x 4, 8 or 16 threads; F32/BF16/F16), or 32x8, 16x8, 32x4 or 64x4 of the reference
+ * kernel; default 30x6.
  * Errors as for the single-instance calls; dugks_batch_last_error(b) gives the reason
  * (NULL b: the last failed dugks_batch_create in this thread). */
 typedef struct dugks_batch_s *dugks_batch_t;

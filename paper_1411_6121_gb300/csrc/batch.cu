@@ -4,8 +4,9 @@
 // time step, RT, rho0 and the storage type. One time step of the whole batch is one
 // persistent launch (fused_step_batch) that walks a work list of (instance, tile) items,
 // largest instances first; dugks_batch_step replays n such launches as a captured CUDA
-// graph. The tile shape comes from a timing autotuner (dugks_batch_tune) whose choice is
-// cached per (instance sizes, storage, SM count).
+// graph. The tile body is that of the D2Q9 throughput kernel (dugks_step2d.cuh) or of the
+// reference kernel (dugks_step.cuh); the tile comes from a timing autotuner
+// (dugks_batch_tune) whose choice is cached per (instance sizes, storage, SM count).
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -43,6 +44,7 @@ struct dugks_batch_s {
     long long *d_step = nullptr;
     int64_t step = 0;
     bool timedep = false;
+    bool anyforce = false;  // some instance has an acceleration (uniform or field)
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int grid = 0;
@@ -97,6 +99,11 @@ cudaError_t launch_batch_s(const dugks_batch_t b, int parity) {
 }
 
 cudaError_t launch_batch(const dugks_batch_t b, int parity) {
+    // throughput tiles: 30 x (ry - 2) inner cells (dugks_step2d.cuh)
+    if (b->tx == 30) {
+        const int ry = b->ty + 2;
+        return launch_step2d_batch(b->d_params, b->d_items, b->nitems, parity, b->store, ry, b->anyforce, b->stream);
+    }
     switch (b->store) {
         case DUGKS_STORE_F32: return launch_batch_s<float>(b, parity);
         case DUGKS_STORE_BF16: return launch_batch_s<__nv_bfloat16>(b, parity);
@@ -106,7 +113,8 @@ cudaError_t launch_batch(const dugks_batch_t b, int parity) {
 }
 
 bool tile_supported(int tx, int ty) {
-    return (tx == 32 && ty == 8) || (tx == 16 && ty == 8) || (tx == 32 && ty == 4) || (tx == 64 && ty == 4);
+    return (tx == 32 && ty == 8) || (tx == 16 && ty == 8) || (tx == 32 && ty == 4) || (tx == 64 && ty == 4) ||
+           (tx == 30 && (ty == 2 || ty == 6 || ty == 14));
 }
 
 StepParams instance_params(const dugks_batch_t b, int i, int parity) {
@@ -231,7 +239,7 @@ int dugks_batch_create(int32_t count, const dugks_mesh *meshes, const double *nu
                 return bfail(nullptr, DUGKS_E_INVAL, "instance %d: bad boundaries on axis %d", i, d);
         }
     }
-    int tx = o.tile_x ? o.tile_x : 32, ty = o.tile_y ? o.tile_y : 8;
+    int tx = o.tile_x ? o.tile_x : 30, ty = o.tile_y ? o.tile_y : 6;  // default: the throughput tile
     if (!tile_supported(tx, ty)) return bfail(nullptr, DUGKS_E_UNSUPPORTED, "batch tile %dx%d not built", tx, ty);
     dugks_batch_t b = new (std::nothrow) dugks_batch_s();
     if (!b) return bfail(nullptr, DUGKS_E_NOMEM, "host allocation failed");
@@ -253,6 +261,7 @@ int dugks_batch_create(int32_t count, const dugks_mesh *meshes, const double *nu
         b->off.push_back(b->elems);
         b->elems += 9 * b->px.back() * meshes[i].ny;
         if (forces[i].omega != 0.0) b->timedep = true;
+        if (forces[i].field || forces[i].g[0] != 0.0 || forces[i].g[1] != 0.0) b->anyforce = true;
     }
     // the device clock also seeds the stochastic rounding of 16-bit stores
     if (o.store == DUGKS_STORE_BF16 || o.store == DUGKS_STORE_F16) b->timedep = true;
@@ -419,7 +428,7 @@ int dugks_batch_tune(dugks_batch_t b, int32_t *tile_x, int32_t *tile_y) {
     BTRY(b, cudaMemcpyAsync(save, b->buf[b->cur], bytes, cudaMemcpyDeviceToDevice, b->stream));
     BTRY(b, cudaMemcpyAsync(&clock, b->d_step, sizeof clock, cudaMemcpyDeviceToHost, b->stream));
     BTRY(b, cudaStreamSynchronize(b->stream));
-    const int cand[4][2] = {{32, 8}, {16, 8}, {32, 4}, {64, 4}};
+    const int cand[7][2] = {{30, 6}, {30, 14}, {30, 2}, {32, 8}, {16, 8}, {32, 4}, {64, 4}};
     float best = 1e30f;
     int bx = b->tx, by = b->ty;
     cudaEvent_t e0, e1;

@@ -195,6 +195,20 @@ struct Arith<double> { using T = double; };
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
 
+// Sums of products written as explicit fused multiply-adds: left to the compiler, an
+// expression like a*a + b*b may be contracted differently in two instantiations of the same
+// code (e.g. with and without the force term), and the bits of a step would then depend on
+// the instantiation. v.v over the first D components and the ghost value 2 a - b (step 2).
+template <int D, class T>
+__device__ __forceinline__ T dotD(const T u[3], const T v[3]) {
+    return D == 3 ? fmaT(u[0], v[0], fmaT(u[1], v[1], u[2] * v[2])) : fmaT(u[0], v[0], u[1] * v[1]);
+}
+template <class T>
+__device__ __forceinline__ T ghost_value(T a, T b) { return fmaT(T(2), a, -b); }
+// A product rounded on its own (never fused into a later addition).
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // ---------------------------------------------------------------------------------
 // Parameters of one fused step launch (coefficients precomputed on the host in double;
 // the kernel rounds them once to its arithmetic type).
@@ -306,9 +320,9 @@ template <int Q, class T, bool FORCE = true>
 __device__ __forceinline__ void relax(const T g[Q], T drho, const T m[3], const T rGh[3], T rho0, T inv_rho0, T b,
                                       T c, T out[Q]) {
     constexpr int D = Lat<Q>::D;
-    const T mm = m[0] * m[0] + m[1] * m[1] + (D == 3 ? m[2] * m[2] : T(0));
+    const T mm = dotD<D, T>(m, m);
     T gm = T(0);
-    if constexpr (FORCE) gm = (rGh[0] * m[0] + rGh[1] * m[1] + (D == 3 ? rGh[2] * m[2] : T(0))) * inv_rho0;
+    if constexpr (FORCE) gm = dotD<D, T>(rGh, m) * inv_rho0;
     const T base = fmaT(T(-1.5) * inv_rho0, mm, drho);
     const T c45 = T(4.5) * inv_rho0;
     sfor<Q>([&](auto kc) {

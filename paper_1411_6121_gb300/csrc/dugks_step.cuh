@@ -52,7 +52,7 @@ __device__ __forceinline__ void reconstruct(const T *L, const T *R, const T *L1m
 #pragma unroll
     for (int k = 0; k < Q; k++) {
         const T l = L[k], r = R[k];
-        T v = T(0.5) * (l + r);
+        T v = mul_rn(T(0.5), l + r);
         if (Lat<Q>::e(k, d) != 0) v = fmaT(-kappa * (T)Lat<Q>::e(k, d), r - l, v);
         if (Lat<Q>::e(k, t1) != 0) v = fmaT(-qk * (T)Lat<Q>::e(k, t1), (L1p[k] + R1p[k]) - (L1m[k] + R1m[k]), v);
         if (D == 3 && Lat<Q>::e(k, t2) != 0)
@@ -86,8 +86,8 @@ __device__ __forceinline__ void interface_f(const StepParams &p, const Coef<T> &
             dra = (T)p.bc_drho[wid];
             ma[0] = mc[0]; ma[1] = mc[1]; ma[2] = mc[2];
         }
-        const T mma = ma[0] * ma[0] + ma[1] * ma[1] + (D == 3 ? ma[2] * ma[2] : T(0));
-        const T mmc = mc[0] * mc[0] + mc[1] * mc[1] + (D == 3 ? mc[2] * mc[2] : T(0));
+        const T mma = dotD<D, T>(ma, ma);
+        const T mmc = dotD<D, T>(mc, mc);
         const int sgn = side == 0 ? -1 : 1;
 #pragma unroll
         for (int k = 0; k < Q; k++) {
@@ -198,7 +198,7 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
                 T *o = cellp(slot, ry, rx);
                 const T *a = cellp(slot, ry, rx + s1), *b = cellp(slot, ry, rx + 2 * s1);
 #pragma unroll
-                for (int k = 0; k < Q; k++) o[k] = T(2) * a[k] - b[k];
+                for (int k = 0; k < Q; k++) o[k] = ghost_value(a[k], b[k]);
             }
         }
         if (ywall) {
@@ -213,7 +213,7 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
                 T *o = cellp(slot, ry, rx);
                 const T *a = cellp(slot, ry + s1, rx), *b = cellp(slot, ry + 2 * s1, rx);
 #pragma unroll
-                for (int k = 0; k < Q; k++) o[k] = T(2) * a[k] - b[k];
+                for (int k = 0; k < Q; k++) o[k] = ghost_value(a[k], b[k]);
             }
         }
     };
@@ -221,7 +221,8 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
     auto ghost_plane = [&](int pz) __attribute__((always_inline)) {
         const int s = slot_of(pz);
         const int sa = slot_of(pz < 0 ? 0 : nz - 1), sb = slot_of(pz < 0 ? 1 : nz - 2);
-        for (int i = tid; i < K::PLANE; i += NT) phi[s * K::PLANE + i] = T(2) * phi[sa * K::PLANE + i] - phi[sb * K::PLANE + i];
+        for (int i = tid; i < K::PLANE; i += NT)
+            phi[s * K::PLANE + i] = ghost_value(phi[sa * K::PLANE + i], phi[sb * K::PLANE + i]);
     };
     auto plane = [&](int pz) __attribute__((always_inline)) {  // real or periodic planes only
         make_plane(pz);

@@ -134,8 +134,8 @@ __device__ __forceinline__ void face_parts(const float *ph, const float *m, cons
                 alpha[i] = fmaf(fmaf(kappa, ed, 0.5f), f, gam);
                 beta[i] = fmaf(fmaf(-kappa, ed, 0.5f), f, gam);
             } else {
-                alpha[i] = fmaf(kappa, ed, 0.5f) * f;
-                beta[i] = fmaf(-kappa, ed, 0.5f) * f;
+                alpha[i] = mul_rn(fmaf(kappa, ed, 0.5f), f);
+                beta[i] = mul_rn(fmaf(-kappa, ed, 0.5f), f);
             }
         }
     });
@@ -150,10 +150,10 @@ __device__ __forceinline__ void face_relax(const Coef<float> &cf, const float *F
     float m[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) m[a] = FORCE ? fmaf(Gh[a], cf.wface * cf.rho0, j[a]) : j[a];
-    const float mm = m[0] * m[0] + m[1] * m[1] + m[2] * m[2];
+    const float mm = dotD<3, float>(m, m);
     const float base = fmaf(-1.5f * cf.inv_rho0, mm, drho);
     float gm = 0.0f;
-    if (FORCE) gm = (Gh[0] * m[0] + Gh[1] * m[1] + Gh[2] * m[2]) * cf.inv_rho0;
+    if (FORCE) gm = dotD<3, float>(Gh, m) * cf.inv_rho0;
     const float c45 = 4.5f * cf.inv_rho0;
     sfor<Q>([&](auto kc) {
         constexpr int k = kc;
@@ -170,7 +170,7 @@ __device__ __forceinline__ void face_relax(const Coef<float> &cf, const float *F
             // interface values need no conservation-exact form (the same value is used by
             // both cells, so the flux telescopes exactly whatever its rounding)
             const float q = fmaf(c45 * em, em, base);
-            const float geq = w * fmaf(em, 3.0f, q), geqb = w * fmaf(em, -3.0f, q);
+            const float geq = mul_rn(w, fmaf(em, 3.0f, q)), geqb = mul_rn(w, fmaf(em, -3.0f, q));
             float v = fmaf(cf.b7, geq - F[i], F[i]), vb = fmaf(cf.b7, geqb - F[ib], F[ib]);
             if (FORCE) {
                 v = fmaf(cf.c7 * 3.0f * (ge - gm), fmaf(w, cf.rho0, geq), v);
@@ -344,7 +344,7 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
                 float *o = R(s, row, lane);
                 const float *a = R(s, row, lane + d1), *b = R(s, row, lane + 2 * d1);
 #pragma unroll
-                for (int k = 0; k < CS; k++) o[k] = 2.0f * a[k] - b[k];
+                for (int k = 0; k < CS; k++) o[k] = ghost_value(a[k], b[k]);
             }
         }
         if (ywall_tile) {
@@ -354,7 +354,7 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
                 float *o = R(s, row, lane);
                 const float *a = R(s, row + d1, lane), *b = R(s, row + 2 * d1, lane);
 #pragma unroll
-                for (int k = 0; k < CS; k++) o[k] = 2.0f * a[k] - b[k];
+                for (int k = 0; k < CS; k++) o[k] = ghost_value(a[k], b[k]);
             }
         }
     };
@@ -363,7 +363,7 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
         const float *a = R(slot_of(pz < 0 ? 0 : nz - 1), row, lane);
         const float *b = R(slot_of(pz < 0 ? 1 : nz - 2), row, lane);
 #pragma unroll
-        for (int k = 0; k < CS; k++) o[k] = 2.0f * a[k] - b[k];
+        for (int k = 0; k < CS; k++) o[k] = ghost_value(a[k], b[k]);
     };
 
     // direct path for one interface (walls, chunk start): all velocities from the ring,

@@ -26,10 +26,16 @@ def _instances():
     ]
 
 
-def _single(ins, steps, p, u, tile):
+def _single(ins, steps, p, u, batch_tile):
+    """The instance alone, through the single-instance API with the same tile body: the
+    throughput kernel (batch tiles 30 x (rows - 2)) or the reference kernel."""
     from paper_1411_6121_gb300 import dugks
     kw = {k: v for k, v in ins.items()}
-    s = dugks.Sim(q=9, dt=0.5, tile=tile, kernel=1, **kw)
+    tx, ty = batch_tile
+    if tx == 30:
+        s = dugks.Sim(q=9, dt=0.5, tile=(32, ty + 2), kernel=0, **kw)
+    else:
+        s = dugks.Sim(q=9, dt=0.5, tile=(16, 8) if (tx, ty) == (16, 8) else (32, 8), kernel=1, **kw)
     s.init(p=p, u=u)
     s.step(steps)
     m = s.moments()
@@ -37,10 +43,11 @@ def _single(ins, steps, p, u, tile):
     return m
 
 
-def test_batch_matches_single_instances_and_oracle():
+@pytest.mark.parametrize("tile", [(30, 6), (30, 14), (30, 2), (32, 8), (64, 4)])
+def test_batch_matches_single_instances_and_oracle(tile):
     from paper_1411_6121_gb300 import dugks
     ins = _instances()
-    b = dugks.Batch(ins, dt=0.5, tile=(32, 8))
+    b = dugks.Batch(ins, dt=0.5, tile=tile)
     fields = []
     for i, d in enumerate(ins):
         p, u = W.random_state_fields(d["shape"], seed=10 + i, u_amp=0.02, p_amp=1e-4)
@@ -50,8 +57,8 @@ def test_batch_matches_single_instances_and_oracle():
     b.step(57)
     for i, d in enumerate(ins):
         got = b.moments(i)
-        ref = _single(d, 60, *fields[i], tile=(32, 8))
-        assert np.array_equal(got, ref), i
+        ref = _single(d, 60, *fields[i], tile)
+        assert np.array_equal(got, ref), (tile, i)
     # two instances against the oracle
     for i in (0, 3):
         d = ins[i]
@@ -75,7 +82,7 @@ def test_batch_tuner_restores_state():
     b.step(10)
     before = [b.moments(i) for i in range(len(ins))]
     tx, ty = b.tune()
-    assert (tx, ty) in [(32, 8), (16, 8), (32, 4), (64, 4)]
+    assert (tx, ty) in [(30, 6), (30, 14), (30, 2), (32, 8), (16, 8), (32, 4), (64, 4)]
     after = [b.moments(i) for i in range(len(ins))]
     for x, y in zip(before, after):
         assert np.array_equal(x, y)
@@ -83,7 +90,7 @@ def test_batch_tuner_restores_state():
     b.step(20)
     for i in range(len(ins)):
         p, u = W.random_state_fields(ins[i]["shape"], seed=20 + i, u_amp=0.02, p_amp=1e-4)
-        ref = _single(ins[i], 30, p, u, tile=(32, 8) if (tx, ty) not in [(16, 8)] else (16, 8))
+        ref = _single(ins[i], 30, p, u, (tx, ty))
         got = b.moments(i)
-        assert np.allclose(got, ref, rtol=1e-6, atol=1e-9)
+        assert np.array_equal(got, ref), ((tx, ty), i)
     b.close()
