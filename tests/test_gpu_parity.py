@@ -88,7 +88,7 @@ def test_d2q9_1000_steps(name):
     s64 = _sim(store=3, **cfg)
     s64.init()
     s64.step(1000)
-    # FP64 path: state element-wise and moments at the spec bar (1e-6)
+    # FP64 path: state element-wise and moments within relative L2 1e-6
     d = np.abs(state_f64(s64) - state_dev(o)).max() / np.abs(state_dev(o)).max()
     assert d < 1e-10, d
     got = s64.moments()
