@@ -369,6 +369,50 @@ def run_adjoint(torch, dev, count=64):
                     "transposed steps, per instance on its own stream, all instances concurrently"}
 
 
+def run_case(torch, case, size, steps, warmup, dev):
+    """One workload alone, for profiling (prints its own short JSON line, not the benchmark
+    line). `cavity2d`: the D2Q9 lid-driven cavity of size x size cells at Re = 1000, FP32
+    storage, `steps` timed steps after `warmup`, no graph (one launch per step). `adjoint`: the
+    largest of the 64 uneven channels with a per-cell force field, `steps` recorded steps with
+    a checkpoint every 10, then one reverse sweep, timed with CUDA events."""
+    from paper_1411_6121_gb300 import dugks
+    from paper_1411_6121_gb300 import workloads as W
+    st = torch.cuda.Stream(device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if case == "cavity2d":
+        cfg = W.cavity2d(n=size, re=RE)
+        s = dugks.Sim(store=dugks.STORE_F32, stream=st.cuda_stream, use_graph=False, **cfg)
+        s.init()
+        s.step(warmup)
+        s.sync()
+        e0.record(st)
+        s.step(steps)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        s.close()
+        return {"case": case, "shape": [size, size], "steps": steps, "ms_per_step": ms,
+                "mlups": size * size / ms / 1e3, "gbs_at_72B": size * size * 72 / ms / 1e6}
+    specs = W.batched_channels(64, seed=0x1411)
+    sp = max(specs, key=lambda c: c["shape"][0] * c["shape"][1])
+    nx, ny = sp["shape"]
+    fld = torch.tensor(W.force_field(sp["shape"], sp["g"][0], seed=1, rel=0.1), dtype=torch.float32, device=dev)
+    s = dugks.Sim(shape=sp["shape"], q=9, nu=sp["nu"], dt=sp["dt"], g=sp["g"], bcs=sp["bcs"], field=fld,
+                  store=dugks.STORE_F32, stream=st.cuda_stream)
+    s.init()
+    s.record(steps, 10)
+    seed = torch.ones((3, nx * ny), dtype=torch.float32, device=dev)
+    torch.cuda.synchronize(dev)
+    e0.record(st)
+    s.adjoint(seed)
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    s.close()
+    return {"case": case, "shape": [nx, ny], "steps": steps, "every": 10, "ms_per_step": ms,
+            "mlups": nx * ny / ms / 1e3, "gbs_at_132B": nx * ny * ADJ_BYTES / ms / 1e6}
+
+
 def cpu_baseline(seconds=12.0):
     """The FP64 oracle as it stands on a bounded sample of the same workload: a 40^3 cube
     at the same Reynolds number (same lid speed, nu scaled with the size), single thread."""
@@ -421,6 +465,9 @@ def main():
     ap.add_argument("--size", type=int, default=256, help="cube edge (256 for the benchmark; smaller for ncu)")
     ap.add_argument("--store", type=int, default=0, help="storage of the main leg (0 f32, 1 bf16, 2 f16, 3 f64)")
     ap.add_argument("--rows", type=int, default=0, help="thread-block rows of the 3D kernel (0: library default)")
+    ap.add_argument("--case", default="", choices=["", "cavity2d", "adjoint"],
+                    help="run one other workload alone for profiling (D2Q9 cavity of --size cells per side, "
+                         "or the adjoint of the largest channel over --steps steps) and print its own line")
     args = ap.parse_args()
     global N
     N = args.size
@@ -462,6 +509,10 @@ def main():
     torch.cuda.set_device(dev)
     from paper_1411_6121_gb300 import dugks
     dugks.load()
+    if args.case:
+        if rank == 0:
+            print(json.dumps(run_case(torch, args.case, args.size, args.steps, warmup, dev)), flush=True)
+        return 0
 
     sampler = ClockSampler(local)
     if ws > 1:
