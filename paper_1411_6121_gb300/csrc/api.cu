@@ -395,20 +395,28 @@ int dugks_state_bytes(dugks_t h, size_t *bytes) {
     return DUGKS_OK;
 }
 
+// Copy between the padded device state and an unpadded buffer: one linear copy when the rows
+// carry no padding (nx a multiple of 8), else one row per x line.
+static cudaError_t copy_state(dugks_t h, void *dst, size_t dpitch, const void *src, size_t spitch,
+                              cudaMemcpyKind kind) {
+    const size_t row = h->nx * h->esize;
+    const size_t rows = (size_t)h->q * h->ny * h->nz;
+    if (dpitch == row && spitch == row) return cudaMemcpyAsync(dst, src, row * rows, kind, h->stream);
+    return cudaMemcpy2DAsync(dst, dpitch, src, spitch, row, rows, kind, h->stream);
+}
+
 int dugks_get_state(dugks_t h, void *buf, size_t bytes, int32_t buf_is_device) {
     if (!h || !buf || bytes != (size_t)h->q * h->ncell * h->esize) return DUGKS_E_INVAL;
-    const size_t row = h->nx * h->esize;
-    CUDA_TRY(h, cudaMemcpy2DAsync(buf, row, h->buf[h->cur], h->px * h->esize, row, (size_t)h->q * h->ny * h->nz,
-                                  buf_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, copy_state(h, buf, h->nx * h->esize, h->buf[h->cur], h->px * h->esize,
+                           buf_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return DUGKS_OK;
 }
 
 int dugks_set_state(dugks_t h, const void *buf, size_t bytes, int32_t buf_is_device) {
     if (!h || !buf || bytes != (size_t)h->q * h->ncell * h->esize) return DUGKS_E_INVAL;
-    const size_t row = h->nx * h->esize;
-    CUDA_TRY(h, cudaMemcpy2DAsync(h->buf[h->cur], h->px * h->esize, buf, row, row, (size_t)h->q * h->ny * h->nz,
-                                  buf_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, copy_state(h, h->buf[h->cur], h->px * h->esize, buf, h->nx * h->esize,
+                           buf_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return DUGKS_OK;
 }

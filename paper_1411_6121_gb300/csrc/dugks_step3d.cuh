@@ -24,13 +24,24 @@
 //  * Each cell forms the relaxed interface values (step 7) of its +x, +y, +z interfaces;
 //    x neighbours exchange through warp shuffles, y neighbours through shared memory, so
 //    every interface is computed once and both cells use the same bits.
-//  * Wall interfaces (and the chunk's first z interface) take the direct path of
-//    dugks_step.cuh: all velocities reconstructed from the ring, NEQ (step 5), relax.
+//  * x-wall interfaces take the regular path and then step 5 (NEQ) as a correction, with
+//    the values at x_c (the boundary cell's opposite interface) shuffled from the next lane
+//    inward. y- and z-wall interfaces (and the chunk's first z interface) take the direct
+//    path of dugks_step.cuh: all velocities reconstructed from the ring, NEQ, relax.
 #pragma once
 
 #include "dugks_step.cuh"
 
 namespace dugks {
+
+// Velocity whose compact flux index along d is i.
+template <int Q>
+__host__ __device__ constexpr int flux_vel(int d, int i) {
+    int r = -1;
+    for (int k = 0; k < Q; k++)
+        if (Lat<Q>::e(k, d) != 0 && flux_index<Q>(d, k) == i) r = k;
+    return r;
+}
 
 template <int Q, int RY, class S = float>
 struct Shape3 {
@@ -170,14 +181,64 @@ __device__ __forceinline__ void face_relax(const Coef<float> &cf, const float *F
             // interface values need no conservation-exact form (the same value is used by
             // both cells, so the flux telescopes exactly whatever its rounding)
             const float q = fmaf(c45 * em, em, base);
-            const float geq = mul_rn(w, fmaf(em, 3.0f, q)), geqb = mul_rn(w, fmaf(em, -3.0f, q));
-            float v = fmaf(cf.b7, geq - F[i], F[i]), vb = fmaf(cf.b7, geqb - F[ib], F[ib]);
-            if (FORCE) {
+            if constexpr (FORCE) {
+                const float geq = mul_rn(w, fmaf(em, 3.0f, q)), geqb = mul_rn(w, fmaf(em, -3.0f, q));
+                float v = fmaf(cf.b7, geq - F[i], F[i]), vb = fmaf(cf.b7, geqb - F[ib], F[ib]);
                 v = fmaf(cf.c7 * 3.0f * (ge - gm), fmaf(w, cf.rho0, geq), v);
                 vb = fmaf(cf.c7 * 3.0f * (-ge - gm), fmaf(w, cf.rho0, geqb), vb);
+                out[i] = v;
+                out[ib] = vb;
+            } else {
+                // (1 - b7) F + (b7 W) (q +- 3 e.m): one operation less than F + b7 (geq - F)
+                const float bw = cf.b7 * w, ob = 1.0f - cf.b7;
+                out[i] = fmaf(bw, fmaf(em, 3.0f, q), ob * F[i]);
+                out[ib] = fmaf(bw, fmaf(em, -3.0f, q), ob * F[ib]);
             }
-            out[i] = v;
-            out[ib] = vb;
+        }
+    });
+}
+
+// Step 5 (eq. NEQ) at a wall interface normal to d, formed from the values of the regular
+// path: F (compact step-4 values of the crossing velocities) and its interface moments (drb,
+// jb: sums over all velocities, without the force shift), and the same at x_c, the boundary
+// cell's opposite interface (Fc, drc, jc, with its acceleration Ghc). The velocities that
+// enter from the wall (e_d > 0 at the low wall, SIDE 0; e_d < 0 at the high wall, SIDE 1)
+// become f_eq(rho_a, u_a) + [Fc - f_eq(rho_c, u_c)], and the interface moments take the
+// moments of that change, so step 6 sees the moments of the modified values.
+template <int Q, int d, bool FORCE, int SIDE>
+__device__ __forceinline__ void neq_wall(const StepParams &p, const Coef<float> &cf, float *F, float &drb,
+                                         float jb[3], const float *Fc, float drc, const float jc[3],
+                                         const float Ghc[3]) {
+    constexpr int wid = 2 * d + SIDE;
+    float mc[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) mc[a] = FORCE ? fmaf(Ghc[a], cf.wface * cf.rho0, jc[a]) : jc[a];
+    float dra, ma[3];
+    if (p.bc[wid] == 1) {  // velocity condition: u_a = u_w, rho_a = rho_c
+        dra = drc;
+#pragma unroll
+        for (int a = 0; a < 3; a++) ma[a] = (float)(p.bc_u[wid][a] * p.rho0 * p.inv_c);
+    } else {  // pressure condition: rho_a = rho0 + p_w / RT, u_a = u_c
+        dra = (float)p.bc_drho[wid];
+#pragma unroll
+        for (int a = 0; a < 3; a++) ma[a] = mc[a];
+    }
+    const float mma = dotD<3, float>(ma, ma), mmc = dotD<3, float>(mc, mc);
+    sfor<Q>([&](auto kc) {
+        constexpr int k = kc;
+        constexpr int ed = Lat<Q>::e(k, d);
+        if constexpr (SIDE == 0 ? ed > 0 : ed < 0) {
+            constexpr int i = flux_index<Q>(d, k);
+            const float v = geq_k<Q, float>(k, dra, ma, mma, cf.inv_rho0) +
+                            (Fc[i] - geq_k<Q, float>(k, drc, mc, mmc, cf.inv_rho0));
+            const float dv = v - F[i];
+            drb += dv;
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                if (Lat<Q>::e(k, a) > 0) jb[a] += dv;
+                if (Lat<Q>::e(k, a) < 0) jb[a] -= dv;
+            }
+            F[i] = v;
         }
     });
 }
@@ -506,21 +567,35 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
             float F[NF], jb[3];
 #pragma unroll
             for (int i = 0; i < NF; i++) F[i] = alx[i] + __shfl_down_sync(0xffffffffu, bex[i], 1);
-            const float drb = Ax[0] + __shfl_down_sync(0xffffffffu, Bx[0], 1);
+            float drb = Ax[0] + __shfl_down_sync(0xffffffffu, Bx[0], 1);
 #pragma unroll
             for (int a = 0; a < 3; a++) jb[a] = Ax[1 + a] + __shfl_down_sync(0xffffffffu, Bx[1 + a], 1);
-            if (need_x) {
-                if (!perx && (gx == -1 || gx == nx - 1)) {
-                    float t[NF];
-                    direct_face(0, kz, gx + 1, t);
+            float Gb[3] = {0.0f, 0.0f, 0.0f};
+            if (FORCE && need_x) faceG(0, gx + 1, gy, kz, Gb);
+            if (xwall_tile) {
+                // the wall interfaces take step 5 from x_c, the interface that the next lane
+                // inward owns (lane + 1 at the low wall, lane - 1 at the high wall); every lane
+                // takes part in the exchange
+                float Fn[NF], jd[3], ju[3], Gd[3] = {0.0f, 0.0f, 0.0f}, Gu[3] = {0.0f, 0.0f, 0.0f};
+                sfor<NF>([&](auto ic) {
+                    constexpr int i = ic;
+                    if constexpr (Lat<Q>::e(flux_vel<Q>(0, i), 0) > 0) Fn[i] = __shfl_down_sync(0xffffffffu, F[i], 1);
+                    else Fn[i] = __shfl_up_sync(0xffffffffu, F[i], 1);
+                });
+                const float dd = __shfl_down_sync(0xffffffffu, drb, 1), du = __shfl_up_sync(0xffffffffu, drb, 1);
 #pragma unroll
-                    for (int i = 0; i < NF; i++) fxp[i] = t[i];
-                } else {
-                    float Gb[3] = {0.0f, 0.0f, 0.0f};
-                    if (FORCE) faceG(0, gx + 1, gy, kz, Gb);
-                    face_relax<Q, 0, FORCE>(cf, F, drb, jb, Gb, fxp);
+                for (int a = 0; a < 3; a++) {
+                    jd[a] = __shfl_down_sync(0xffffffffu, jb[a], 1);
+                    ju[a] = __shfl_up_sync(0xffffffffu, jb[a], 1);
+                    if (FORCE) {
+                        Gd[a] = __shfl_down_sync(0xffffffffu, Gb[a], 1);
+                        Gu[a] = __shfl_up_sync(0xffffffffu, Gb[a], 1);
+                    }
                 }
+                if (need_x && gx == -1) neq_wall<Q, 0, FORCE, 0>(p, cf, F, drb, jb, Fn, dd, jd, Gd);
+                if (need_x && gx == nx - 1) neq_wall<Q, 0, FORCE, 1>(p, cf, F, drb, jb, Fn, du, ju, Gu);
             }
+            if (need_x) face_relax<Q, 0, FORCE>(cf, F, drb, jb, Gb, fxp);
         }
         // ---- P4: y parts of plane kz; publish beta_y, B_y; y interfaces ----
         float aly[NF], Ay[4];
