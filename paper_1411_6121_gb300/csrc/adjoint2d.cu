@@ -197,29 +197,40 @@ __device__ __forceinline__ void moments2(const AdjParams<T> &a, const T f[Q], co
     m[1] += a.rho0 * Gh[1] * w;
 }
 
-// Relaxation P_k = f_k + b (geq_k - f_k) + c S_k with S_k = 3 (Gh.e_k - Gh.m/rho0) f_eq,k
-// (steps 1 and 7). Given weights wk = dL/dP_k, adds dL/d(drho), dL/dm and dL/dGh through
-// the moment dependence (the direct part (1 - b) wk is left to the caller).
+// ---- the general path, velocity-parallel: one half-warp per item of the boundary frame,
+// lane k of the half (k < Q) holding velocity k and lanes k >= Q zeros. Sums over the
+// velocities are butterflies over the half-warp: every lane ends with the same bits and the
+// order is fixed. The two halves of a warp work on different items and may diverge, so the
+// shuffles name only their own half. ----
+__device__ __forceinline__ int half_lane() { return threadIdx.x & 15; }
 template <class T>
-__device__ __forceinline__ void relax_T(const AdjParams<T> &a, const T wk[Q], T dr, const T m[2], const T Gh[2],
-                                        T b, T c, T &bdr, T bm[2], T bG[2]) {
+__device__ __forceinline__ T wsum(T v) {
+    const unsigned m = 0xffffu << (threadIdx.x & 16);
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) v += __shfl_xor_sync(m, v, o, 16);
+    return v;
+}
+
+// Relaxation P_k = f_k + b (geq_k - f_k) + c S_k with S_k = 3 (Gh.e_k - Gh.m/rho0) f_eq,k
+// (steps 1 and 7). Given the weight w = dL/dP_k of one velocity k, its share of dL/d(drho),
+// dL/dm and dL/dGh through the moment dependence (the direct part (1 - b) w is left to the
+// caller); summed over the velocities by the caller.
+template <class T>
+__device__ __forceinline__ void relax_T_one(const AdjParams<T> &a, int k, T w, T dr, const T m[2], const T Gh[2],
+                                            T b, T c, T &bdr, T bm[2], T bG[2]) {
     const T gm = (Gh[0] * m[0] + Gh[1] * m[1]) * a.inv_rho0;
-    for (int k = 0; k < Q; k++) {
-        const T w = wk[k];
-        if (w == T(0)) continue;
-        const T e0 = (T)L9::e(k, 0), e1 = (T)L9::e(k, 1);
-        const T W = L9::wt<T>(k);
-        const T s = T(3) * (Gh[0] * e0 + Gh[1] * e1 - gm);
-        const T feq = W * a.rho0 + geq(a, k, dr, m);
-        T dg[2];
-        geq_dm(a, k, m, dg);
-        const T coef = b + c * s;  // dP/dgeq
-        bdr += w * coef * W;
-        bm[0] += w * (coef * dg[0] - c * T(3) * Gh[0] * a.inv_rho0 * feq);
-        bm[1] += w * (coef * dg[1] - c * T(3) * Gh[1] * a.inv_rho0 * feq);
-        bG[0] += w * c * T(3) * (e0 - m[0] * a.inv_rho0) * feq;
-        bG[1] += w * c * T(3) * (e1 - m[1] * a.inv_rho0) * feq;
-    }
+    const T e0 = (T)L9::e(k, 0), e1 = (T)L9::e(k, 1);
+    const T W = L9::wt<T>(k);
+    const T s = T(3) * (Gh[0] * e0 + Gh[1] * e1 - gm);
+    const T feq = W * a.rho0 + geq(a, k, dr, m);
+    T dg[2];
+    geq_dm(a, k, m, dg);
+    const T coef = b + c * s;  // dP/dgeq
+    bdr = w * coef * W;
+    bm[0] = w * (coef * dg[0] - c * T(3) * Gh[0] * a.inv_rho0 * feq);
+    bm[1] = w * (coef * dg[1] - c * T(3) * Gh[1] * a.inv_rho0 * feq);
+    bG[0] = w * c * T(3) * (e0 - m[0] * a.inv_rho0) * feq;
+    bG[1] = w * c * T(3) * (e1 - m[1] * a.inv_rho0) * feq;
 }
 
 // ---- acceleration at cells and interfaces (reading R2) ----
@@ -255,10 +266,11 @@ __device__ __forceinline__ void face_Gh(const AdjParams<T> &a, int d, int i, int
         Gh[c] = (a.g[c] + T(0.5) * (field_at(a, c, lx, ly) + field_at(a, c, hx, hy))) * a.cthc;
 }
 
-// ---- forward state of one interface (steps 3-6) ----
+// ---- forward state of one interface (steps 3-6), one velocity per lane ----
 template <class T>
-struct FaceState {
-    T F[Q];                // step-4 values, incoming velocities replaced at a wall (step 5)
+struct FaceLane {
+    T F, Fc;               // step-4 value of the lane's velocity (incoming ones replaced at a
+                           // wall, step 5) and its value at x_c (wall only)
     T dr, m[2], Gh[2];     // step-6 moments and the interface acceleration
     int wall, side;
     T drc, mc[2];          // moments at x_c (wall only)
@@ -266,68 +278,74 @@ struct FaceState {
 };
 
 template <class T>
-__device__ __forceinline__ void face_forward(const AdjParams<T> &a, int d, int i, int j, FaceState<T> &s) {
-    for (int k = 0; k < Q; k++) s.F[k] = recon(a, d, i, j, k);
+__device__ __forceinline__ void face_forward_lane(const AdjParams<T> &a, int d, int i, int j, int k, bool act,
+                                                  FaceLane<T> &s) {
+    const T e0 = (T)L9::e(k, 0), e1 = (T)L9::e(k, 1);
+    s.F = act ? recon(a, d, i, j, k) : T(0);
     const int pos = d == 0 ? i : j;
     s.wall = !a.per[d] && (pos == 0 || pos == a.n[d]);
     s.side = pos == 0 ? 0 : 1;
     face_Gh(a, d, i, j, s.Gh);
+    s.Fc = T(0);
     if (s.wall) {
         // x_c: the boundary cell's opposite interface (reading R4)
         const int sh = s.side == 0 ? 1 : -1;
         const int ci = d == 0 ? i + sh : i, cj = d == 1 ? j + sh : j;
-        T Fc[Q], Ghc[2];
-        for (int k = 0; k < Q; k++) Fc[k] = recon(a, d, ci, cj, k);
+        s.Fc = act ? recon(a, d, ci, cj, k) : T(0);
+        T Ghc[2];
         face_Gh(a, d, ci, cj, Ghc);
-        moments2(a, Fc, Ghc, a.wface, s.drc, s.mc);
+        s.drc = wsum(s.Fc);
+        s.mc[0] = wsum(e0 * s.Fc) + a.rho0 * Ghc[0] * a.wface;
+        s.mc[1] = wsum(e1 * s.Fc) + a.rho0 * Ghc[1] * a.wface;
         const int wid = 2 * d + s.side;
         const bool vel = a.bc[wid] == DUGKS_BC_NEQ_VELOCITY;
         const T dra = vel ? s.drc : a.drw[wid];
         s.ma[0] = vel ? a.mw[wid][0] : s.mc[0];
         s.ma[1] = vel ? a.mw[wid][1] : s.mc[1];
         const int sgn = s.side == 0 ? -1 : 1;
-        for (int k = 0; k < Q; k++)
-            if (sgn * L9::e(k, d) < 0) s.F[k] = geq(a, k, dra, s.ma) + Fc[k] - geq(a, k, s.drc, s.mc);
+        if (act && sgn * L9::e(k, d) < 0) s.F = geq(a, k, dra, s.ma) + s.Fc - geq(a, k, s.drc, s.mc);
     }
-    moments2(a, s.F, s.Gh, a.wface, s.dr, s.m);
+    s.dr = wsum(s.F);
+    s.m[0] = wsum(e0 * s.F) + a.rho0 * s.Gh[0] * a.wface;
+    s.m[1] = wsum(e1 * s.F) + a.rho0 * s.Gh[1] * a.wface;
 }
 
-// Adjoint of steps 5-9 at interface (d, i, j) for lambda'. Fb: dL/d(step-4 values), zero
-// for the velocities a wall replaces; Gb: dL/dGh of the interface. At a wall also what
-// flows to the step-4 values and Gh of x_c (Fcb, Gcb) and to the wall velocity (Wb).
+// Adjoint of steps 5-9 at interface (d, i, j) for lambda', velocity k of this lane. Fb:
+// dL/d(step-4 value), zero for a velocity the wall replaces; Gb: dL/dGh of the interface
+// (the same in every lane). At a wall also what flows to the step-4 value and Gh of x_c
+// (Fcb, Gcb) and to the wall velocity (Wb).
 template <class T>
-__device__ __forceinline__ void face_adjoint(const AdjParams<T> &a, int d, int i, int j, T Fb[Q], T Gb[2],
-                                             T Fcb[Q], T Gcb[2], T Wb[2], int &wall) {
-    FaceState<T> s;
-    face_forward(a, d, i, j, s);
+__device__ __forceinline__ void face_adjoint_lane(const AdjParams<T> &a, int d, int i, int j, int k, bool act,
+                                                  T &Fb, T Gb[2], T &Fcb, T Gcb[2], T Wb[2], int &wall) {
+    FaceLane<T> s;
+    face_forward_lane(a, d, i, j, k, act, s);
     wall = s.wall;
     const int64_t nc = ncell(a);
     const int pos = d == 0 ? i : j, nd = a.n[d];
+    const T e0 = (T)L9::e(k, 0), e1 = (T)L9::e(k, 1);
     // steps 8-9: velocity k of this interface enters the update of its low cell with
     // -2 kappa e_d and of its high cell with +2 kappa e_d
     const bool haslo = pos > 0, hashi = pos < nd;
     const int plo = pos > 0 ? pos - 1 : nd - 1, phi_c = pos < nd ? pos : 0;
     const int64_t clo = d == 0 ? plo + (int64_t)a.n[0] * j : i + (int64_t)a.n[0] * plo;
     const int64_t chi = d == 0 ? phi_c + (int64_t)a.n[0] * j : i + (int64_t)a.n[0] * phi_c;
-    T fbar[Q];
-    for (int k = 0; k < Q; k++) {
-        const int ed = L9::e(k, d);
-        T v = T(0);
-        if (ed) {
-            if (haslo) v -= a.lam1[k * nc + clo];
-            if (hashi) v += a.lam1[k * nc + chi];
-        }
-        fbar[k] = a.two_kappa * (T)ed * v;
+    const int ed = L9::e(k, d);
+    T v = T(0);
+    if (act && ed) {
+        if (haslo) v -= a.lam1[k * nc + clo];
+        if (hashi) v += a.lam1[k * nc + chi];
     }
+    const T fbar = a.two_kappa * (T)ed * v;
     // step 7 (eq. original_f) at the step-6 moments, then step 6
-    T bdr = T(0), bm[2] = {T(0), T(0)};
-    Gb[0] = Gb[1] = T(0);
-    relax_T(a, fbar, s.dr, s.m, s.Gh, a.b7, a.c7, bdr, bm, Gb);
-    Gb[0] += a.rho0 * a.wface * bm[0];
-    Gb[1] += a.rho0 * a.wface * bm[1];
-    for (int k = 0; k < Q; k++)
-        Fb[k] = (T(1) - a.b7) * fbar[k] + bdr + (T)L9::e(k, 0) * bm[0] + (T)L9::e(k, 1) * bm[1];
-    for (int k = 0; k < Q; k++) Fcb[k] = T(0);
+    T bdr, bm[2], bG[2];
+    relax_T_one(a, k, fbar, s.dr, s.m, s.Gh, a.b7, a.c7, bdr, bm, bG);
+    bdr = wsum(bdr);
+    bm[0] = wsum(bm[0]);
+    bm[1] = wsum(bm[1]);
+    Gb[0] = wsum(bG[0]) + a.rho0 * a.wface * bm[0];
+    Gb[1] = wsum(bG[1]) + a.rho0 * a.wface * bm[1];
+    Fb = act ? (T(1) - a.b7) * fbar + bdr + e0 * bm[0] + e1 * bm[1] : T(0);
+    Fcb = T(0);
     Gcb[0] = Gcb[1] = T(0);
     Wb[0] = Wb[1] = T(0);
     if (!wall) return;
@@ -337,26 +355,24 @@ __device__ __forceinline__ void face_adjoint(const AdjParams<T> &a, int d, int i
     const int wid = 2 * d + s.side;
     const bool vel = a.bc[wid] == DUGKS_BC_NEQ_VELOCITY;
     const int sgn = s.side == 0 ? -1 : 1;
+    const bool incoming = act && sgn * ed < 0;
+    const T w = incoming ? Fb : T(0);
+    if (incoming) Fb = T(0);
+    Fcb = w;
     T bdrc = T(0), bmc[2] = {T(0), T(0)};
-    for (int k = 0; k < Q; k++) {
-        if (!(sgn * L9::e(k, d) < 0)) continue;
-        const T w = Fb[k];
-        Fb[k] = T(0);
-        Fcb[k] += w;
-        if (vel) {
-            T da[2], dc[2];
-            geq_dm(a, k, s.ma, da);
-            geq_dm(a, k, s.mc, dc);
-            Wb[0] += w * da[0] * a.dmw;
-            Wb[1] += w * da[1] * a.dmw;
-            bmc[0] -= w * dc[0];
-            bmc[1] -= w * dc[1];
-        } else {
-            bdrc -= w * L9::wt<T>(k);
-        }
+    if (vel) {
+        T da[2], dc[2];
+        geq_dm(a, k, s.ma, da);
+        geq_dm(a, k, s.mc, dc);
+        Wb[0] = wsum(w * da[0] * a.dmw);
+        Wb[1] = wsum(w * da[1] * a.dmw);
+        bmc[0] = -wsum(w * dc[0]);
+        bmc[1] = -wsum(w * dc[1]);
+    } else {
+        bdrc = -wsum(w * L9::wt<T>(k));
     }
     // step 6 at x_c
-    for (int k = 0; k < Q; k++) Fcb[k] += bdrc + (T)L9::e(k, 0) * bmc[0] + (T)L9::e(k, 1) * bmc[1];
+    if (act) Fcb += bdrc + e0 * bmc[0] + e1 * bmc[1];
     Gcb[0] = a.rho0 * a.wface * bmc[0];
     Gcb[1] = a.rho0 * a.wface * bmc[1];
 }
@@ -551,6 +567,51 @@ __global__ void __launch_bounds__(256) adj_cells_fwd(const AdjParams<T> a) {
     }
 }
 
+// The t-th interface of the frame of both axes (walls: NEQ and dL/du_w; x_c interfaces;
+// periodic seams), one velocity per lane of the calling half-warp.
+template <class T>
+__device__ __noinline__ void faces_frame_item(const AdjParams<T> &a, int64_t t) {
+    const Rect r0 = face_rect(0, a.n[0], a.n[1], a.per[0], a.per[1]);
+    const Rect r1 = face_rect(1, a.n[0], a.n[1], a.per[0], a.per[1]);
+    const int64_t c0 = frame_count(r0);
+    const int lane = half_lane();
+    const bool act = lane < Q;
+    const int k = act ? lane : 0;
+    const int d = t < c0 ? 0 : 1;
+    int i, j;
+    frame_at(d == 0 ? r0 : r1, d == 0 ? t : t - c0, i, j);
+    const int64_t f = fidx(a, d, i, j);
+    const int pos = d == 0 ? i : j, nd = a.n[d];
+    T Fb, Gb[2], Fcb, Gcb[2], Wb[2];
+    int wall;
+    face_adjoint_lane(a, d, i, j, k, act, Fb, Gb, Fcb, Gcb, Wb, wall);
+    if (wall && a.dW && lane == 0 && a.bc[2 * d + (pos == 0 ? 0 : 1)] == DUGKS_BC_NEQ_VELOCITY) {
+        const int64_t slot = d == 0 ? (pos == 0 ? 0 : a.n[1]) + j : 2 * (int64_t)a.n[1] + (pos == 0 ? 0 : a.n[0]) + i;
+        a.dW[2 * slot] += (double)Wb[0];
+        a.dW[2 * slot + 1] += (double)Wb[1];
+    }
+    // this interface is x_c of the wall interface at 0 (pos == 1) and/or at nd (pos == nd - 1)
+    if (!a.per[d]) {
+        for (int sd = 0; sd < 2; sd++) {
+            if (pos != (sd == 0 ? 1 : nd - 1)) continue;
+            const int wp = sd == 0 ? 0 : nd;
+            T wFb, wGb[2], wFcb, wGcb[2], wWb[2];
+            int ww;
+            face_adjoint_lane(a, d, d == 0 ? wp : i, d == 1 ? wp : j, k, act, wFb, wGb, wFcb, wGcb, wWb, ww);
+            Fb += wFcb;
+            Gb[0] += wGcb[0];
+            Gb[1] += wGcb[1];
+        }
+    }
+    T *fb = a.fb[d], *gb = a.gb[d];
+    const int64_t nf = nface(a, d);
+    if (act) fb[k * nf + f] = Fb;
+    if (lane == 0) {
+        gb[f] = Gb[0];
+        gb[nf + f] = Gb[1];
+    }
+}
+
 // Interior interfaces of both axes (blockIdx.z = axis), 2D blocks over the fast rectangle.
 template <class T>
 __global__ void __launch_bounds__(128, 4) adj_faces_fast(const AdjParams<T> a) {
@@ -563,47 +624,11 @@ __global__ void __launch_bounds__(128, 4) adj_faces_fast(const AdjParams<T> a) {
     else face_fast<T, 1>(a, i, j, f, nface(a, 1));
 }
 
-// The frame of both axes: walls (NEQ, dL/du_w), x_c interfaces, periodic seams.
+// The frame interfaces of both axes, one per half-warp.
 template <class T>
-__global__ void __launch_bounds__(64) adj_faces_frame(const AdjParams<T> a) {
-    const Rect r0 = face_rect(0, a.n[0], a.n[1], a.per[0], a.per[1]);
-    const Rect r1 = face_rect(1, a.n[0], a.n[1], a.per[0], a.per[1]);
-    const int64_t c0 = frame_count(r0), ntot = c0 + frame_count(r1);
-    const int64_t n0 = nface(a, 0);
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntot; t += (int64_t)gridDim.x * blockDim.x) {
-        const int d = t < c0 ? 0 : 1;
-        int i, j;
-        frame_at(d == 0 ? r0 : r1, d == 0 ? t : t - c0, i, j);
-        const int64_t f = fidx(a, d, i, j);
-        const int pos = d == 0 ? i : j, nd = a.n[d];
-        T Fb[Q], Gb[2], Fcb[Q], Gcb[2], Wb[2];
-        int wall;
-        face_adjoint(a, d, i, j, Fb, Gb, Fcb, Gcb, Wb, wall);
-        if (wall && a.dW && a.bc[2 * d + (pos == 0 ? 0 : 1)] == DUGKS_BC_NEQ_VELOCITY) {
-            const int64_t slot =
-                d == 0 ? (pos == 0 ? 0 : a.n[1]) + j : 2 * (int64_t)a.n[1] + (pos == 0 ? 0 : a.n[0]) + i;
-            a.dW[2 * slot] += (double)Wb[0];
-            a.dW[2 * slot + 1] += (double)Wb[1];
-        }
-        // this interface is x_c of the wall interface at 0 (pos == 1) and/or at nd (pos == nd - 1)
-        if (!a.per[d]) {
-            for (int sd = 0; sd < 2; sd++) {
-                if (pos != (sd == 0 ? 1 : nd - 1)) continue;
-                const int wp = sd == 0 ? 0 : nd;
-                T wFb[Q], wGb[2], wFcb[Q], wGcb[2], wWb[2];
-                int ww;
-                face_adjoint(a, d, d == 0 ? wp : i, d == 1 ? wp : j, wFb, wGb, wFcb, wGcb, wWb, ww);
-                for (int k = 0; k < Q; k++) Fb[k] += wFcb[k];
-                Gb[0] += wGcb[0];
-                Gb[1] += wGcb[1];
-            }
-        }
-        T *fb = a.fb[d], *gb = a.gb[d];
-        const int64_t nf = d == 0 ? n0 : nface(a, 1);
-        for (int k = 0; k < Q; k++) fb[k * nf + f] = Fb[k];
-        gb[f] = Gb[0];
-        gb[nf + f] = Gb[1];
-    }
+__global__ void __launch_bounds__(128) adj_faces_frame(const AdjParams<T> a, int64_t ntot) {
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+    if (t < ntot) faces_frame_item(a, t);
 }
 
 // dL/dGh summed over the interfaces whose acceleration averages cell (x, y), with the
@@ -635,54 +660,59 @@ __device__ __forceinline__ T face_G_T(const AdjParams<T> &a, int comp, int x, in
 }
 
 // The t-th frame cell (cells whose stencil meets a wall ghost, a periodic image or a
-// wall-clamped interface acceleration).
+// wall-clamped interface acceleration), one velocity per lane of the calling half-warp.
 template <class T>
 __device__ __noinline__ void cells_frame_item(const AdjParams<T> &a, int64_t t) {
     const int64_t nc = ncell(a);
     const Rect r = cell_rect(a.n[0], a.n[1], a.per[0], a.per[1]);
-    {
-        int x, y;
-        frame_at(r, t, x, y);
-        const int64_t c = x + (int64_t)a.n[0] * y;
-        int ux[3], uy[3];
-        T wx[3], wy[3];
-        const int nux = ext_users<T>(x, a.n[0], a.per[0], ux, wx);
-        const int nuy = ext_users<T>(y, a.n[1], a.per[1], uy, wy);
-        // adjoint of fbar+ of this cell: eq. f_tilde_+ (4/3 fbar+) and every interface
-        // value reconstructed from it, directly or through a ghost / periodic image
-        T pb[Q];
-        for (int k = 0; k < Q; k++) {
-            T v = T(4) / T(3) * a.lam1[k * nc + c];
-            for (int p = 0; p < nux; p++)
-                for (int q = 0; q < nuy; q++) v += wx[p] * wy[q] * recon_T(a, k, ux[p], uy[q]);
-            pb[k] = v;
-        }
-        // step 1 (eq. f_bar_+) and the cell moments (eq. macro_values)
-        const T dr = a.mom[c];
-        const T m[2] = {a.mom[nc + c], a.mom[2 * nc + c]};
-        T Gh[2];
-        cell_Gh(a, x, y, Gh);
-        T bdr = T(0), bm[2] = {T(0), T(0)}, bG[2] = {T(0), T(0)};
-        relax_T(a, pb, dr, m, Gh, a.b1, a.c1, bdr, bm, bG);
-        for (int k = 0; k < Q; k++)
-            a.lam0[k * nc + c] = -a.lam1[k * nc + c] / T(3) + (T(1) - a.b1) * pb[k] + bdr +
-                                 (T)L9::e(k, 0) * bm[0] + (T)L9::e(k, 1) * bm[1];
-        if (a.dG) {
-            for (int comp = 0; comp < 2; comp++) {
-                const T sv = (bG[comp] + a.rho0 * a.wcell * bm[comp]) * a.ctc + face_G_T(a, comp, x, y) * a.cthc;
-                a.dG[comp * nc + c] += (double)sv;
-            }
-        }
+    const int lane = half_lane();
+    const bool act = lane < Q;
+    const int k = act ? lane : 0;
+    int x, y;
+    frame_at(r, t, x, y);
+    const int64_t c = x + (int64_t)a.n[0] * y;
+    int ux[3], uy[3];
+    T wx[3], wy[3];
+    const int nux = ext_users<T>(x, a.n[0], a.per[0], ux, wx);
+    const int nuy = ext_users<T>(y, a.n[1], a.per[1], uy, wy);
+    // adjoint of fbar+ of this cell: eq. f_tilde_+ (4/3 fbar+) and every interface value
+    // reconstructed from it, directly or through a ghost / periodic image
+    const T l1 = act ? a.lam1[k * nc + c] : T(0);
+    T pb = T(0);
+    if (act) {
+        T v = T(4) / T(3) * l1;
+        for (int p = 0; p < nux; p++)
+            for (int q = 0; q < nuy; q++) v += wx[p] * wy[q] * recon_T(a, k, ux[p], uy[q]);
+        pb = v;
+    }
+    // step 1 (eq. f_bar_+) and the cell moments (eq. macro_values)
+    const T dr = a.mom[c];
+    const T m[2] = {a.mom[nc + c], a.mom[2 * nc + c]};
+    T Gh[2];
+    cell_Gh(a, x, y, Gh);
+    T bdr, bm[2], bG[2];
+    relax_T_one(a, k, pb, dr, m, Gh, a.b1, a.c1, bdr, bm, bG);
+    bdr = wsum(bdr);
+    bm[0] = wsum(bm[0]);
+    bm[1] = wsum(bm[1]);
+    bG[0] = wsum(bG[0]);
+    bG[1] = wsum(bG[1]);
+    if (act)
+        a.lam0[k * nc + c] = -l1 / T(3) + (T(1) - a.b1) * pb + bdr + (T)L9::e(k, 0) * bm[0] + (T)L9::e(k, 1) * bm[1];
+    if (a.dG && lane < 2) {
+        const int comp = lane;
+        const T sv = (bG[comp] + a.rho0 * a.wcell * bm[comp]) * a.ctc + face_G_T(a, comp, x, y) * a.cthc;
+        a.dG[comp * nc + c] += (double)sv;
     }
 }
 
-// All cells in one launch of 128-thread blocks: frame blocks first, then 32 x 4 tiles of the
-// fast rectangle (tx x ty blocks).
+// All cells in one launch of 128-thread blocks: frame blocks first (a half-warp per frame cell),
+// then 32 x 4 tiles of the fast rectangle (tx x ty blocks).
 template <class T>
 __global__ void __launch_bounds__(128) adj_cells_all(const AdjParams<T> a, int nfb, int tx, int ty) {
-    if ((int)blockIdx.x < nfb) {
+    if ((int)blockIdx.x < nfb) {  // eight frame cells per block, one per half-warp
         const Rect r = cell_rect(a.n[0], a.n[1], a.per[0], a.per[1]);
-        const int64_t t = (int64_t)blockIdx.x * 128 + threadIdx.x;
+        const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 4);
         if (t < frame_count(r)) cells_frame_item(a, t);
         return;
     }
@@ -831,13 +861,13 @@ cudaError_t reverse_step(AdjParams<T> a, const dugks_t h, const void *state, dou
     }
     const int64_t ff = frame_count(r0) + frame_count(r1);
     if (ff > 0) {
-        adj_faces_frame<T><<<blocks_for(ff, 64), 64, 0, st>>>(a);
+        adj_faces_frame<T><<<blocks_for(ff, 8), 128, 0, st>>>(a, ff);  // eight interfaces per block
         n++;
     }
     {
         const Rect rc = cell_rect(nx, ny, a.per[0], a.per[1]);
         const int tx = rect_empty(rc) ? 0 : (rc.x1 - rc.x0 + 32) / 32, ty = rect_empty(rc) ? 0 : (rc.y1 - rc.y0 + 4) / 4;
-        const int nfb = (int)((frame_count(rc) + 127) / 128);
+        const int nfb = (int)((frame_count(rc) + 7) / 8);
         const int nb = nfb + tx * ty;
         if (nb > 0) {
             adj_cells_all<T><<<nb, 128, 0, st>>>(a, nfb, tx, ty);
