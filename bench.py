@@ -199,37 +199,68 @@ def run_form(torch, store, steps, warmup, dev, tile=None):
     return total_ms / steps, sum(kern) / len(kern), l1 - l0, res
 
 
-def run_e2e(torch, steps, dev):
+def parse_cpulist(text):
+    """The CPU set of a sysfs cpulist such as "0-71,144-215"."""
+    cpus = set()
+    for part in text.strip().split(","):
+        if part:
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+    return cpus
+
+
+def gpu_local_cpus(torch, dev):
+    """CPUs local to the GPU (the sysfs local_cpulist of its PCI function), or None. Pinned
+    host buffers are placed on the NUMA node of the thread that allocates them, and copies from
+    a remote node cross the CPU-to-CPU link."""
+    try:
+        pr = torch.cuda.get_device_properties(dev)
+        path = "/sys/bus/pci/devices/%04x:%02x:%02x.0/local_cpulist" % (pr.pci_domain_id, pr.pci_bus_id,
+                                                                         pr.pci_device_id)
+        return parse_cpulist(open(path).read()) & os.sched_getaffinity(0) or None
+    except Exception:
+        return None
+
+
+def run_e2e(torch, steps, dev, trials=3):
     """End to end through the C ABI with host buffers: every step uploads the state from
-    pinned host memory, advances one step and reads the moments back to pinned host memory."""
-    import numpy as np
-    from paper_1411_6121_gb300 import dugks
-    cfg = workload()
-    stream = torch.cuda.Stream(device=dev)
-    sim = dugks.Sim(store=0, stream=stream.cuda_stream, use_graph=False, **cfg)
-    sim.init()
-    nb = sim.state_bytes()
-    host_state = torch.empty(nb // 4, dtype=torch.float32, pin_memory=True)
-    host_mom = torch.empty((4, N ** 3), dtype=torch.float32, pin_memory=True)
-    # one warm pass
-    dptr = host_state.data_ptr()
+    pinned host memory, advances one step and reads the moments back to pinned host memory.
+    The process runs on the GPU's local CPUs meanwhile (so the pinned buffers sit on the GPU's
+    NUMA node); the median of `trials` timed runs of `steps` steps is reported."""
     import ctypes as C
-    lib = sim.lib
-    rc = lib.dugks_get_state(sim.h, C.c_void_p(dptr), nb, 0)
-    assert rc == 0
-    for _ in range(2):
-        lib.dugks_set_state(sim.h, C.c_void_p(dptr), nb, 0)
-        sim.step(1)
-        lib.dugks_moments(sim.h, C.c_void_p(host_mom.data_ptr()), 0)
-    torch.cuda.synchronize(dev)
-    t = time.perf_counter()
-    for _ in range(steps):
-        assert lib.dugks_set_state(sim.h, C.c_void_p(dptr), nb, 0) == 0
-        sim.step(1)
-        assert lib.dugks_moments(sim.h, C.c_void_p(host_mom.data_ptr()), 0) == 0
-    el = time.perf_counter() - t
-    sim.close()
-    return el / steps, nb, 4 * 4 * N ** 3
+    from paper_1411_6121_gb300 import dugks
+    old_aff = os.sched_getaffinity(0)
+    local = gpu_local_cpus(torch, dev)
+    try:
+        if local:
+            os.sched_setaffinity(0, local)
+        cfg = workload()
+        stream = torch.cuda.Stream(device=dev)
+        sim = dugks.Sim(store=0, stream=stream.cuda_stream, use_graph=False, **cfg)
+        sim.init()
+        nb = sim.state_bytes()
+        host_state = torch.empty(nb // 4, dtype=torch.float32, pin_memory=True)
+        host_mom = torch.empty((4, N ** 3), dtype=torch.float32, pin_memory=True)
+        dptr, mptr = C.c_void_p(host_state.data_ptr()), C.c_void_p(host_mom.data_ptr())
+        lib = sim.lib
+        assert lib.dugks_get_state(sim.h, dptr, nb, 0) == 0
+        for _ in range(2):  # warm pass
+            lib.dugks_set_state(sim.h, dptr, nb, 0)
+            sim.step(1)
+            lib.dugks_moments(sim.h, mptr, 0)
+        torch.cuda.synchronize(dev)
+        per = []
+        for _ in range(trials):
+            t = time.perf_counter()
+            for _ in range(steps):
+                assert lib.dugks_set_state(sim.h, dptr, nb, 0) == 0
+                sim.step(1)
+                assert lib.dugks_moments(sim.h, mptr, 0) == 0
+            per.append((time.perf_counter() - t) / steps)
+        sim.close()
+    finally:
+        os.sched_setaffinity(0, old_aff)
+    return sorted(per)[len(per) // 2], nb, 4 * 4 * N ** 3, local is not None
 
 
 def run_batched(torch, steps, warmup, dev):
@@ -555,9 +586,10 @@ def main():
             extras["adjoint"] = {"error": str(ex)}
     e2e = None
     if rank == 0 and not args.no_extras:
-        sec, bi, bo = run_e2e(torch, max(3, min(10, args.steps // 20)), dev)
+        sec, bi, bo, pinned_local = run_e2e(torch, max(3, min(10, args.steps // 20)), dev)
         e2e = {"value": cells / sec / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
-               "note": "per step: state upload from pinned host, one step, moments to pinned host, via the C ABI"}
+               "note": "per step: state upload from pinned host, one step, moments to pinned host, via the C ABI; "
+                       "median of 3 runs" + ("; on the GPU's local CPUs" if pinned_local else "")}
     cpu = cpu_baseline() if (rank == 0 and ws == 1 and not args.no_extras) else None
     if ws > 1:
         dist.barrier()

@@ -1,4 +1,6 @@
 // aux.cu -- initialisation, moments and FP64 reductions of the DUGKS state (sm_103a).
+// The per-cell sums of 32- and 16-bit states run in compensated FP32; the reductions (residual,
+// conservation totals) accumulate in FP64.
 #include "dugks_internal.h"
 
 namespace dugks {
@@ -54,17 +56,104 @@ __device__ __forceinline__ void cell_moments_d(const StepParams &p, const S *src
     }
 }
 
+// Knuth's TwoSum: s + e == a + b exactly (round to nearest; the intrinsics keep the
+// compiler from reassociating or contracting).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Cell sums of a 32- or 16-bit state in FP32, each carried as an unevaluated pair
+// (compensated summation with TwoSum): drho = r[0] + r[1], sum_k e_ka g_k = j[a][0] + j[a][1].
+// The pair holds the sum to about 2^-48 of sum |g|, as an FP64 sum of the same values would,
+// while the FP64 unit (a small fraction of the FP32 rate on this part) stays free.
+template <int Q, class S>
+__device__ __forceinline__ void cell_sums_f(const StepParams &p, const S *src, int64_t off, float r[2],
+                                            float j[3][2]) {
+    constexpr int D = Lat<Q>::D;
+    r[0] = r[1] = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; a++) j[a][0] = j[a][1] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < Q; k++) {
+        const float g = (float)Store<S>::ld(src + k * p.dstride + off);
+        float t, e;
+        two_sum(r[0], g, t, e);
+        r[0] = t;
+        r[1] += e;
+#pragma unroll
+        for (int a = 0; a < D; a++) {
+            if (Lat<Q>::e(k, a) == 0) continue;
+            two_sum(j[a][0], Lat<Q>::e(k, a) > 0 ? g : -g, t, e);
+            j[a][0] = t;
+            j[a][1] += e;
+        }
+    }
+}
+
+// Cell moments in double from the stored state: drho = sum g, u = c/rho0 sum e g + G dt/2
+// (the sums of 32- and 16-bit states in compensated FP32, converted once).
+template <int Q, class S>
+__device__ __forceinline__ void cell_moments_dd(const StepParams &p, const S *src, int64_t n, int64_t ncell, double ct,
+                                                double dtc, double c, double &drho, double u[3]) {
+    if constexpr (sizeof(S) == 8) {
+        cell_moments_d<Q, S>(p, src, n, ncell, ct, dtc, c, drho, u);
+    } else {
+        constexpr int D = Lat<Q>::D;
+        const int x = (int)(n % p.nx);
+        const int y = (int)((n / p.nx) % p.ny);
+        const int z = (int)(n / ((int64_t)p.nx * p.ny));
+        const int64_t off = (int64_t)z * p.plane + (int64_t)y * p.px + x;
+        float r[2], j[3][2];
+        cell_sums_f<Q, S>(p, src, off, r, j);
+        drho = (double)r[0] + (double)r[1];
+        for (int a = 0; a < 3; a++) {
+            double G = a < D ? (double)p.g[a] : 0.0;
+            if (p.field && a < D) G += (double)p.field[a * ncell + n];
+            u[a] = a < D ? c / (double)p.rho0 * ((double)j[a][0] + (double)j[a][1]) + G * ct * dtc : 0.0;
+        }
+    }
+}
+
+// Moments as FP32 output from a 32- or 16-bit state, without FP64 arithmetic.
+template <int Q, class S>
+__device__ __forceinline__ void cell_moments_out_f(const StepParams &p, const S *src, int64_t n, int64_t ncell,
+                                                   float ctdt, float c_over_rho0, float rt, float *out) {
+    constexpr int D = Lat<Q>::D;
+    const int x = (int)(n % p.nx);
+    const int y = (int)((n / p.nx) % p.ny);
+    const int z = (int)(n / ((int64_t)p.nx * p.ny));
+    const int64_t off = (int64_t)z * p.plane + (int64_t)y * p.px + x;
+    float r[2], j[3][2];
+    cell_sums_f<Q, S>(p, src, off, r, j);
+    out[n] = (r[0] + r[1]) * rt;
+#pragma unroll
+    for (int a = 0; a < D; a++) {
+        float G = (float)p.g[a];
+        if (p.field) G += p.field[a * ncell + n];
+        out[(a + 1) * ncell + n] = fmaf(c_over_rho0, j[a][0] + j[a][1], G * ctdt);
+    }
+}
+
 // Moments (eq. macro_values): out[0] = p = (rho - rho0) RT, out[1+a] = u_a; [dim+1][ncell].
 template <int Q, class S>
 __global__ void moments_kernel(const StepParams p, double ct, double rt, double c, float *out) {
     constexpr int D = Lat<Q>::D;
     const int64_t ncell = (int64_t)p.nx * p.ny * p.nz;
     const S *src = reinterpret_cast<const S *>(p.src);
-    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < ncell; n += (int64_t)gridDim.x * blockDim.x) {
-        double drho, u[3];
-        cell_moments_d<Q, S>(p, src, n, ncell, ct, 0.5 * p.dt, c, drho, u);
-        out[n] = (float)(drho * rt);
-        for (int a = 0; a < D; a++) out[(a + 1) * ncell + n] = (float)u[a];
+    if constexpr (sizeof(S) != 8) {
+        const float ctdt = (float)(ct * 0.5 * p.dt), cr = (float)(c / p.rho0), rtf = (float)rt;
+        for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < ncell; n += (int64_t)gridDim.x * blockDim.x)
+            cell_moments_out_f<Q, S>(p, src, n, ncell, ctdt, cr, rtf, out);
+    } else {
+        for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < ncell;
+             n += (int64_t)gridDim.x * blockDim.x) {
+            double drho, u[3];
+            cell_moments_d<Q, S>(p, src, n, ncell, ct, 0.5 * p.dt, c, drho, u);
+            out[n] = (float)(drho * rt);
+            for (int a = 0; a < D; a++) out[(a + 1) * ncell + n] = (float)u[a];
+        }
     }
 }
 
@@ -83,7 +172,7 @@ __global__ void __launch_bounds__(RES_THREADS) residual_kernel(const StepParams 
     double s[RES_SLOTS] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < ncell; n += (int64_t)gridDim.x * blockDim.x) {
         double drho, u[3];
-        cell_moments_d<Q, S>(p, src, n, ncell, ct, 0.5 * p.dt, c, drho, u);
+        cell_moments_dd<Q, S>(p, src, n, ncell, ct, 0.5 * p.dt, c, drho, u);
         for (int a = 0; a < D; a++) {
             const double du = u[a] - (have_prev ? uprev[a * ncell + n] : 0.0);
             s[0] += du * du;
