@@ -522,14 +522,21 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
     for (int i = 0; i < NF; i++) alz[i] = fzm[i] = 0.0f;
 #pragma unroll
     for (int i = 0; i < 4; i++) Az[i] = 0.0f;
+    // carried too, by the rows that own x interfaces: the x and y differences of the current
+    // plane (per velocity and of the moments), formed with the z parts of the previous
+    // iteration and used again by the x and y parts of this one
+    const bool xrow = row >= 1 && row <= K::TYI;  // warp-uniform
+    float cAX[Q], cAY[Q], mAX[4], mAY[4];
+    if (xrow) {
+        cdiff(z0, AX, cAX);
+        cdiff(z0, AY, cAY);
+        mdiff(z0, AX, mAX);
+        mdiff(z0, AY, mAY);
+    }
     if (upd) {
-        float C1[Q], C2[Q], d1[4], d2[4], bz[NF], Bz[4];
-        cdiff(z0, AX, C1);
-        cdiff(z0, AY, C2);
-        mdiff(z0, AX, d1);
-        mdiff(z0, AY, d2);
+        float bz[NF], Bz[4];
         const float *c = R(slot_of(z0), row, lane);
-        face_parts<Q, 2>(c, c + Q, C1, C2, d1, d2, cf.kappa, alz, bz, Az, Bz);
+        face_parts<Q, 2>(c, c + Q, cAX, cAY, mAX, mAY, cf.kappa, alz, bz, Az, Bz);
         float t[NF];
         direct_face(2, z0 - 1, z0, t);
 #pragma unroll
@@ -558,12 +565,9 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
         float fxp[NF];
 #pragma unroll
         for (int i = 0; i < NF; i++) fxp[i] = 0.0f;
-        if (row >= 1 && row <= K::TYI) {  // warp-uniform: halo rows own no x interface
+        if (xrow) {  // halo rows own no x interface
             float alx[NF], bex[NF], Ax[4], Bx[4];
-            float Cy[Q], dy[4];
-            cdiff(kz, AY, Cy);
-            mdiff(kz, AY, dy);
-            face_parts<Q, 0>(cur, cur + Q, Cy, Cz, dy, dz, cf.kappa, alx, bex, Ax, Bx);
+            face_parts<Q, 0>(cur, cur + Q, cAY, Cz, mAY, dz, cf.kappa, alx, bex, Ax, Bx);
             float F[NF], jb[3];
 #pragma unroll
             for (int i = 0; i < NF; i++) F[i] = alx[i] + __shfl_down_sync(0xffffffffu, bex[i], 1);
@@ -601,8 +605,15 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
         float aly[NF], Ay[4];
         if (ycol) {
             float bey[NF], By[4], Cx[Q], dx[4];
-            cdiff(kz, AX, Cx);
-            mdiff(kz, AX, dx);
+            if (xrow) {
+#pragma unroll
+                for (int k = 0; k < Q; k++) Cx[k] = cAX[k];
+#pragma unroll
+                for (int i = 0; i < 4; i++) dx[i] = mAX[i];
+            } else {
+                cdiff(kz, AX, Cx);
+                mdiff(kz, AX, dx);
+            }
             face_parts<Q, 1>(cur, cur + Q, Cx, Cz, dx, dz, cf.kappa, aly, bey, Ay, By);
             float *b = xb + (row * 32 + lane) * K::BS;
 #pragma unroll
@@ -637,14 +648,16 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
 
         // ---- P2: z parts of plane kz+1 and the z interface kz+1/2 ----
         float alzn[NF], Azn[4], fzp[NF];
+        if (xrow) {
+            cdiff(kz + 1, AX, cAX);
+            cdiff(kz + 1, AY, cAY);
+            mdiff(kz + 1, AX, mAX);
+            mdiff(kz + 1, AY, mAY);
+        }
         if (upd) {
-            float C1[Q], C2[Q], d1[4], d2[4], bezn[NF], Bzn[4];
-            cdiff(kz + 1, AX, C1);
-            cdiff(kz + 1, AY, C2);
-            mdiff(kz + 1, AX, d1);
-            mdiff(kz + 1, AY, d2);
+            float bezn[NF], Bzn[4];
             const float *nxt = R(slot_of(kz + 1), row, lane);
-            face_parts<Q, 2>(nxt, nxt + Q, C1, C2, d1, d2, cf.kappa, alzn, bezn, Azn, Bzn);
+            face_parts<Q, 2>(nxt, nxt + Q, cAX, cAY, mAX, mAY, cf.kappa, alzn, bezn, Azn, Bzn);
             if (!perz && kz + 1 == nz) {
                 float t[NF];
                 direct_face(2, kz, kz + 1, t);

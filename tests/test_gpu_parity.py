@@ -149,6 +149,21 @@ def test_d3q19_force_field_time_dependent():
         assert d < 2e-6, (kernel, d)
 
 
+def test_d3q19_force_field_x_walls():
+    """x walls (one moving) with a per-cell force field and G(t): the throughput kernel takes
+    NEQ at x walls as a correction of its regular interface path, with x_c's values and its
+    interface acceleration from the neighbouring lane."""
+    cfg = dict(shape=(23, 34, 9), q=19, nu=0.04, dt=0.5, g=(0.0, 2e-5, 1e-5), omega=0.03,
+               bcs=[W.wall(), W.wall((0.0, 0.03, 0.01)), W.periodic(), W.periodic(), W.wall(), W.wall()])
+    field = W.force_field(cfg["shape"], 1e-5, seed=23, rel=1.0)
+    p, u = W.random_state_fields(cfg["shape"], seed=29, u_amp=0.02, p_amp=1e-4)
+    for kernel in (0, 1):
+        o, s = run_pair(cfg, 25, p, u, field=field, kernel=kernel)
+        ref = state_dev(o)
+        d = np.abs(state_f64(s) - ref).max() / np.abs(ref).max()
+        assert d < 2e-6, (kernel, d)
+
+
 def test_d3q19_cavity_1000_steps():
     cfg = dict(shape=(24, 20, 18), q=19, nu=0.05, dt=0.5, bcs=W.cavity_bcs(3, 0.1))
     o = Oracle(**cfg)
