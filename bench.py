@@ -44,9 +44,9 @@ Q = 19
 BYTES_PER_VALUE = {0: 4, 1: 2, 2: 2, 3: 8}
 
 
-def workload():
+def workload(q=Q):
     from paper_1411_6121_gb300 import workloads as W
-    return W.cavity3d(n=N, re=RE, lid_u=LID, q=Q)
+    return W.cavity3d(n=N, re=RE, lid_u=LID, q=q)
 
 
 def config_json(extra=None):
@@ -162,13 +162,14 @@ class ClockSampler:
                 "power_w_max": max(pw) if pw else None}
 
 
-def run_form(torch, store, steps, warmup, dev, tile=None):
-    """Times `steps` fused steps of the 256^3 cube (storage `store`) after `warmup`.
-    Returns (ms per step, mean fused-kernel ms, launches of our kernels in the region)."""
+def run_form(torch, store, steps, warmup, dev, tile=None, q=Q, kernel=0):
+    """Times `steps` fused steps of the 256^3 cube (storage `store`, velocity set q, kernel
+    selector `kernel`) after `warmup`. Returns (ms per step, mean fused-kernel ms, launches of
+    our kernels in the region, the last residual)."""
     from paper_1411_6121_gb300 import dugks
-    cfg = workload()
+    cfg = workload(q)
     stream = torch.cuda.Stream(device=dev)
-    sim = dugks.Sim(store=store, stream=stream.cuda_stream, use_graph=False, tile=tile, **cfg)
+    sim = dugks.Sim(store=store, stream=stream.cuda_stream, use_graph=False, tile=tile, kernel=kernel, **cfg)
     sim.init()
     sim.residual()
     for i in range(warmup):
@@ -574,6 +575,20 @@ def main():
                                              "frac": ach / peak, "bytes_per_cell_update": 2 * Q * BYTES_PER_VALUE[store]}}
             except Exception as ex:  # reported, not hidden
                 extras[name] = {"error": str(ex)}
+    if not args.no_extras and rank == 0:
+        # the paper's own 3D set (D3Q27, 216 B per cell update in FP32) on the same cube, through
+        # the throughput kernel and the reference kernel
+        try:
+            d27 = {"unit": "MLUPS", "bytes_per_cell_update": 2 * 27 * 4}
+            for kern, name in ((0, "throughput"), (1, "reference")):
+                ms_s, ms_k, _, _ = run_form(torch, 0, max(20, args.steps // 4), warmup, dev, q=27, kernel=kern)
+                ach = 2 * 27 * 4 * cells / (ms_k * 1e-3) / 1e9
+                d27[name] = {"value": cells / (ms_s * 1e-3) / 1e6, "ms_per_step": ms_s,
+                             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                          "frac": ach / peak}}
+            extras["d3q27"] = d27
+        except Exception as ex:
+            extras["d3q27"] = {"error": str(ex)}
     if not args.no_extras and rank == 0:
         try:
             extras["batched"] = run_batched(torch, max(50, args.steps), warmup, dev)

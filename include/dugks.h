@@ -104,7 +104,8 @@ typedef struct {
     int32_t use_graph;      /* 1: dugks_step replays a captured CUDA graph (default) */
     int32_t tile_x, tile_y; /* 0: default tile. Throughput kernels (kernel 0, F32/BF16/F16
                                storage): tile_y = thread-block rows (D2Q9: 4, 8 or 16;
-                               D3Q19: 8 or 10; default 8), tile_x ignored. Reference
+                               D3Q19: 8 or 10; D3Q27: 8; default 8), tile_x ignored.
+                               Reference
                                kernel: tile_x x tile_y = 32x8 or 16x8                   */
     int32_t kernel;         /* 0: fastest kernel built for the case (default);
                                1: the reference fused kernel (any lattice/storage)     */

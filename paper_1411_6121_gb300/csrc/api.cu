@@ -89,6 +89,7 @@ StepParams dugks::handle_params(const dugks_t h) {
 cudaError_t dugks::handle_launch_step(dugks_t h, StepParams &p) {
     if (h->kernel == 0 && h->q == 19 && h->store != DUGKS_STORE_F64)
         return launch_step3d_q19(p, h->store, h->ry3d, h->stream);
+    if (h->kernel == 0 && h->q == 27 && h->store != DUGKS_STORE_F64) return launch_step3d_q27(p, h->store, h->stream);
     if (h->kernel == 0 && h->q == 9 && h->store != DUGKS_STORE_F64)
         return launch_step2d_q9(p, h->store, h->ry3d, h->stream);
     switch (h->q) {
@@ -151,13 +152,14 @@ int dugks_create(const dugks_mesh *mesh, int32_t lattice, double nu, double dt, 
     }
     // tile of the reference kernel (tile_x x tile_y cells), or, for the D3Q19 throughput
     // kernel, tile_y = rows of its 32 x tile_y thread block
-    const bool thr3d = o.kernel == 0 && lattice == DUGKS_D3Q19 && o.store != DUGKS_STORE_F64;
+    const bool thr3d = o.kernel == 0 && (lattice == DUGKS_D3Q19 || lattice == DUGKS_D3Q27) && o.store != DUGKS_STORE_F64;
     const bool thr2d = o.kernel == 0 && lattice == DUGKS_D2Q9 && o.store != DUGKS_STORE_F64;
     int tx = o.tile_x, ty = o.tile_y;
     int ry3d = 8;  // CTA rows of the throughput kernels
     if (thr3d) {
         if (ty != 0) ry3d = ty;
-        if (!(ry3d == 8 || ry3d == 10)) return handle_fail(NULL, DUGKS_E_UNSUPPORTED, "3D kernel rows %d not built", ry3d);
+        if (!(ry3d == 8 || (ry3d == 10 && lattice == DUGKS_D3Q19)))
+            return handle_fail(NULL, DUGKS_E_UNSUPPORTED, "3D kernel rows %d not built", ry3d);
         tx = 32;
         ty = 8;
     } else if (thr2d) {

@@ -16,6 +16,8 @@ cudaError_t launch_step_q19(const StepParams &p, int store, int tx, int ty, cuda
 cudaError_t launch_step_q27(const StepParams &p, int store, int tx, int ty, cudaStream_t stream);
 // Throughput kernel for D3Q19 with F32/BF16/F16 storage (dugks_step3d.cuh); ry = CTA rows.
 cudaError_t launch_step3d_q19(const StepParams &p, int store, int ry, cudaStream_t stream);
+// The same throughput kernel for D3Q27 (32 x 8 columns per CTA).
+cudaError_t launch_step3d_q27(const StepParams &p, int store, cudaStream_t stream);
 // Throughput kernel for D2Q9 with F32/BF16/F16 storage (dugks_step2d.cuh); ry = CTA rows
 // (4, 8 or 16; the inner tile is 30 x (ry - 2) cells). The batch form walks a work list of
 // (instance, x0, y0) inner-tile origins over params[2 i + parity] on a persistent grid.

@@ -137,8 +137,9 @@ def test_3d_state_elementwise(name, store, kernel):
     assert np.abs(got - ref).max() < tol * scale, (np.abs(got - ref).max(), scale)
 
 
-def test_d3q19_force_field_time_dependent():
-    cfg = dict(shape=(37, 18, 11), q=19, nu=0.04, dt=0.5, g=(1e-5, 0.0, -1e-5), omega=0.02,
+@pytest.mark.parametrize("q", [19, 27])
+def test_3d_force_field_time_dependent(q):
+    cfg = dict(shape=(37, 18, 11), q=q, nu=0.04, dt=0.5, g=(1e-5, 0.0, -1e-5), omega=0.02,
                bcs=[W.periodic(), W.periodic(), W.wall(), W.wall((0.02, 0.0, 0.01)), W.periodic(), W.periodic()])
     field = W.force_field(cfg["shape"], 1e-5, seed=19, rel=1.0)
     p, u = W.random_state_fields(cfg["shape"], seed=7, u_amp=0.02, p_amp=1e-4)
@@ -149,11 +150,12 @@ def test_d3q19_force_field_time_dependent():
         assert d < 2e-6, (kernel, d)
 
 
-def test_d3q19_force_field_x_walls():
+@pytest.mark.parametrize("q", [19, 27])
+def test_3d_force_field_x_walls(q):
     """x walls (one moving) with a per-cell force field and G(t): the throughput kernel takes
     NEQ at x walls as a correction of its regular interface path, with x_c's values and its
     interface acceleration from the neighbouring lane."""
-    cfg = dict(shape=(23, 34, 9), q=19, nu=0.04, dt=0.5, g=(0.0, 2e-5, 1e-5), omega=0.03,
+    cfg = dict(shape=(23, 34, 9), q=q, nu=0.04, dt=0.5, g=(0.0, 2e-5, 1e-5), omega=0.03,
                bcs=[W.wall(), W.wall((0.0, 0.03, 0.01)), W.periodic(), W.periodic(), W.wall(), W.wall()])
     field = W.force_field(cfg["shape"], 1e-5, seed=23, rel=1.0)
     p, u = W.random_state_fields(cfg["shape"], seed=29, u_amp=0.02, p_amp=1e-4)
@@ -177,6 +179,23 @@ def test_d3q19_cavity_1000_steps():
         s = _sim(store=store, kernel=kernel, **cfg)
         s.init()
         s.step(1000)
+        got = s.moments()
+        assert rel_l2(got[1:], ref[1:]) < tol, (store, kernel, rel_l2(got[1:], ref[1:]))
+        assert rel_l2(got[0], ref[0]) < ptol, (store, kernel, rel_l2(got[0], ref[0]))
+
+
+def test_d3q27_cavity_300_steps():
+    """The paper's 3D velocity set through the throughput kernel, every storage: FP32 within the
+    FP32 drift, the 16-bit stores within the bounds of the D3Q19 cube test."""
+    cfg = dict(shape=(24, 20, 18), q=27, nu=0.05, dt=0.5, bcs=W.cavity_bcs(3, 0.1))
+    o = Oracle(**cfg)
+    o.init()
+    o.step(300)
+    ref = o.moments()
+    for store, kernel, tol, ptol in ((0, 0, 2e-5, 2e-5), (0, 1, 2e-5, 2e-5), (2, 0, 1e-3, 2e-3), (1, 0, 3e-3, 1.5e-2)):
+        s = _sim(store=store, kernel=kernel, **cfg)
+        s.init()
+        s.step(300)
         got = s.moments()
         assert rel_l2(got[1:], ref[1:]) < tol, (store, kernel, rel_l2(got[1:], ref[1:]))
         assert rel_l2(got[0], ref[0]) < ptol, (store, kernel, rel_l2(got[0], ref[0]))
