@@ -67,6 +67,8 @@ extern "C" {
 #define DUGKS_BC_PERIODIC 0
 #define DUGKS_BC_NEQ_VELOCITY 1 /* eq. NEQ, velocity condition: u_a = u_w, rho_a = rho(x_c)  */
 #define DUGKS_BC_NEQ_PRESSURE 2 /* eq. NEQ, pressure condition: rho_a = rho0 + p_w/RT, u_a = u(x_c) */
+#define DUGKS_BC_BOUNCE_BACK 3  /* eq. BB: fbar_k = fbar_-k + 2 rho0 W_k xi_k.u_w / RT for xi.n < 0
+                                   (rho_w = rho0), at the wall interface before step 6        */
 
 /* ---- parameter records ----------------------------------------------------------- */
 typedef struct {
@@ -78,7 +80,7 @@ typedef struct {
 
 typedef struct {
     int32_t type;    /* DUGKS_BC_* */
-    double u[3];     /* wall velocity u_w (velocity condition) */
+    double u[3];     /* wall velocity u_w (velocity condition, bounce-back) */
     double p;        /* wall pressure p_w = (rho_w - rho0) RT (pressure condition) */
 } dugks_face_bc;
 

@@ -46,6 +46,10 @@
  *      corner velocities removed and the standard weights 1/3, 1/18, 1/36; it has the
  *      same moments up to fourth order, which is all eq. icfeq uses.
  *  R9  Pressure p = (rho - rho0) RT (the paper initialises rho = rho0 + p/RT).
+ *  R10 Bounce-back (Sec. 2.4, eq. BB) is applied, like NEQ, to fbar at the wall interface
+ *      in the Appendix's step 5: for xi_k . n < 0, fbar_k = fbar_(-k) + 2 rho_w W_k
+ *      xi_k . u_w / RT, with the opposite velocity's step-4 value at the same interface
+ *      and rho_w = rho0 (the incompressible limit the paper names).
  *
  * Complex-step build: compiled with -DORACLE_COMPLEX_STEP the same code runs on
  * double _Complex values. The scheme only adds, subtracts and multiplies state values, so
@@ -72,6 +76,7 @@ void oracle_destroy(void *p);
 #define BC_PERIODIC 0
 #define BC_NEQ_VELOCITY 1
 #define BC_NEQ_PRESSURE 2
+#define BC_BOUNCE_BACK 3
 
 /* Plain configuration record (mirrored by ctypes in oracle.py). */
 typedef struct {
@@ -178,6 +183,14 @@ static real source(const ostate *s, int k, const real G[3], const real u[3], rea
     real gx = 0;
     for (int a = 0; a < 3; a++) gx += G[a] * (s->c * s->e[k][a] - u[a]);
     return gx / s->cfg.rt * fe;
+}
+
+/* Index of the velocity opposite to k. */
+static int opposite(const ostate *s, int k)
+{
+    for (int j = 0; j < s->Q; j++)
+        if (s->e[j][0] == -s->e[k][0] && s->e[j][1] == -s->e[k][1] && s->e[j][2] == -s->e[k][2]) return j;
+    return k;
 }
 
 /* Macroscopic variables, eq. macro_values (cell, weight dt/2) and the Appendix's step 6
@@ -398,7 +411,7 @@ static void step_once(ostate *s)
     }
 
     /* Step 5: boundary processing of fbar at the wall interfaces: NEQ, eq. NEQ
-     * (reading R4). */
+     * (reading R4), or bounce-back, eq. BB (reading R10). */
     for (int d = 0; d < D; d++) {
         if (s->cfg.bc_type[2 * d] == BC_PERIODIC) continue;
         for (int side = 0; side < 2; side++) {
@@ -411,6 +424,16 @@ static void step_once(ostate *s)
             for (x[2] = lo[2]; x[2] <= hi[2]; x[2]++)
                 for (x[1] = lo[1]; x[1] <= hi[1]; x[1]++)
                     for (x[0] = lo[0]; x[0] <= hi[0]; x[0]++) {
+                        if (type == BC_BOUNCE_BACK) {
+                            real *Fw = s->Fb[d] + face_index(s, d, x) * Q;
+                            for (int k = 0; k < Q; k++) {
+                                if (nsign * s->e[k][d] >= 0) continue; /* only xi.n < 0 */
+                                real xu = 0;
+                                for (int a = 0; a < 3; a++) xu += s->c * s->e[k][a] * s->wall_u[wall][a];
+                                Fw[k] = Fw[opposite(s, k)] + 2.0 * rho0 * s->W[k] * xu / s->cfg.rt;
+                            }
+                            continue;
+                        }
                         int xc[3] = {x[0], x[1], x[2]};
                         xc[d] = side == 0 ? 1 : s->n[d] - 1;
                         const real *Fc = s->Fb[d] + face_index(s, d, xc) * Q;
@@ -518,7 +541,7 @@ static int check_config(const oracle_config *c)
     for (int d = 0; d < c->dim; d++) {
         const int lo = c->bc_type[2 * d], hi = c->bc_type[2 * d + 1];
         if ((lo == BC_PERIODIC) != (hi == BC_PERIODIC)) return -1;
-        if (lo < 0 || lo > 2 || hi < 0 || hi > 2) return -1;
+        if (lo < 0 || lo > 3 || hi < 0 || hi > 3) return -1;
         if (lo != BC_PERIODIC && n[d] < 2) return -1;
     }
     return 0;

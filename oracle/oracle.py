@@ -14,6 +14,7 @@ from . import build as _build
 BC_PERIODIC = 0
 BC_NEQ_VELOCITY = 1
 BC_NEQ_PRESSURE = 2
+BC_BOUNCE_BACK = 3
 
 
 class OracleConfig(C.Structure):

@@ -272,7 +272,7 @@ struct FaceLane {
     T F, Fc;               // step-4 value of the lane's velocity (incoming ones replaced at a
                            // wall, step 5) and its value at x_c (wall only)
     T dr, m[2], Gh[2];     // step-6 moments and the interface acceleration
-    int wall, side;
+    int wall, side, bb;    // bb: bounce-back wall (eq. BB)
     T drc, mc[2];          // moments at x_c (wall only)
     T ma[2];               // m_a of step 5 (wall only)
 };
@@ -287,7 +287,15 @@ __device__ __forceinline__ void face_forward_lane(const AdjParams<T> &a, int d, 
     s.side = pos == 0 ? 0 : 1;
     face_Gh(a, d, i, j, s.Gh);
     s.Fc = T(0);
-    if (s.wall) {
+    s.bb = s.wall && a.bc[2 * d + s.side] == DUGKS_BC_BOUNCE_BACK;
+    if (s.bb) {
+        // step 5, eq. BB: the incoming velocity takes its opposite's value (lane 8 - k of the
+        // half) plus 6 W_k e_k.m_w
+        const T Fo = __shfl_sync(0xffffu << (threadIdx.x & 16), s.F, Q - 1 - k, 16);
+        const int sgn = s.side == 0 ? -1 : 1;
+        const T *mw = a.mw[2 * d + s.side];
+        if (act && sgn * L9::e(k, d) < 0) s.F = Fo + T(6) * L9::wt<T>(k) * (e0 * mw[0] + e1 * mw[1]);
+    } else if (s.wall) {
         // x_c: the boundary cell's opposite interface (reading R4)
         const int sh = s.side == 0 ? 1 : -1;
         const int ci = d == 0 ? i + sh : i, cj = d == 1 ? j + sh : j;
@@ -349,6 +357,19 @@ __device__ __forceinline__ void face_adjoint_lane(const AdjParams<T> &a, int d, 
     Gcb[0] = Gcb[1] = T(0);
     Wb[0] = Wb[1] = T(0);
     if (!wall) return;
+    if (s.bb) {
+        // step 5, eq. BB: F_k = F_-k + 6 W_k e_k.m_w for incoming k: the weight of an
+        // incoming velocity passes to its opposite (lane 8 - k) and to u_w
+        const int sgn = s.side == 0 ? -1 : 1;
+        const bool incoming = act && sgn * ed < 0;
+        const T w = incoming ? Fb : T(0);
+        const T back = __shfl_sync(0xffffu << (threadIdx.x & 16), w, Q - 1 - k, 16);
+        Fb = (incoming ? T(0) : Fb) + back;
+        const T c6 = T(6) * L9::wt<T>(k) * w * a.dmw;
+        Wb[0] = wsum(c6 * e0);
+        Wb[1] = wsum(c6 * e1);
+        return;
+    }
     // step 5 (eq. NEQ): F_k = geq_k(drho_a, m_a) + Fc_k - geq_k(drho_c, m_c), incoming k.
     // Velocity condition: drho_a = drho_c (the W_k terms cancel), m_a from u_w.
     // Pressure condition: m_a = m_c (the m terms cancel), drho_a fixed.
@@ -585,7 +606,8 @@ __device__ __noinline__ void faces_frame_item(const AdjParams<T> &a, int64_t t) 
     T Fb, Gb[2], Fcb, Gcb[2], Wb[2];
     int wall;
     face_adjoint_lane(a, d, i, j, k, act, Fb, Gb, Fcb, Gcb, Wb, wall);
-    if (wall && a.dW && lane == 0 && a.bc[2 * d + (pos == 0 ? 0 : 1)] == DUGKS_BC_NEQ_VELOCITY) {
+    const int wbc = a.bc[2 * d + (pos == 0 ? 0 : 1)];
+    if (wall && a.dW && lane == 0 && (wbc == DUGKS_BC_NEQ_VELOCITY || wbc == DUGKS_BC_BOUNCE_BACK)) {
         const int64_t slot = d == 0 ? (pos == 0 ? 0 : a.n[1]) + j : 2 * (int64_t)a.n[1] + (pos == 0 ? 0 : a.n[0]) + i;
         a.dW[2 * slot] += (double)Wb[0];
         a.dW[2 * slot + 1] += (double)Wb[1];
@@ -760,6 +782,9 @@ __global__ void adj_to_float(const double *src, float *dst, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         dst[i] = (float)src[i];
 }
+
+// Face types whose wall velocity enters the step (and so has a gradient).
+static int moving_wall(int type) { return type == DUGKS_BC_NEQ_VELOCITY || type == DUGKS_BC_BOUNCE_BACK; }
 
 int blocks_for(int64_t n, int threads) {
     const int64_t b = (n + threads - 1) / threads;
@@ -986,8 +1011,8 @@ int enqueue_adjoint(dugks_t h, const float *dL_dmom, float *dL_dfield, void *dL_
         if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "adjoint: %s", cudaGetErrorString(e));
     }
     adj_wall_sum<<<1, 32, 0, st>>>(t.dW, t.dW_face, (int)h->nx, (int)h->ny,
-                                   h->bcs.face[0].type == DUGKS_BC_NEQ_VELOCITY, h->bcs.face[1].type == DUGKS_BC_NEQ_VELOCITY,
-                                   h->bcs.face[2].type == DUGKS_BC_NEQ_VELOCITY, h->bcs.face[3].type == DUGKS_BC_NEQ_VELOCITY);
+                                   moving_wall(h->bcs.face[0].type), moving_wall(h->bcs.face[1].type),
+                                   moving_wall(h->bcs.face[2].type), moving_wall(h->bcs.face[3].type));
     h->launches++;
     e = cudaMemcpyAsync(t.h_wall, t.dW_face, sizeof(double) * 18, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaGetLastError();

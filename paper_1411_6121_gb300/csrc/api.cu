@@ -145,7 +145,7 @@ int dugks_create(const dugks_mesh *mesh, int32_t lattice, double nu, double dt, 
     for (int d = 0; d < 3; d++) {
         const int lo = bcs->face[2 * d].type, hi = bcs->face[2 * d + 1].type;
         if (d >= dim) continue;
-        if (lo < 0 || lo > 2 || hi < 0 || hi > 2) return handle_fail(NULL, DUGKS_E_INVAL, "bad boundary type");
+        if (lo < 0 || lo > 3 || hi < 0 || hi > 3) return handle_fail(NULL, DUGKS_E_INVAL, "bad boundary type");
         if ((lo == DUGKS_BC_PERIODIC) != (hi == DUGKS_BC_PERIODIC))
             return handle_fail(NULL, DUGKS_E_INVAL, "periodic faces must be paired (axis %d)", d);
         if (lo != DUGKS_BC_PERIODIC && n[d] < 2) return handle_fail(NULL, DUGKS_E_INVAL, "a wall axis needs >= 2 cells");

@@ -235,7 +235,7 @@ int dugks_batch_create(int32_t count, const dugks_mesh *meshes, const double *nu
         const int64_t n[2] = {m.nx, m.ny};
         for (int d = 0; d < 2; d++) {
             const int lo = bcs[i].face[2 * d].type, hi = bcs[i].face[2 * d + 1].type;
-            if (lo < 0 || lo > 2 || hi < 0 || hi > 2 || ((lo == 0) != (hi == 0)) || (lo != 0 && n[d] < 2))
+            if (lo < 0 || lo > 3 || hi < 0 || hi > 3 || ((lo == 0) != (hi == 0)) || (lo != 0 && n[d] < 2))
                 return bfail(nullptr, DUGKS_E_INVAL, "instance %d: bad boundaries on axis %d", i, d);
         }
     }

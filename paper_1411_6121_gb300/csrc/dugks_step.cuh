@@ -62,15 +62,37 @@ __device__ __forceinline__ void reconstruct(const T *L, const T *R, const T *L1m
 }
 
 // Steps 5-7 at one interface normal to axis d. F: step-4 values (modified in place by the
-// NEQ condition when wall != 0). Fc: step-4 values at x_c, the boundary cell's opposite
-// interface (read only when wall != 0). side: 0 for the low wall (outward normal -e_d),
+// wall condition, NEQ or bounce-back, when wall != 0). Fc: step-4 values at x_c, the boundary
+// cell's opposite interface (read only by NEQ). side: 0 for the low wall (outward normal -e_d),
 // 1 for the high wall. Writes the original f of eq. original_f for the velocities with
 // e_d != 0 into out[flux_index(d, k)] (stride 1).
 template <int Q, int d, class T>
 __device__ __forceinline__ void interface_f(const StepParams &p, const Coef<T> &cf, T F[Q], const T Gh[3], int wall,
                                             int side, const T *Fc, const T Ghc[3], T *out) {
     constexpr int D = Lat<Q>::D;
-    if (wall) {
+    if (wall && p.bc[2 * d + side] == 3) {
+        // Step 5, eq. BB: F_k = F_-k + 2 rho0 W_k xi_k.u_w / RT for xi . n < 0, i.e.
+        // g_k = g_-k + 6 W_k e_k.m_w with m_w = rho0 u_w / c (deviations: W_k = W_-k)
+        const int wid = 2 * d + side;
+        T mw[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) mw[a] = (T)(p.bc_u[wid][a] * p.rho0 * p.inv_c);
+        const int sgn = side == 0 ? -1 : 1;
+        sfor<Q>([&](auto kc) {
+            constexpr int k = kc;
+            if constexpr (Lat<Q>::e(k, d) != 0) {
+                if (sgn * Lat<Q>::e(k, d) < 0) {
+                    T em = T(0);
+#pragma unroll
+                    for (int a = 0; a < D; a++) {
+                        if (Lat<Q>::e(k, a) > 0) em += mw[a];
+                        if (Lat<Q>::e(k, a) < 0) em -= mw[a];
+                    }
+                    F[k] = F[opposite<Q>(k)] + wmul<Q, T>(k, T(6) * em);
+                }
+            }
+        });
+    } else if (wall) {
         // Step 5, eq. NEQ: f(x_w) = f_eq(rho_a, u_a) + [f(x_c) - f_eq(rho_c, u_c)] for
         // xi . n < 0, applied to fbar (Appendix step 5) with the moments of step 6 at x_c.
         const int wid = 2 * d + side;

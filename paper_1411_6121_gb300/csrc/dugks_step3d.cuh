@@ -198,18 +198,49 @@ __device__ __forceinline__ void face_relax(const Coef<float> &cf, const float *F
     });
 }
 
-// Step 5 (eq. NEQ) at a wall interface normal to d, formed from the values of the regular
-// path: F (compact step-4 values of the crossing velocities) and its interface moments (drb,
-// jb: sums over all velocities, without the force shift), and the same at x_c, the boundary
-// cell's opposite interface (Fc, drc, jc, with its acceleration Ghc). The velocities that
-// enter from the wall (e_d > 0 at the low wall, SIDE 0; e_d < 0 at the high wall, SIDE 1)
-// become f_eq(rho_a, u_a) + [Fc - f_eq(rho_c, u_c)], and the interface moments take the
+// Step 5 at a wall interface normal to d, formed from the values of the regular path: F
+// (compact step-4 values of the crossing velocities) and its interface moments (drb, jb: sums
+// over all velocities, without the force shift), and the same at x_c, the boundary cell's
+// opposite interface (Fc, drc, jc, with its acceleration Ghc). The velocities that enter from
+// the wall (e_d > 0 at the low wall, SIDE 0; e_d < 0 at the high wall, SIDE 1) become
+// f_eq(rho_a, u_a) + [Fc - f_eq(rho_c, u_c)] (eq. NEQ), or, at a bounce-back wall, the
+// opposite velocity's value plus the wall term of eq. BB. The interface moments take the
 // moments of that change, so step 6 sees the moments of the modified values.
 template <int Q, int d, bool FORCE, int SIDE>
 __device__ __forceinline__ void neq_wall(const StepParams &p, const Coef<float> &cf, float *F, float &drb,
                                          float jb[3], const float *Fc, float drc, const float jc[3],
                                          const float Ghc[3]) {
     constexpr int wid = 2 * d + SIDE;
+    if (p.bc[wid] == 3) {
+        // eq. BB instead: F_k = F_-k + 6 W_k e_k.m_w (m_w = rho0 u_w / c), from this
+        // interface's own values
+        float mw[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) mw[a] = (float)(p.bc_u[wid][a] * p.rho0 * p.inv_c);
+        sfor<Q>([&](auto kc) {
+            constexpr int k = kc;
+            constexpr int ed = Lat<Q>::e(k, d);
+            if constexpr (SIDE == 0 ? ed > 0 : ed < 0) {
+                constexpr int i = flux_index<Q>(d, k), ib = flux_index<Q>(d, opposite<Q>(k));
+                float em = 0.0f;
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    if (Lat<Q>::e(k, a) > 0) em += mw[a];
+                    if (Lat<Q>::e(k, a) < 0) em -= mw[a];
+                }
+                const float v = F[ib] + wmul<Q, float>(k, 6.0f * em);
+                const float dv = v - F[i];
+                drb += dv;
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    if (Lat<Q>::e(k, a) > 0) jb[a] += dv;
+                    if (Lat<Q>::e(k, a) < 0) jb[a] -= dv;
+                }
+                F[i] = v;
+            }
+        });
+        return;
+    }
     float mc[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) mc[a] = FORCE ? fmaf(Ghc[a], cf.wface * cf.rho0, jc[a]) : jc[a];

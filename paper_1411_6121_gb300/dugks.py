@@ -20,7 +20,7 @@ ERRORS = {
 }
 D2Q9, D3Q19, D3Q27 = 9, 19, 27
 STORE_F32, STORE_BF16, STORE_F16, STORE_F64 = 0, 1, 2, 3
-BC_PERIODIC, BC_NEQ_VELOCITY, BC_NEQ_PRESSURE = 0, 1, 2
+BC_PERIODIC, BC_NEQ_VELOCITY, BC_NEQ_PRESSURE, BC_BOUNCE_BACK = 0, 1, 2, 3
 
 LIB_PATH = _build.LIB
 

@@ -12,6 +12,7 @@ import numpy as np
 BC_PERIODIC = 0
 BC_NEQ_VELOCITY = 1
 BC_NEQ_PRESSURE = 2
+BC_BOUNCE_BACK = 3
 
 RT_LATTICE = 1.0 / 3.0
 RHO0 = 1.0
@@ -33,6 +34,11 @@ def wall(u=(0.0, 0.0, 0.0)):
 
 def pressure(p):
     return (BC_NEQ_PRESSURE, (0.0, 0.0, 0.0), float(p))
+
+
+def bounce_back(u=(0.0, 0.0, 0.0)):
+    """Bounce-back wall (eq. BB) moving with velocity u."""
+    return (BC_BOUNCE_BACK, tuple(float(a) for a in u) + (0.0,) * (3 - len(u)), 0.0)
 
 
 def channel_bcs(dim=2):

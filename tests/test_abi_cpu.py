@@ -50,7 +50,8 @@ def test_cfl_violation_rejected():
 
 @pytest.mark.parametrize("kw", [dict(dim=4), dict(q=19), dict(dim=3, q=9, nz=4), dict(nx=0), dict(nu=-1.0),
                                 dict(bcs=[(1, (0, 0, 0), 0.0), (0, (0, 0, 0), 0.0)]),
-                                dict(nx=1, bcs=[(1, (0, 0, 0), 0.0), (1, (0, 0, 0), 0.0)])])
+                                dict(nx=1, bcs=[(1, (0, 0, 0), 0.0), (1, (0, 0, 0), 0.0)]),
+                                dict(bcs=[(4, (0, 0, 0), 0.0), (4, (0, 0, 0), 0.0)])])
 def test_invalid_arguments_rejected(kw):
     rc, h, msg = _create(**kw)
     assert rc in (-1, -7) and not h.value and msg
@@ -62,3 +63,10 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.dugks_init(None, None, None) == -1
     assert lib.dugks_sync(None, 0.1) == -1
     lib.dugks_destroy(None)
+
+
+def test_header_constants_match_binding():
+    src = open(os.path.join(ROOT, "include", "dugks.h")).read()
+    consts = dict((k, int(v)) for k, v in re.findall(r"#define DUGKS_(BC_[A-Z_]+|STORE_[A-Z0-9_]+)\s+(-?\d+)", src))
+    for name, value in consts.items():
+        assert getattr(dugks, name) == value, name

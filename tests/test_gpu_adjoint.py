@@ -32,7 +32,7 @@ def _sim(**kw):
 
 
 # tiny grids: every boundary kind of the adjoint (periodic seams, NEQ velocity walls with a
-# moving lid, a pressure wall, corners), a field, a time-dependent G
+# moving lid, a pressure wall, bounce-back walls, corners), a field, a time-dependent G
 CASES = {
     "channel_lid": dict(shape=(6, 5), q=9, nu=0.05, dt=0.5, g=(2e-5, 0.0, 0.0),
                         bcs=[W.periodic(), W.periodic(), W.wall(), W.wall((0.03, 0.0, 0.0))]),
@@ -47,6 +47,12 @@ CASES = {
     "periodic_wide": dict(shape=(10, 8), q=9, nu=0.04, dt=0.5, g=(1e-5, 2e-5, 0.0), bcs=W.all_periodic()),
     "cavity_wide": dict(shape=(9, 10), q=9, nu=0.04, dt=0.5,
                         bcs=[W.wall(), W.pressure(-1e-3), W.wall(), W.wall((0.05, 0.0, 0.0))]),
+    # bounce-back walls (eq. BB): a moving one, and beside NEQ walls
+    "bb_channel": dict(shape=(6, 5), q=9, nu=0.05, dt=0.5, g=(2e-5, 0.0, 0.0),
+                       bcs=[W.periodic(), W.periodic(), W.bounce_back(), W.bounce_back((0.03, 0.0, 0.0))]),
+    "bb_cavity_wide": dict(shape=(9, 10), q=9, nu=0.04, dt=0.5, g=(1e-5, 0.0, 0.0),
+                           bcs=[W.bounce_back((0.0, 0.01, 0.0)), W.bounce_back(), W.wall(),
+                                W.bounce_back((0.05, 0.0, 0.0))]),
 }
 STEPS = 12
 
@@ -110,7 +116,7 @@ def test_adjoint_equals_oracle_complex_step(case):
     # wall velocities: every velocity-wall face, tangential and normal component
     wref = np.zeros((6, 3))
     for f in range(4):
-        if cfg["bcs"][f][0] != W.BC_NEQ_VELOCITY:
+        if cfg["bcs"][f][0] not in (W.BC_NEQ_VELOCITY, W.BC_BOUNCE_BACK):
             continue
         for a in range(2):
             d = np.zeros(18)

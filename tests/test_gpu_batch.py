@@ -23,6 +23,8 @@ def _instances():
         dict(shape=(40, 21), nu=0.04, bcs=W.cavity_bcs(2, 0.08)),
         dict(shape=(32, 16), nu=0.03, bcs=[W.pressure(1e-3), W.pressure(-1e-3), W.wall(), W.wall()]),
         dict(shape=(50, 26), nu=0.06, g=(1e-5, 0.0, 0.0), omega=0.02, field=fld, bcs=W.channel_bcs(2)),
+        dict(shape=(31, 18), nu=0.03, g=(1e-5, 0.0, 0.0),
+             bcs=[W.periodic(), W.periodic(), W.bounce_back(), W.bounce_back((0.02, 0.0))]),
     ]
 
 
@@ -59,8 +61,8 @@ def test_batch_matches_single_instances_and_oracle(tile):
         got = b.moments(i)
         ref = _single(d, 60, *fields[i], tile)
         assert np.array_equal(got, ref), (tile, i)
-    # two instances against the oracle
-    for i in (0, 3):
+    # three instances against the oracle (the last one has bounce-back walls)
+    for i in (0, 3, 5):
         d = ins[i]
         o = Oracle(d["shape"], 9, nu=d["nu"], dt=0.5, g=d.get("g", (0, 0, 0)), bcs=d["bcs"])
         o.init(*fields[i])

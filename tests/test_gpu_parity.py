@@ -58,6 +58,12 @@ CASES_2D = {
     "cavity": dict(shape=(45, 38), q=9, nu=0.05, dt=0.5, bcs=W.cavity_bcs(2, 0.1)),
     "pressure": dict(shape=(36, 19), q=9, nu=0.04, dt=0.5,
                      bcs=[W.pressure(1e-3), W.pressure(-1e-3), W.wall(), W.wall()]),
+    # bounce-back walls (eq. BB): a closed box with a moving lid, and pressure-driven flow
+    # between bounce-back walls (NEQ pressure inlet and outlet)
+    "bb_cavity": dict(shape=(45, 38), q=9, nu=0.05, dt=0.5,
+                      bcs=[W.bounce_back(), W.bounce_back(), W.bounce_back(), W.bounce_back((0.1, 0.0))]),
+    "bb_pressure": dict(shape=(36, 19), q=9, nu=0.04, dt=0.5, g=(0.0, 1e-5, 0.0),
+                        bcs=[W.pressure(1e-3), W.pressure(-1e-3), W.bounce_back(), W.bounce_back((0.02, 0.0))]),
 }
 
 
@@ -76,6 +82,17 @@ def test_d2q9_state_elementwise(name, store):
 
 def state_f64(s):
     return s.get_state().astype(np.float64)
+
+
+@pytest.mark.parametrize("name", ["bb_cavity", "bb_pressure"])
+def test_d2q9_bounce_back_reference_kernel(name):
+    """Bounce-back through the reference kernel (the throughput kernel runs in the
+    element-wise test above)."""
+    cfg = CASES_2D[name]
+    p, u = W.random_state_fields(cfg["shape"], seed=sum(map(ord, name)), u_amp=0.03, p_amp=1e-3)
+    o, s = run_pair(cfg, 20, p, u, kernel=1)
+    ref = state_dev(o)
+    assert np.abs(state_f64(s) - ref).max() < 2e-6 * np.abs(ref).max()
 
 
 @pytest.mark.parametrize("name", ["channel", "cavity", "pressure"])
@@ -119,6 +136,14 @@ CASES_3D = {
     "pressure19": dict(shape=(20, 9, 10), q=19, nu=0.04, dt=0.5,
                        bcs=[W.pressure(1e-3), W.pressure(-1e-3), W.wall(), W.wall(), W.periodic(), W.periodic()]),
     "cavity27": dict(shape=(34, 10, 9), q=27, nu=0.05, dt=0.5, bcs=W.cavity_bcs(3, 0.1)),
+    # bounce-back on every face (the x walls take the throughput kernel's correction path)
+    # with a moving lid and a moving x wall, and bounce-back beside NEQ walls
+    "bb_cavity19": dict(shape=(40, 20, 12), q=19, nu=0.05, dt=0.5, g=(0.0, 0.0, 1e-5),
+                        bcs=[W.bounce_back((0.0, 0.01, 0.02)), W.bounce_back(), W.bounce_back(),
+                             W.bounce_back((0.1, 0.0, 0.0)), W.bounce_back(), W.bounce_back()]),
+    "bb_mixed27": dict(shape=(33, 11, 9), q=27, nu=0.05, dt=0.5,
+                       bcs=[W.bounce_back(), W.wall(), W.bounce_back(), W.bounce_back((0.1, 0.0, 0.03)),
+                            W.wall(), W.wall()]),
 }
 
 
