@@ -46,7 +46,7 @@
  *      corner velocities removed and the standard weights 1/3, 1/18, 1/36; it has the
  *      same moments up to fourth order, which is all eq. icfeq uses.
  *  R9  Pressure p = (rho - rho0) RT (the paper initialises rho = rho0 + p/RT).
- *  R10 Bounce-back (Sec. 2.4, eq. BB) is applied, like NEQ, to fbar at the wall interface
+ *  R14 Bounce-back (Sec. 2.4, eq. BB) is applied, like NEQ, to fbar at the wall interface
  *      in the Appendix's step 5: for xi_k . n < 0, fbar_k = fbar_(-k) + 2 rho_w W_k
  *      xi_k . u_w / RT, with the opposite velocity's step-4 value at the same interface
  *      and rho_w = rho0 (the incompressible limit the paper names).
@@ -411,7 +411,7 @@ static void step_once(ostate *s)
     }
 
     /* Step 5: boundary processing of fbar at the wall interfaces: NEQ, eq. NEQ
-     * (reading R4), or bounce-back, eq. BB (reading R10). */
+     * (reading R4), or bounce-back, eq. BB (reading R14). */
     for (int d = 0; d < D; d++) {
         if (s->cfg.bc_type[2 * d] == BC_PERIODIC) continue;
         for (int side = 0; side < 2; side++) {
