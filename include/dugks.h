@@ -70,6 +70,12 @@ extern "C" {
 #define DUGKS_BC_BOUNCE_BACK 3  /* eq. BB: fbar_k = fbar_-k + 2 rho0 W_k xi_k.u_w / RT for xi.n < 0
                                    (rho_w = rho0), at the wall interface before step 6        */
 
+/* Equilibrium models (Sec. 2.1-2.2). The incompressible model is the paper's: eq. icfeq with
+ * rho0 u = sum xi f~ + rho0 G dt/2 (eq. macro_values). The original DUGKS, the model it is
+ * compared against, uses eq. feq with rho u = sum xi f~ + rho G dt/2. */
+#define DUGKS_MODEL_INCOMPRESSIBLE 0
+#define DUGKS_MODEL_ORIGINAL 1
+
 /* ---- parameter records ----------------------------------------------------------- */
 typedef struct {
     int32_t dim;     /* 2 or 3 */
@@ -111,6 +117,8 @@ typedef struct {
                                kernel: tile_x x tile_y = 32x8 or 16x8                   */
     int32_t kernel;         /* 0: fastest kernel built for the case (default);
                                1: the reference fused kernel (any lattice/storage)     */
+    int32_t model;          /* DUGKS_MODEL_INCOMPRESSIBLE (default) or DUGKS_MODEL_ORIGINAL
+                               (runs on the reference kernel; no adjoint, no batch)    */
 } dugks_opts;
 
 typedef struct dugks_s *dugks_t;
@@ -147,8 +155,8 @@ int dugks_moments(dugks_t h, float *out, int32_t out_is_device);
 /* FP64 reductions of the current state (the steady-state criterion of Sec. 3.1 and the
  * conservation totals): out[0] = ||u - u_prev||_2 / ||u||_2 where u_prev is the velocity
  * field at the previous dugks_residual call (or at dugks_init; +inf before any), then
- * stores u as the new u_prev; out[1] = sum rho; out[2+a] = sum rho0 u_a (per cell, no
- * volume factor). out: HOST array of dim+2 doubles. Returns DUGKS_E_UNSTABLE if any sum
+ * stores u as the new u_prev; out[1] = sum rho; out[2+a] = sum rho0 u_a (sum rho u_a in the
+ * original model; per cell, no volume factor). out: HOST array of dim+2 doubles. Returns DUGKS_E_UNSTABLE if any sum
  * is not finite. Synchronous. */
 int dugks_residual(dugks_t h, double *out);
 

@@ -46,6 +46,10 @@
  *      corner velocities removed and the standard weights 1/3, 1/18, 1/36; it has the
  *      same moments up to fourth order, which is all eq. icfeq uses.
  *  R9  Pressure p = (rho - rho0) RT (the paper initialises rho = rho0 + p/RT).
+ *  R16 The original DUGKS (the comparison model of Sec. 2.1 and 2.2, model = 1): eq. feq
+ *      in place of eq. icfeq everywhere f_eq appears (step 1, the NEQ equilibria, step 7,
+ *      the force term S, the initial state), with rho u = sum xi f~ + rho G dt/2 at cells
+ *      and the same with h at interfaces; the incompressible model is model = 0.
  *  R14 Bounce-back (Sec. 2.4, eq. BB) is applied, like NEQ, to fbar at the wall interface
  *      in the Appendix's step 5: for xi_k . n < 0, fbar_k = fbar_(-k) + 2 rho_w W_k
  *      xi_k . u_w / RT, with the opposite velocity's step-4 value at the same interface
@@ -93,6 +97,8 @@ typedef struct {
     int bc_type[6];   /* faces -x,+x,-y,+y,-z,+z */
     double bc_u[6][3];/* wall velocity u_w (velocity condition) */
     double bc_p[6];   /* wall pressure p_w (pressure condition) */
+    int model;        /* 0: the incompressible model (eq. icfeq, eq. macro_values);
+                         1: the original DUGKS (eq. feq, rho u = sum xi f~ + rho G dt/2) */
 } oracle_config;
 
 typedef struct {
@@ -174,7 +180,10 @@ static real feq(const ostate *s, int k, real rho, const real u[3])
         xu += s->c * s->e[k][a] * u[a];
         uu += u[a] * u[a];
     }
-    return s->W[k] * (rho + rho0 * (xu / rt + xu * xu / (2.0 * rt * rt) - uu / (2.0 * rt)));
+    const real bracket = xu / rt + xu * xu / (2.0 * rt * rt) - uu / (2.0 * rt);
+    /* the original DUGKS (reading R16), eq. feq: W_k rho [1 + bracket] */
+    if (s->cfg.model == 1) return s->W[k] * rho * (1.0 + bracket);
+    return s->W[k] * (rho + rho0 * bracket);
 }
 
 /* Force term, eq. S: S_k = G.(xi_k - u)/RT f_eq_k (with f_eq of eq. icfeq). */
@@ -194,7 +203,9 @@ static int opposite(const ostate *s, int k)
 }
 
 /* Macroscopic variables, eq. macro_values (cell, weight dt/2) and the Appendix's step 6
- * (interface, weight h/2): rho = sum_k f_k, rho0 u = sum_k xi_k f_k + rho0 G w. */
+ * (interface, weight h/2): rho = sum_k f_k, rho0 u = sum_k xi_k f_k + rho0 G w. The original
+ * DUGKS (reading R16) divides by and weights the force with rho instead:
+ * rho u = sum_k xi_k f_k + rho G w. */
 static void moments(const ostate *s, const real *f, const real G[3], double w, real *rho,
                     real u[3])
 {
@@ -204,7 +215,8 @@ static void moments(const ostate *s, const real *f, const real G[3], double w, r
         for (int a = 0; a < 3; a++) j[a] += s->c * s->e[k][a] * f[k];
     }
     *rho = r;
-    for (int a = 0; a < 3; a++) u[a] = (j[a] + s->cfg.rho0 * G[a] * w) / s->cfg.rho0;
+    const real rd = s->cfg.model == 1 ? r : (real)s->cfg.rho0;
+    for (int a = 0; a < 3; a++) u[a] = (j[a] + rd * G[a] * w) / rd;
 }
 
 /* ------------------------------- indexing --------------------------------------- */
@@ -537,6 +549,7 @@ static int check_config(const oracle_config *c)
     if (c->nx < 1 || c->ny < 1 || c->nz < 1) return -1;
     if (c->dim == 2 && c->nz != 1) return -1;
     if (!(c->dx > 0 && c->rt > 0 && c->rho0 > 0 && c->nu > 0 && c->dt > 0)) return -1;
+    if (!(c->model == 0 || c->model == 1)) return -1;
     const int n[3] = {c->nx, c->ny, c->nz};
     for (int d = 0; d < c->dim; d++) {
         const int lo = c->bc_type[2 * d], hi = c->bc_type[2 * d + 1];

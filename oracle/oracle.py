@@ -34,6 +34,7 @@ class OracleConfig(C.Structure):
         ("bc_type", C.c_int * 6),
         ("bc_u", (C.c_double * 3) * 6),
         ("bc_p", C.c_double * 6),
+        ("model", C.c_int),
     ]
 
 
@@ -96,7 +97,7 @@ class Oracle:
     """
 
     def __init__(self, shape, q, nu, dt, dx=1.0, rt=1.0 / 3.0, rho0=1.0, g=(0.0, 0.0, 0.0),
-                 omega=0.0, bcs=None, field=None, complex_step=False):
+                 omega=0.0, bcs=None, field=None, complex_step=False, model=0):
         dim = len(shape)
         nx, ny = int(shape[0]), int(shape[1])
         nz = int(shape[2]) if dim == 3 else 1
@@ -106,6 +107,7 @@ class Oracle:
         for a in range(3):
             cfg.g[a] = float(g[a]) if a < len(g) else 0.0
         cfg.omega = omega
+        cfg.model = int(model)
         bcs = list(bcs or [])
         bcs += [(BC_PERIODIC, (0.0, 0.0, 0.0), 0.0)] * (6 - len(bcs))
         for w in range(6):

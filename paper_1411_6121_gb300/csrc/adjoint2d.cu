@@ -1051,6 +1051,8 @@ static int check_adjoint_support(dugks_t h) {
         return handle_fail(h, DUGKS_E_UNSUPPORTED, "record/adjoint: built for D2Q9 only");
     if (h->store != DUGKS_STORE_F32 && h->store != DUGKS_STORE_F64)
         return handle_fail(h, DUGKS_E_UNSUPPORTED, "record/adjoint: F32 or F64 storage only");
+    if (h->model != DUGKS_MODEL_INCOMPRESSIBLE)
+        return handle_fail(h, DUGKS_E_UNSUPPORTED, "record/adjoint: the incompressible model only");
     return DUGKS_OK;
 }
 

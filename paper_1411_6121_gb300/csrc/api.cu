@@ -76,6 +76,7 @@ StepParams dugks::handle_params(const dugks_t h) {
     p.dt = h->dt;
     p.step_ctr = h->d_step;
     p.step_off = 0;
+    p.model = h->model;
     for (int w = 0; w < 6; w++) {
         p.bc[w] = h->bcs.face[w].type;
         for (int a = 0; a < 3; a++) p.bc_u[w][a] = h->bcs.face[w].u[a];
@@ -138,6 +139,9 @@ int dugks_create(const dugks_mesh *mesh, int32_t lattice, double nu, double dt, 
         return handle_fail(NULL, DUGKS_E_INVAL, "dx, nu, dt, RT and rho0 must be positive");
     if (o.store < 0 || o.store > 3) return handle_fail(NULL, DUGKS_E_INVAL, "bad storage type");
     if (o.kernel < 0 || o.kernel > 1) return handle_fail(NULL, DUGKS_E_INVAL, "bad kernel selector");
+    if (!(o.model == DUGKS_MODEL_INCOMPRESSIBLE || o.model == DUGKS_MODEL_ORIGINAL))
+        return handle_fail(NULL, DUGKS_E_INVAL, "bad model selector");
+    if (o.model == DUGKS_MODEL_ORIGINAL) o.kernel = 1;  // the original model runs on the reference kernel
     const double c = sqrt(3.0 * o.rt);
     if (dt > mesh->dx / c * (1.0 + 1e-12))
         return handle_fail(NULL, DUGKS_E_CFL, "dt = %g exceeds dx/sqrt(3RT) = %g (CFL number > 1)", dt, mesh->dx / c);
@@ -209,6 +213,7 @@ int dugks_create(const dugks_mesh *mesh, int32_t lattice, double nu, double dt, 
     h->tile_x = tx;
     h->tile_y = ty;
     h->kernel = o.kernel;
+    h->model = o.model;
     h->ry3d = ry3d;
     h->esize = o.store == DUGKS_STORE_F32 ? 4 : (o.store == DUGKS_STORE_F64 ? 8 : 2);
     h->state_bytes = (size_t)h->q * h->px * h->ny * h->nz * h->esize;

@@ -6,7 +6,8 @@
 namespace dugks {
 
 // Initial state (Sec. 3: the equilibrium is initialised from the given fields):
-// g~ = f_eq(rho0 + p/RT, u) - W rho0 of eq. icfeq, evaluated in double and rounded once.
+// g~ = f_eq(rho0 + p/RT, u) - W rho0 of eq. icfeq (eq. feq for the original model: rho in
+// place of rho0 in the velocity part), evaluated in double and rounded once.
 template <int Q, class S>
 __global__ void init_kernel(const StepParams p, const double *pres, const double *vel, double rt, double c) {
     constexpr int D = Lat<Q>::D;
@@ -25,7 +26,8 @@ __global__ void init_kernel(const StepParams p, const double *pres, const double
         for (int k = 0; k < Q; k++) {
             double eu = 0.0;
             for (int a = 0; a < D; a++) eu += Lat<Q>::e(k, a) * uh[a];
-            const double g = Lat<Q>::template wt<double>(k) * (drho + (double)p.rho0 * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
+            const double rv = p.model == 1 ? (double)p.rho0 + drho : (double)p.rho0;
+            const double g = Lat<Q>::template wt<double>(k) * (drho + rv * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
             Store<S>::st(dst + k * p.dstride + off, (typename Arith<S>::T)g);
         }
     }
@@ -49,10 +51,12 @@ __device__ __forceinline__ void cell_moments_d(const StepParams &p, const S *src
         for (int a = 0; a < D; a++) j[a] += Lat<Q>::e(k, a) * g;
     }
     drho = r;
+    // u = c j / rho0 + G dt/2 (eq. macro_values); c j / rho + G dt/2 in the original model
+    const double rd = p.model == 1 ? (double)p.rho0 + r : (double)p.rho0;
     for (int a = 0; a < 3; a++) {
         double G = a < D ? (double)p.g[a] : 0.0;
         if (p.field && a < D) G += (double)p.field[a * ncell + n];
-        u[a] = a < D ? c / (double)p.rho0 * j[a] + G * ct * dtc : 0.0;
+        u[a] = a < D ? c / rd * j[a] + G * ct * dtc : 0.0;
     }
 }
 
@@ -108,10 +112,11 @@ __device__ __forceinline__ void cell_moments_dd(const StepParams &p, const S *sr
         float r[2], j[3][2];
         cell_sums_f<Q, S>(p, src, off, r, j);
         drho = (double)r[0] + (double)r[1];
+        const double rd = p.model == 1 ? (double)p.rho0 + drho : (double)p.rho0;
         for (int a = 0; a < 3; a++) {
             double G = a < D ? (double)p.g[a] : 0.0;
             if (p.field && a < D) G += (double)p.field[a * ncell + n];
-            u[a] = a < D ? c / (double)p.rho0 * ((double)j[a][0] + (double)j[a][1]) + G * ct * dtc : 0.0;
+            u[a] = a < D ? c / rd * ((double)j[a][0] + (double)j[a][1]) + G * ct * dtc : 0.0;
         }
     }
 }
@@ -128,11 +133,13 @@ __device__ __forceinline__ void cell_moments_out_f(const StepParams &p, const S 
     float r[2], j[3][2];
     cell_sums_f<Q, S>(p, src, off, r, j);
     out[n] = (r[0] + r[1]) * rt;
+    // c / rho0, or c / rho in the original model
+    const float cr = p.model == 1 ? c_over_rho0 * (float)p.rho0 / ((float)p.rho0 + (r[0] + r[1])) : c_over_rho0;
 #pragma unroll
     for (int a = 0; a < D; a++) {
         float G = (float)p.g[a];
         if (p.field) G += p.field[a * ncell + n];
-        out[(a + 1) * ncell + n] = fmaf(c_over_rho0, j[a][0] + j[a][1], G * ctdt);
+        out[(a + 1) * ncell + n] = fmaf(cr, j[a][0] + j[a][1], G * ctdt);
     }
 }
 
@@ -177,7 +184,7 @@ __global__ void __launch_bounds__(RES_THREADS) residual_kernel(const StepParams 
             const double du = u[a] - (have_prev ? uprev[a * ncell + n] : 0.0);
             s[0] += du * du;
             s[1] += u[a] * u[a];
-            s[3 + a] += (double)p.rho0 * u[a];
+            s[3 + a] += (p.model == 1 ? (double)p.rho0 + drho : (double)p.rho0) * u[a];  // rho0 u, or rho u
             uprev[a * ncell + n] = u[a];
         }
         s[2] += (double)p.rho0 + drho;

@@ -239,6 +239,8 @@ int dugks_batch_create(int32_t count, const dugks_mesh *meshes, const double *nu
                 return bfail(nullptr, DUGKS_E_INVAL, "instance %d: bad boundaries on axis %d", i, d);
         }
     }
+    if (o.model != DUGKS_MODEL_INCOMPRESSIBLE)
+        return bfail(nullptr, DUGKS_E_UNSUPPORTED, "the batch runs the incompressible model only");
     int tx = o.tile_x ? o.tile_x : 30, ty = o.tile_y ? o.tile_y : 6;  // default: the throughput tile
     if (!tile_supported(tx, ty)) return bfail(nullptr, DUGKS_E_UNSUPPORTED, "batch tile %dx%d not built", tx, ty);
     dugks_batch_t b = new (std::nothrow) dugks_batch_s();

@@ -232,6 +232,7 @@ struct StepParams {
     double omega, dt;          // G(t) = (g + field) cos(omega t)
     const long long *step_ctr; // device step counter: t_n = (*step_ctr + step_off) dt
     int step_off;
+    int model;                 // 0: incompressible model (eq. icfeq); 1: original DUGKS (eq. feq)
     int bc[6];                 // DUGKS_BC_* per face
     double bc_u[6][3];         // wall velocity
     double bc_drho[6];         // pressure condition: rho_a - rho0 = p_w / RT

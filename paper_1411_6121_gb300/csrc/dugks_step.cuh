@@ -61,6 +61,20 @@ __device__ __forceinline__ void reconstruct(const T *L, const T *R, const T *L1m
     }
 }
 
+// The model switch of the reference path. For the incompressible model (eq. icfeq,
+// eq. macro_values) the momentum variable is m = rho0 u / c and f_eq, S divide by rho0;
+// returns 1/rho0. For the original DUGKS (p.model == 1: eq. feq, rho u = sum xi f~ + rho G w)
+// m = rho u / c: the force shift that moments() applied with rho0 is completed to
+// rho = rho0 + drho, and 1/rho is returned for f_eq and S.
+template <class T>
+__device__ __forceinline__ T original_model(const StepParams &p, const Coef<T> &cf, const T Gh[3], T w, T drho,
+                                            T m[3]) {
+    if (p.model != 1) return cf.inv_rho0;
+#pragma unroll
+    for (int a = 0; a < 3; a++) m[a] = fmaT(Gh[a], w * drho, m[a]);
+    return T(1) / (cf.rho0 + drho);
+}
+
 // Steps 5-7 at one interface normal to axis d. F: step-4 values (modified in place by the
 // wall condition, NEQ or bounce-back, when wall != 0). Fc: step-4 values at x_c, the boundary
 // cell's opposite interface (read only by NEQ). side: 0 for the low wall (outward normal -e_d),
@@ -98,16 +112,22 @@ __device__ __forceinline__ void interface_f(const StepParams &p, const Coef<T> &
         const int wid = 2 * d + side;
         T drc, mc[3];
         moments<Q, T>(Fc, Ghc, cf.wface * cf.rho0, drc, mc);
+        const T irc = original_model(p, cf, Ghc, cf.wface, drc, mc);
         T dra, ma[3];
         if (p.bc[wid] == 1) {  // velocity condition: u_a = u_w, rho_a = rho_c
             dra = drc;
-            ma[0] = (T)(p.bc_u[wid][0] * p.rho0 * p.inv_c);
-            ma[1] = (T)(p.bc_u[wid][1] * p.rho0 * p.inv_c);
-            ma[2] = (T)(p.bc_u[wid][2] * p.rho0 * p.inv_c);
+            // m = rho u / c: rho0 u_w / c, or rho_a u_w / c in the original model
+            const double ra = p.model == 1 ? p.rho0 + (double)drc : p.rho0;
+            ma[0] = (T)(p.bc_u[wid][0] * ra * p.inv_c);
+            ma[1] = (T)(p.bc_u[wid][1] * ra * p.inv_c);
+            ma[2] = (T)(p.bc_u[wid][2] * ra * p.inv_c);
         } else {               // pressure condition: rho_a = rho0 + p_w/RT, u_a = u_c
             dra = (T)p.bc_drho[wid];
-            ma[0] = mc[0]; ma[1] = mc[1]; ma[2] = mc[2];
+            // m_a = rho0 u_c / c = m_c, or rho_a u_c / c = m_c rho_a / rho_c (original model)
+            const T sc = p.model == 1 ? (cf.rho0 + dra) * irc : T(1);
+            ma[0] = mc[0] * sc; ma[1] = mc[1] * sc; ma[2] = mc[2] * sc;
         }
+        const T ira = p.model == 1 ? T(1) / (cf.rho0 + dra) : cf.inv_rho0;
         const T mma = dotD<D, T>(ma, ma);
         const T mmc = dotD<D, T>(mc, mc);
         const int sgn = side == 0 ? -1 : 1;
@@ -115,14 +135,15 @@ __device__ __forceinline__ void interface_f(const StepParams &p, const Coef<T> &
         for (int k = 0; k < Q; k++) {
             if (Lat<Q>::e(k, d) == 0) continue;
             if (sgn * Lat<Q>::e(k, d) < 0)
-                F[k] = geq_k<Q, T>(k, dra, ma, mma, cf.inv_rho0) + (Fc[k] - geq_k<Q, T>(k, drc, mc, mmc, cf.inv_rho0));
+                F[k] = geq_k<Q, T>(k, dra, ma, mma, ira) + (Fc[k] - geq_k<Q, T>(k, drc, mc, mmc, irc));
         }
     }
     // Step 6: interface moments (weight h/2 on G). Step 7: original distribution.
     T drb, mb[3];
     moments<Q, T>(F, Gh, cf.wface * cf.rho0, drb, mb);
+    const T irb = original_model(p, cf, Gh, cf.wface, drb, mb);
     T t[Q];
-    relax<Q, T>(F, drb, mb, Gh, cf.rho0, cf.inv_rho0, cf.b7, cf.c7, t);
+    relax<Q, T>(F, drb, mb, Gh, cf.rho0, irb, cf.b7, cf.c7, t);
     sfor<Q>([&](auto kc) {
         constexpr int k = kc;
         if constexpr (Lat<Q>::e(k, d) != 0) out[flux_index<Q>(d, k)] = t[k];
@@ -203,7 +224,8 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
             T Gh[3], drho, m[3];
             cell_G<D, T>(p, cell, ncell, ct, Gh);
             moments<Q, T>(g, Gh, cf.wcell * cf.rho0, drho, m);
-            relax<Q, T>(g, drho, m, Gh, cf.rho0, cf.inv_rho0, cf.b1, cf.c1, out);
+            const T ir = original_model(p, cf, Gh, cf.wcell, drho, m);
+            relax<Q, T>(g, drho, m, Gh, cf.rho0, ir, cf.b1, cf.c1, out);
         }
         // Step 2 (reading: linear extrapolation ghost = 2 f0 - f1, axis by axis).
         const bool xwall = !perx && (x0 == 0 || x0 + TX >= nx);

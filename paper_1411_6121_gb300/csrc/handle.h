@@ -40,6 +40,7 @@ struct dugks_s {
     cudaStream_t stream;
     int use_graph, tile_x, tile_y;
     int kernel;            // 0: throughput kernel where built, 1: reference kernel
+    int model;             // DUGKS_MODEL_*
     int ry3d;              // CTA rows of the 3D throughput kernel
     int own_stream;
     size_t esize;          // bytes per stored element

@@ -21,6 +21,7 @@ ERRORS = {
 D2Q9, D3Q19, D3Q27 = 9, 19, 27
 STORE_F32, STORE_BF16, STORE_F16, STORE_F64 = 0, 1, 2, 3
 BC_PERIODIC, BC_NEQ_VELOCITY, BC_NEQ_PRESSURE, BC_BOUNCE_BACK = 0, 1, 2, 3
+MODEL_INCOMPRESSIBLE, MODEL_ORIGINAL = 0, 1
 
 LIB_PATH = _build.LIB
 
@@ -54,7 +55,8 @@ class Force(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("rt", C.c_double), ("rho0", C.c_double), ("store", C.c_int32), ("stream", C.c_void_p),
-                ("use_graph", C.c_int32), ("tile_x", C.c_int32), ("tile_y", C.c_int32), ("kernel", C.c_int32)]
+                ("use_graph", C.c_int32), ("tile_x", C.c_int32), ("tile_y", C.c_int32), ("kernel", C.c_int32),
+                ("model", C.c_int32)]
 
 
 class DugksError(RuntimeError):
@@ -148,7 +150,8 @@ class Sim:
     """One simulation handle (see ``include/dugks.h``)."""
 
     def __init__(self, shape, q, nu, dt, dx=1.0, rt=1.0 / 3.0, rho0=1.0, g=(0.0, 0.0, 0.0), omega=0.0,
-                 bcs=None, field=None, store=STORE_F32, stream=None, use_graph=True, tile=None, kernel=0):
+                 bcs=None, field=None, store=STORE_F32, stream=None, use_graph=True, tile=None, kernel=0,
+                 model=MODEL_INCOMPRESSIBLE):
         lib = load()
         self.lib = lib
         dim = len(shape)
@@ -170,6 +173,7 @@ class Sim:
         if tile:
             o.tile_x, o.tile_y = int(tile[0]), int(tile[1])
         o.kernel = int(kernel)
+        o.model = int(model)
         self.bcs = make_bcs(bcs)
         h = C.c_void_p()
         rc = lib.dugks_create(C.byref(m), int(q), float(nu), float(dt), C.byref(f), C.byref(self.bcs), C.byref(o),

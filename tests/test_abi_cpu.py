@@ -37,6 +37,7 @@ def _create(**kw):
     o = dugks.Opts()
     lib.dugks_opts_default(C.byref(o))
     o.rt = args["rt"]
+    o.model = args.get("model", 0)
     h = C.c_void_p()
     rc = lib.dugks_create(C.byref(m), args["q"], args["nu"], args["dt"], C.byref(f), C.byref(b), C.byref(o), C.byref(h))
     return rc, h, lib.dugks_last_error(None).decode()
@@ -51,7 +52,7 @@ def test_cfl_violation_rejected():
 @pytest.mark.parametrize("kw", [dict(dim=4), dict(q=19), dict(dim=3, q=9, nz=4), dict(nx=0), dict(nu=-1.0),
                                 dict(bcs=[(1, (0, 0, 0), 0.0), (0, (0, 0, 0), 0.0)]),
                                 dict(nx=1, bcs=[(1, (0, 0, 0), 0.0), (1, (0, 0, 0), 0.0)]),
-                                dict(bcs=[(4, (0, 0, 0), 0.0), (4, (0, 0, 0), 0.0)])])
+                                dict(bcs=[(4, (0, 0, 0), 0.0), (4, (0, 0, 0), 0.0)]), dict(model=2)])
 def test_invalid_arguments_rejected(kw):
     rc, h, msg = _create(**kw)
     assert rc in (-1, -7) and not h.value and msg
