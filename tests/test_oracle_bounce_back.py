@@ -77,8 +77,7 @@ def test_bounce_back_poiseuille_second_order():
     assert e8 < _poiseuille_error(8, W.wall)
 
 
-@pytest.mark.skipif(not __import__("os").environ.get("DUGKS_SLOW_TESTS"),
-                    reason="about two minutes of oracle time; set DUGKS_SLOW_TESTS=1")
+@pytest.mark.slow
 @pytest.mark.parametrize("rt", [5.0, 100.0 / 3.0])
 def test_paper_poiseuille_bb_neq_close(rt):
     """Sec. 3.2's setting: unit square of 8 x 8 cells, rho0 = 1, Re = 10, G = 1e-3, dt = 1e-4,

@@ -71,3 +71,24 @@ def test_uniform_flow_of_rho0_is_fixed_in_both_models(q, shape):
         assert np.abs(o.get_state() - f0).max() < 1e-15
         states.append(f0)
     assert np.abs(states[0] - states[1]).max() < 1e-16
+
+
+@pytest.mark.slow
+def test_mach_sensitivity_oracle():
+    """Sec. 3.1's compressibility study in the oracle (golden fixture, cited): about four
+    minutes of FP64 CPU time."""
+    from oracle.oracle import rel_change
+    from tests import mach_study
+
+    def run(cfg, p, u, field):
+        o = Oracle(field=field, **cfg)
+        o.init(p=p, u=u)
+        prev = o.moments()[1:]
+        while True:
+            o.step(1000)
+            cur = o.moments()[1:]
+            if rel_change(cur, prev) <= 1e-6:
+                return cur
+            prev = cur
+
+    mach_study.check(lambda ma, m: mach_study.steady_error(ma, m, run))
