@@ -88,6 +88,8 @@ typedef struct {
     int32_t type;    /* DUGKS_BC_* */
     double u[3];     /* wall velocity u_w (velocity condition, bounce-back) */
     double p;        /* wall pressure p_w = (rho_w - rho0) RT (pressure condition) */
+    double p_amp;    /* pressure condition: p_w(t) = p + p_amp cos(omega t), with the omega of
+                        the force record (0: steady)                               */
 } dugks_face_bc;
 
 typedef struct {

@@ -99,6 +99,7 @@ typedef struct {
     double bc_p[6];   /* wall pressure p_w (pressure condition) */
     int model;        /* 0: the incompressible model (eq. icfeq, eq. macro_values);
                          1: the original DUGKS (eq. feq, rho u = sum xi f~ + rho G dt/2) */
+    double bc_p_amp[6];/* pressure condition: p_w(t) = bc_p + bc_p_amp cos(omega t) */
 } oracle_config;
 
 typedef struct {
@@ -457,7 +458,9 @@ static void step_once(ostate *s)
                             rhoa = rhoc;
                             for (int a = 0; a < 3; a++) ua[a] = s->wall_u[wall][a];
                         } else {
-                            rhoa = rho0 + s->cfg.bc_p[wall] / s->cfg.rt;
+                            /* the wall pressure at the interface time t + h */
+                            const double pw = s->cfg.bc_p[wall] + s->cfg.bc_p_amp[wall] * cos(s->cfg.omega * (t + h));
+                            rhoa = rho0 + pw / s->cfg.rt;
                             for (int a = 0; a < 3; a++) ua[a] = uc[a];
                         }
                         for (int k = 0; k < Q; k++) {

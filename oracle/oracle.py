@@ -35,6 +35,7 @@ class OracleConfig(C.Structure):
         ("bc_u", (C.c_double * 3) * 6),
         ("bc_p", C.c_double * 6),
         ("model", C.c_int),
+        ("bc_p_amp", C.c_double * 6),
     ]
 
 
@@ -111,11 +112,12 @@ class Oracle:
         bcs = list(bcs or [])
         bcs += [(BC_PERIODIC, (0.0, 0.0, 0.0), 0.0)] * (6 - len(bcs))
         for w in range(6):
-            t, u, p = bcs[w]
+            t, u, p = bcs[w][:3]
             cfg.bc_type[w] = int(t)
             for a in range(3):
                 cfg.bc_u[w][a] = float(u[a]) if a < len(u) else 0.0
             cfg.bc_p[w] = float(p)
+            cfg.bc_p_amp[w] = float(bcs[w][3]) if len(bcs[w]) > 3 else 0.0
         self.lib = _lib(complex_step)
         self.complex_step = complex_step
         self.cfg = cfg

@@ -52,11 +52,13 @@ struct AdjParams {
     int bc[4];               // DUGKS_BC_* of the faces -x, +x, -y, +y
     T mw[4][2];              // wall momentum rho0 u_w / c of a velocity condition
     T drw[4];                // rho_a - rho0 = p_w / RT of a pressure condition
+    T drw1[4];               // its oscillating part: + drw1 cos(omega (t_n + h))
     T rho0, inv_rho0, dmw;   // dmw = d m_w / d u_w = rho0 / c
     T b1, c1, b7, c7, kappa, two_kappa, wcell, wface;
     T g[2];                  // uniform acceleration
     const float *field;      // [2][ncell] acceleration field or null
     T ctc, cthc;             // cos(omega t_n) / c and cos(omega (t_n + h)) / c
+    T cwh;                   // cos(omega (t_n + h))
     const T *state;          // g~^n (padded layout)
     T *phi;                  // [Q][ncell] fbar+ of the cells
     T *mom;                  // [3][ncell] drho, m_x, m_y of the cells (m in units of c)
@@ -307,7 +309,7 @@ __device__ __forceinline__ void face_forward_lane(const AdjParams<T> &a, int d, 
         s.mc[1] = wsum(e1 * s.Fc) + a.rho0 * Ghc[1] * a.wface;
         const int wid = 2 * d + s.side;
         const bool vel = a.bc[wid] == DUGKS_BC_NEQ_VELOCITY;
-        const T dra = vel ? s.drc : a.drw[wid];
+        const T dra = vel ? s.drc : a.drw[wid] + a.drw1[wid] * a.cwh;
         s.ma[0] = vel ? a.mw[wid][0] : s.mc[0];
         s.ma[1] = vel ? a.mw[wid][1] : s.mc[1];
         const int sgn = s.side == 0 ? -1 : 1;
@@ -835,6 +837,7 @@ AdjParams<T> base_params(const dugks_t h, const AdjBufs &B) {
         a.mw[w][0] = (T)(p.bc_u[w][0] * p.rho0 * p.inv_c);
         a.mw[w][1] = (T)(p.bc_u[w][1] * p.rho0 * p.inv_c);
         a.drw[w] = (T)p.bc_drho[w];
+        a.drw1[w] = (T)p.bc_drho1[w];
     }
     a.rho0 = (T)p.rho0;
     a.inv_rho0 = (T)(1.0 / p.rho0);
@@ -869,6 +872,7 @@ cudaError_t reverse_step(AdjParams<T> a, const dugks_t h, const void *state, dou
     const double om = h->force.omega, inv_c = 1.0 / h->c;
     a.ctc = (T)(cos(om * tn) * inv_c);
     a.cthc = (T)(cos(om * (tn + 0.5 * h->dt)) * inv_c);
+    a.cwh = (T)cos(om * (tn + 0.5 * h->dt));
     a.state = (const T *)state;
     a.lam1 = (const T *)lam1;
     a.lam0 = (T *)lam0;

@@ -81,6 +81,7 @@ StepParams dugks::handle_params(const dugks_t h) {
         p.bc[w] = h->bcs.face[w].type;
         for (int a = 0; a < 3; a++) p.bc_u[w][a] = h->bcs.face[w].u[a];
         p.bc_drho[w] = (h->bcs.face[w].p / h->rt);
+        p.bc_drho1[w] = (h->bcs.face[w].p_amp / h->rt);
     }
     p.src = h->buf[h->cur];
     p.dst = h->buf[h->cur ^ 1];

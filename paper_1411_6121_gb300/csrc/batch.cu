@@ -151,6 +151,7 @@ StepParams instance_params(const dugks_batch_t b, int i, int parity) {
         p.bc[w] = b->bcs[i].face[w].type;
         for (int a = 0; a < 3; a++) p.bc_u[w][a] = b->bcs[i].face[w].u[a];
         p.bc_drho[w] = b->bcs[i].face[w].p / b->rt;
+        p.bc_drho1[w] = b->bcs[i].face[w].p_amp / b->rt;
     }
     const char *b0 = static_cast<const char *>(b->buf[parity]) + b->off[i] * b->esize;
     char *b1 = static_cast<char *>(b->buf[parity ^ 1]) + b->off[i] * b->esize;

@@ -236,6 +236,7 @@ struct StepParams {
     int bc[6];                 // DUGKS_BC_* per face
     double bc_u[6][3];         // wall velocity
     double bc_drho[6];         // pressure condition: rho_a - rho0 = p_w / RT
+    double bc_drho1[6];        // its oscillating part: + bc_drho1 cos(omega t)
     const void *src;
     void *dst;
 };

@@ -61,6 +61,16 @@ __device__ __forceinline__ void reconstruct(const T *L, const T *R, const T *L1m
     }
 }
 
+// Density deviation rho_a - rho0 of a pressure wall at the interface time t_n + h (Sec. 2.4:
+// rho_a from the wall pressure p_w(t) = p + p_amp cos(omega t), divided by RT on the host).
+template <class T>
+__device__ __forceinline__ T wall_drho(const StepParams &p, int wid) {
+    double v = p.bc_drho[wid];
+    if (p.bc_drho1[wid] != 0.0)
+        v += p.bc_drho1[wid] * cos(p.omega * (((double)(*p.step_ctr) + (double)p.step_off) * p.dt + 0.5 * p.dt));
+    return (T)v;
+}
+
 // The model switch of the reference path. For the incompressible model (eq. icfeq,
 // eq. macro_values) the momentum variable is m = rho0 u / c and f_eq, S divide by rho0;
 // returns 1/rho0. For the original DUGKS (p.model == 1: eq. feq, rho u = sum xi f~ + rho G w)
@@ -122,7 +132,7 @@ __device__ __forceinline__ void interface_f(const StepParams &p, const Coef<T> &
             ma[1] = (T)(p.bc_u[wid][1] * ra * p.inv_c);
             ma[2] = (T)(p.bc_u[wid][2] * ra * p.inv_c);
         } else {               // pressure condition: rho_a = rho0 + p_w/RT, u_a = u_c
-            dra = (T)p.bc_drho[wid];
+            dra = wall_drho<T>(p, wid);
             // m_a = rho0 u_c / c = m_c, or rho_a u_c / c = m_c rho_a / rho_c (original model)
             const T sc = p.model == 1 ? (cf.rho0 + dra) * irc : T(1);
             ma[0] = mc[0] * sc; ma[1] = mc[1] * sc; ma[2] = mc[2] * sc;

@@ -42,7 +42,7 @@ class Mesh(C.Structure):
 
 
 class FaceBC(C.Structure):
-    _fields_ = [("type", C.c_int32), ("u", C.c_double * 3), ("p", C.c_double)]
+    _fields_ = [("type", C.c_int32), ("u", C.c_double * 3), ("p", C.c_double), ("p_amp", C.c_double)]
 
 
 class Boundaries(C.Structure):
@@ -133,16 +133,18 @@ def _dp(a):
 
 
 def make_bcs(bcs):
-    """6 tuples (type, (ux, uy, uz), p) in the order -x, +x, -y, +y, -z, +z (missing
-    entries periodic)."""
+    """6 tuples (type, (ux, uy, uz), p[, p_amp]) in the order -x, +x, -y, +y, -z, +z
+    (missing entries periodic; p_amp: amplitude of an oscillating wall pressure)."""
     b = Boundaries()
     bcs = list(bcs or [])
     bcs += [(BC_PERIODIC, (0.0, 0.0, 0.0), 0.0)] * (6 - len(bcs))
-    for w, (t, u, p) in enumerate(bcs[:6]):
+    for w, bc in enumerate(bcs[:6]):
+        t, u, p = bc[:3]
         b.face[w].type = int(t)
         for a in range(3):
             b.face[w].u[a] = float(u[a]) if a < len(u) else 0.0
         b.face[w].p = float(p)
+        b.face[w].p_amp = float(bc[3]) if len(bc) > 3 else 0.0
     return b
 
 

@@ -32,7 +32,10 @@ def wall(u=(0.0, 0.0, 0.0)):
     return (BC_NEQ_VELOCITY, tuple(float(a) for a in u) + (0.0,) * (3 - len(u)), 0.0)
 
 
-def pressure(p):
+def pressure(p, amp=0.0):
+    """NEQ pressure condition p_w = p (+ amp cos(omega t) with the force's omega)."""
+    if amp:
+        return (BC_NEQ_PRESSURE, (0.0, 0.0, 0.0), float(p), float(amp))
     return (BC_NEQ_PRESSURE, (0.0, 0.0, 0.0), float(p))
 
 

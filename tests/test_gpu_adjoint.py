@@ -38,7 +38,7 @@ CASES = {
                         bcs=[W.periodic(), W.periodic(), W.wall(), W.wall((0.03, 0.0, 0.0))]),
     "cavity": dict(shape=(5, 6), q=9, nu=0.04, dt=0.5, bcs=W.cavity_bcs(2, 0.05)),
     "pressure_oscillating": dict(shape=(6, 4), q=9, nu=0.06, dt=0.5, g=(1e-4, -3e-5, 0.0), omega=0.07,
-                                 bcs=[W.pressure(2e-3), W.pressure(-1e-3), W.wall((0.0, 0.01, 0.0)), W.wall()]),
+                                 bcs=[W.pressure(2e-3, 1.5e-3), W.pressure(-1e-3), W.wall((0.0, 0.01, 0.0)), W.wall()]),
     "periodic": dict(shape=(5, 4), q=9, nu=0.05, dt=0.5, g=(1e-5, 2e-5, 0.0), bcs=W.all_periodic()),
     # wide enough for interior cells and interfaces (the kernels' fast path) beside the
     # boundary ones

@@ -64,6 +64,9 @@ CASES_2D = {
                       bcs=[W.bounce_back(), W.bounce_back(), W.bounce_back(), W.bounce_back((0.1, 0.0))]),
     "bb_pressure": dict(shape=(36, 19), q=9, nu=0.04, dt=0.5, g=(0.0, 1e-5, 0.0),
                         bcs=[W.pressure(1e-3), W.pressure(-1e-3), W.bounce_back(), W.bounce_back((0.02, 0.0))]),
+    # an oscillating inlet pressure p + p_amp cos(omega t) (the pressure-driven Womersley form)
+    "pressure_oscillating": dict(shape=(36, 19), q=9, nu=0.04, dt=0.5, omega=0.3,
+                                 bcs=[W.pressure(1e-3, 2e-3), W.pressure(-1e-3), W.bounce_back(), W.wall()]),
 }
 
 
@@ -141,6 +144,9 @@ CASES_3D = {
     "bb_cavity19": dict(shape=(40, 20, 12), q=19, nu=0.05, dt=0.5, g=(0.0, 0.0, 1e-5),
                         bcs=[W.bounce_back((0.0, 0.01, 0.02)), W.bounce_back(), W.bounce_back(),
                              W.bounce_back((0.1, 0.0, 0.0)), W.bounce_back(), W.bounce_back()]),
+    "pressure19_osc": dict(shape=(20, 9, 10), q=19, nu=0.04, dt=0.5, omega=0.3,
+                           bcs=[W.pressure(1e-3, 2e-3), W.pressure(-1e-3, -1e-3), W.wall(), W.wall(),
+                                W.periodic(), W.periodic()]),
     "bb_mixed27": dict(shape=(33, 11, 9), q=27, nu=0.05, dt=0.5,
                        bcs=[W.bounce_back(), W.wall(), W.bounce_back(), W.bounce_back((0.1, 0.0, 0.03)),
                             W.wall(), W.wall()]),
@@ -305,6 +311,34 @@ def test_mach_sensitivity_of_the_two_models():
     original's (golden fixture, cited). FP64 path, element-wise equal to the oracle."""
     from tests import mach_study
     mach_study.check(lambda ma, m: mach_study.steady_error(ma, m, _gpu_steady))
+
+
+def test_womersley_pressure_driven():
+    """Sec. 3.3: the pressure-driven Womersley flow between bounce-back walls with an
+    oscillating NEQ pressure inlet. The paper reports pressure errors over the period below
+    0.42% and velocities in good agreement. FP64 path (element-wise equal to the oracle)."""
+    from tests import womersley_study as WS
+    cfg, exact, spp = WS.setup()
+    p0, u0 = exact(0.0)
+    s = _sim(store=3, **cfg)
+    s.init(p=p0, u=u0)
+
+    def run_periods(n):
+        s.step(n * spp)
+        return s.moments()[1:].astype(np.float64)
+
+    def sample(k):
+        if k:
+            s.step(k)
+        m = s.moments().astype(np.float64)
+        return m[0], m[1:]
+
+    n, ep, eu = WS.errors(run_periods, sample)
+    assert n < 80, "no periodic state"
+    assert ep < 0.0042, ep  # the paper's bound (the oracle: 0.244%)
+    # the paper prints no velocity figure ("good agreement"); the oracle gives 2.03% over the
+    # period on this mesh
+    assert eu < 0.03, eu
 
 
 def test_16bit_storage_2d_cavity():

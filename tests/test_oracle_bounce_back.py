@@ -99,3 +99,28 @@ def test_paper_poiseuille_bb_neq_close(rt):
         u = o.moments()[1].reshape(N, 2)[:, 0] - 0.5e-4 * G
         errs.append(np.linalg.norm(u - ua) / np.linalg.norm(ua))
     assert abs(errs[0] - errs[1]) < 2e-3, errs
+
+
+@pytest.mark.slow
+def test_womersley_pressure_driven_oracle():
+    """Sec. 3.3's pressure-driven Womersley flow in the oracle: pressure errors over the
+    period below the paper's 0.42% (several minutes of FP64 CPU time)."""
+    from oracle.oracle import Oracle as Orc
+    from tests import womersley_study as WS
+    cfg, exact, spp = WS.setup()
+    o = Orc(**cfg)
+    o.init(*exact(0.0))
+
+    def run_periods(n):
+        o.step(n * spp)
+        return o.moments()[1:]
+
+    def sample(k):
+        if k:
+            o.step(k)
+        m = o.moments()
+        return m[0], m[1:]
+
+    n, ep, eu = WS.errors(run_periods, sample)
+    # pressure: the paper's bound (measured 0.244%); velocity: no printed figure, 2.03% measured
+    assert ep < 0.0042 and eu < 0.03, (n, ep, eu)
