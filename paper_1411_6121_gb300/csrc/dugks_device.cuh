@@ -208,6 +208,9 @@ __device__ __forceinline__ T ghost_value(T a, T b) { return fmaT(T(2), a, -b); }
 // A product rounded on its own (never fused into a later addition).
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+// The correctly rounded reciprocal (the value of 1 / x, without the divide's slow path).
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
 
 // ---------------------------------------------------------------------------------
 // Parameters of one fused step launch (coefficients precomputed on the host in double;
@@ -245,9 +248,14 @@ struct StepParams {
 template <class T>
 struct Coef {
     T rho0, inv_rho0, inv_c, b1, c1, b7, c7, kappa, two_kappa, wcell, wface;
+    T cwh;  // cos(omega (t_n + h)): the time factor of an oscillating wall pressure
     __device__ __forceinline__ explicit Coef(const StepParams &p)
         : rho0((T)p.rho0), inv_rho0((T)(1.0 / p.rho0)), inv_c((T)p.inv_c), b1((T)p.b1), c1((T)p.c1), b7((T)p.b7),
-          c7((T)p.c7), kappa((T)p.kappa), two_kappa((T)p.two_kappa), wcell((T)p.wcell), wface((T)p.wface) {}
+          c7((T)p.c7), kappa((T)p.kappa), two_kappa((T)p.two_kappa), wcell((T)p.wcell), wface((T)p.wface),
+          cwh(T(1)) {
+        if (p.omega != 0.0)
+            cwh = (T)cos(p.omega * (((double)(*p.step_ctr) + (double)p.step_off) * p.dt + 0.5 * p.dt));
+    }
 };
 
 // ---------------------------------------------------------------------------------

@@ -62,13 +62,11 @@ __device__ __forceinline__ void reconstruct(const T *L, const T *R, const T *L1m
 }
 
 // Density deviation rho_a - rho0 of a pressure wall at the interface time t_n + h (Sec. 2.4:
-// rho_a from the wall pressure p_w(t) = p + p_amp cos(omega t), divided by RT on the host).
+// rho_a from the wall pressure p_w(t) = p + p_amp cos(omega t), divided by RT on the host;
+// cf.cwh holds the cosine).
 template <class T>
-__device__ __forceinline__ T wall_drho(const StepParams &p, int wid) {
-    double v = p.bc_drho[wid];
-    if (p.bc_drho1[wid] != 0.0)
-        v += p.bc_drho1[wid] * cos(p.omega * (((double)(*p.step_ctr) + (double)p.step_off) * p.dt + 0.5 * p.dt));
-    return (T)v;
+__device__ __forceinline__ T wall_drho(const StepParams &p, const Coef<T> &cf, int wid) {
+    return (T)p.bc_drho[wid] + (T)p.bc_drho1[wid] * cf.cwh;
 }
 
 // The model switch of the reference path. For the incompressible model (eq. icfeq,
@@ -82,7 +80,7 @@ __device__ __forceinline__ T original_model(const StepParams &p, const Coef<T> &
     if (p.model != 1) return cf.inv_rho0;
 #pragma unroll
     for (int a = 0; a < 3; a++) m[a] = fmaT(Gh[a], w * drho, m[a]);
-    return T(1) / (cf.rho0 + drho);
+    return rcp_rn(cf.rho0 + drho);
 }
 
 // Steps 5-7 at one interface normal to axis d. F: step-4 values (modified in place by the
@@ -132,12 +130,12 @@ __device__ __forceinline__ void interface_f(const StepParams &p, const Coef<T> &
             ma[1] = (T)(p.bc_u[wid][1] * ra * p.inv_c);
             ma[2] = (T)(p.bc_u[wid][2] * ra * p.inv_c);
         } else {               // pressure condition: rho_a = rho0 + p_w/RT, u_a = u_c
-            dra = wall_drho<T>(p, wid);
+            dra = wall_drho<T>(p, cf, wid);
             // m_a = rho0 u_c / c = m_c, or rho_a u_c / c = m_c rho_a / rho_c (original model)
             const T sc = p.model == 1 ? (cf.rho0 + dra) * irc : T(1);
             ma[0] = mc[0] * sc; ma[1] = mc[1] * sc; ma[2] = mc[2] * sc;
         }
-        const T ira = p.model == 1 ? T(1) / (cf.rho0 + dra) : cf.inv_rho0;
+        const T ira = p.model == 1 ? rcp_rn(cf.rho0 + dra) : cf.inv_rho0;
         const T mma = dotD<D, T>(ma, ma);
         const T mmc = dotD<D, T>(mc, mc);
         const int sgn = side == 0 ? -1 : 1;

@@ -250,7 +250,7 @@ __device__ __forceinline__ void neq_wall(const StepParams &p, const Coef<float> 
 #pragma unroll
         for (int a = 0; a < 3; a++) ma[a] = (float)(p.bc_u[wid][a] * p.rho0 * p.inv_c);
     } else {  // pressure condition: rho_a = rho0 + p_w / RT, u_a = u_c
-        dra = wall_drho<float>(p, wid);
+        dra = wall_drho<float>(p, cf, wid);
 #pragma unroll
         for (int a = 0; a < 3; a++) ma[a] = mc[a];
     }
