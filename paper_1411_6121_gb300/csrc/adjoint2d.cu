@@ -10,15 +10,20 @@
 //                                  fbar+ (step 1, eq. f_bar_+);
 //   adj_faces     (per interface)  recomputes steps 3-7 and pulls lambda' back through the
 //                                  flux (steps 8-9), the interface relaxation (step 7,
-//                                  eq. original_f), the interface moments (step 6) and the NEQ
-//                                  wall condition (step 5, eq. NEQ), down to the adjoint of
-//                                  the step-4 values and of the interface acceleration;
+//                                  eq. original_f), the interface moments (step 6) and the
+//                                  wall condition (step 5: eq. NEQ, or eq. BB), down to the
+//                                  adjoint of the step-4 values and of the interface
+//                                  acceleration;
 //   adj_cells     (per cell)       transposes the reconstruction (steps 3-4, eq. gradient)
 //                                  and the ghost extrapolation (step 2), then pulls the
 //                                  adjoint of fbar+ back through step 1 and the cell moments
 //                                  to g~^n and G.
-// Every output element is a gather written by one thread (no atomics), so the sweep is
-// bitwise reproducible. Arithmetic in the storage type of the handle (float or double).
+// The interior of each kernel takes a fast path with compile-time velocities; the band along
+// walls, x_c interfaces and periodic seams takes the general path, one item per half-warp with
+// one velocity per lane. Every output element is a gather written by one thread, or by one lane
+// after a fixed-order butterfly over the velocities (no atomics), so the sweep is bitwise
+// reproducible. Arithmetic in the storage type of the handle (float or double). The adjoint
+// covers the incompressible model (eq. icfeq).
 //
 // Interfaces: normal to x, (i, j) with i in [0, nx], j in [0, ny), between cells (i-1, j)
 // and (i, j), index i + (nx+1) j; normal to y, (i, j) with i in [0, nx), j in [0, ny],
