@@ -50,6 +50,15 @@
  *      in place of eq. icfeq everywhere f_eq appears (step 1, the NEQ equilibria, step 7,
  *      the force term S, the initial state), with rho u = sum xi f~ + rho G dt/2 at cells
  *      and the same with h at interfaces; the incompressible model is model = 0.
+ *  R18 Non-uniform mesh (Sec. 3.4, the tanh mesh): the mesh is given by its interface
+ *      coordinates per axis; cell centres are the midpoints of their two interfaces. Step 3
+ *      interpolates linearly in each axis between the two centres around the interface
+ *      (bilinearly at cross points), step 4 divides the normal difference by the centre
+ *      distance and the tangential one by the interface length, step 2 extrapolates
+ *      linearly through the two boundary centres to the ghost centre (the boundary
+ *      centre mirrored in the wall; periodic ghosts sit one period away), the interface G
+ *      is interpolated like fbar+, and step 8 uses each cell's interface areas and volume.
+ *      On a uniform mesh every one of these reduces to the uniform formula.
  *  R14 Bounce-back (Sec. 2.4, eq. BB) is applied, like NEQ, to fbar at the wall interface
  *      in the Appendix's step 5: for xi_k . n < 0, fbar_k = fbar_(-k) + 2 rho_w W_k
  *      xi_k . u_w / RT, with the opposite velocity's step-4 value at the same interface
@@ -100,6 +109,8 @@ typedef struct {
     int model;        /* 0: the incompressible model (eq. icfeq, eq. macro_values);
                          1: the original DUGKS (eq. feq, rho u = sum xi f~ + rho G dt/2) */
     double bc_p_amp[6];/* pressure condition: p_w(t) = bc_p + bc_p_amp cos(omega t) */
+    const double *faces[3]; /* non-uniform mesh (reading R18): the n+1 interface
+                               coordinates per axis, or NULL for uniform spacing dx */
 } oracle_config;
 
 typedef struct {
@@ -127,6 +138,9 @@ typedef struct {
     real wall_u[6][3];  /* u_w per face; real-typed so it can carry a complex step */
     double t;
     long step;
+    int nonuni;         /* the mesh is given by its interface coordinates */
+    double *xf[3];      /* interface coordinates, n+1 per axis */
+    double *xc[3];      /* centres, extended: xc[a][i + 1] for i = -1 .. n (ghosts included) */
 } ostate;
 
 /* ---------------------------------------------------------------------------------
@@ -269,6 +283,22 @@ static void G_cell(const ostate *s, long ci, double t, real G[3])
     for (int a = 0; a < 3; a++) G[a] = (s->cfg.g[a] + s->field[a * s->ncell + ci]) * ct;
 }
 
+/* ---- non-uniform mesh metrics (reading R18) ---- */
+/* Interpolation weight of the high cell at interface i of axis a (centres i-1, i). */
+static double wface(const ostate *s, int a, int i)
+{
+    const double *c = s->xc[a] + 1;
+    return (s->xf[a][i] - c[i - 1]) / (c[i] - c[i - 1]);
+}
+/* 1 / (distance of the two centres across interface i of axis a). */
+static double inv_dc(const ostate *s, int a, int i)
+{
+    const double *c = s->xc[a] + 1;
+    return 1.0 / (c[i] - c[i - 1]);
+}
+/* Width of cell i along axis a. */
+static double width(const ostate *s, int a, int i) { return s->xf[a][i + 1] - s->xf[a][i]; }
+
 /* Acceleration at the interface x (normal axis d) and time t (reading R2). */
 static void G_face(const ostate *s, int d, const int x[3], double t, real G[3])
 {
@@ -288,6 +318,11 @@ static void G_face(const ostate *s, int d, const int x[3], double t, real G[3])
     }
     G_cell(s, cell_index(s, lo), t, Gl);
     G_cell(s, cell_index(s, hi), t, Gh);
+    if (s->nonuni && lo[d] != hi[d]) { /* linear interpolation to the interface (R18) */
+        const double w = wface(s, d, x[d]);
+        for (int a = 0; a < 3; a++) G[a] = (1.0 - w) * Gl[a] + w * Gh[a];
+        return;
+    }
     for (int a = 0; a < 3; a++) G[a] = 0.5 * (Gl[a] + Gh[a]);
 }
 
@@ -349,7 +384,14 @@ static void step_once(ostate *s)
                             y1[d] = side == 0 ? 1 : nd - 2;
                             const real *f0 = s->fc + ext_index(s, y0) * Q;
                             const real *f1 = s->fc + ext_index(s, y1) * Q;
-                            for (int k = 0; k < Q; k++) g[k] = 2.0 * f0[k] - f1[k];
+                            if (s->nonuni) { /* linear through the two centres to the ghost (R18) */
+                                const double *c = s->xc[d] + 1;
+                                const int i0 = y0[d], i1 = y1[d], ig = x[d];
+                                const double eg = (c[ig] - c[i0]) / (c[i1] - c[i0]);
+                                for (int k = 0; k < Q; k++) g[k] = f0[k] + eg * (f1[k] - f0[k]);
+                            } else {
+                                for (int k = 0; k < Q; k++) g[k] = 2.0 * f0[k] - f1[k];
+                            }
                         }
                     }
         }
@@ -365,7 +407,12 @@ static void step_once(ostate *s)
                     const real *fl = s->fc + ext_index(s, l) * Q;
                     const real *fr = s->fc + ext_index(s, x) * Q;
                     real *fb = s->fb[d] + face_index(s, d, x) * Q;
-                    for (int k = 0; k < Q; k++) fb[k] = 0.5 * (fl[k] + fr[k]);
+                    if (s->nonuni) {
+                        const double w = wface(s, d, x[d]);
+                        for (int k = 0; k < Q; k++) fb[k] = (1.0 - w) * fl[k] + w * fr[k];
+                    } else {
+                        for (int k = 0; k < Q; k++) fb[k] = 0.5 * (fl[k] + fr[k]);
+                    }
                 }
     }
     for (int p = 0; p < (D == 3 ? 3 : 1); p++) {
@@ -383,7 +430,12 @@ static void step_once(ostate *s)
                             y[a] += da;
                             y[b] += db;
                             const real *f = s->fc + ext_index(s, y) * Q;
-                            for (int k = 0; k < Q; k++) fbc[k] += 0.25 * f[k];
+                            double wt = 0.25;
+                            if (s->nonuni) { /* bilinear in the two axes (R18) */
+                                const double wa = wface(s, a, x[a]), wb = wface(s, b, x[b]);
+                                wt = (da == 0 ? wa : 1.0 - wa) * (db == 0 ? wb : 1.0 - wb);
+                            }
+                            for (int k = 0; k < Q; k++) fbc[k] += wt * f[k];
                         }
                 }
     }
@@ -413,9 +465,15 @@ static void step_once(ostate *s)
                     }
                     for (int k = 0; k < Q; k++) {
                         real sigma[3] = {0, 0, 0};
-                        sigma[d] = (fr[k] - fl[k]) / dx;
-                        for (int tdir = 0; tdir < D; tdir++)
-                            if (tdir != d) sigma[tdir] = (cp[tdir][k] - cm[tdir][k]) / dx;
+                        if (s->nonuni) {
+                            sigma[d] = (fr[k] - fl[k]) * inv_dc(s, d, x[d]);
+                            for (int tdir = 0; tdir < D; tdir++)
+                                if (tdir != d) sigma[tdir] = (cp[tdir][k] - cm[tdir][k]) / width(s, tdir, x[tdir]);
+                        } else {
+                            sigma[d] = (fr[k] - fl[k]) / dx;
+                            for (int tdir = 0; tdir < D; tdir++)
+                                if (tdir != d) sigma[tdir] = (cp[tdir][k] - cm[tdir][k]) / dx;
+                        }
                         real xs = 0;
                         for (int a = 0; a < D; a++) xs += s->c * s->e[k][a] * sigma[a];
                         Fb[k] = fb[k] - h * xs;
@@ -502,7 +560,8 @@ static void step_once(ostate *s)
     }
 
     /* Step 8: micro-flux m = sum over the cell's interfaces of (xi.n_j) f(x_j) s_j
-     * (eq. microflux); on the uniform mesh s_j = dx^(D-1). */
+     * (eq. microflux); on the uniform mesh s_j = dx^(D-1), on a non-uniform one the cell's
+     * extent across the other axes (R18). */
     const double area = D == 3 ? dx * dx : dx;
     const double vol = D == 3 ? dx * dx * dx : dx * dx;
     for (x[2] = 0; x[2] < s->n[2]; x[2]++)
@@ -510,14 +569,21 @@ static void step_once(ostate *s)
             for (x[0] = 0; x[0] < s->n[0]; x[0]++) {
                 real *m = s->m + cell_index(s, x) * Q;
                 for (int k = 0; k < Q; k++) m[k] = 0;
+                double cvol = vol;
+                if (s->nonuni) {
+                    cvol = 1.0;
+                    for (int a = 0; a < D; a++) cvol *= width(s, a, x[a]);
+                }
                 for (int d = 0; d < D; d++) {
                     int xp[3] = {x[0], x[1], x[2]};
                     xp[d] += 1;
                     const real *fm = s->Fb[d] + face_index(s, d, x) * Q;  /* n = -e_d */
                     const real *fp = s->Fb[d] + face_index(s, d, xp) * Q; /* n = +e_d */
+                    /* interface area s_j: the cell's extent across the other axes */
+                    const double ar = s->nonuni ? cvol / width(s, d, x[d]) : area;
                     for (int k = 0; k < Q; k++) {
                         const double xn = s->c * s->e[k][d];
-                        m[k] += xn * fp[k] * area - xn * fm[k] * area;
+                        m[k] += xn * fp[k] * ar - xn * fm[k] * ar;
                     }
                 }
             }
@@ -531,9 +597,14 @@ static void step_once(ostate *s)
                 real *F = s->F + ci * Q;
                 const real *f = s->fc + ext_index(s, x) * Q;
                 const real *m = s->m + ci * Q;
+                double cvol = vol;
+                if (s->nonuni) {
+                    cvol = 1.0;
+                    for (int a = 0; a < D; a++) cvol *= width(s, a, x[a]);
+                }
                 for (int k = 0; k < Q; k++) {
                     real ftp = 4.0 / 3.0 * f[k] - 1.0 / 3.0 * F[k];
-                    F[k] = ftp - dt / vol * m[k];
+                    F[k] = ftp - dt / cvol * m[k];
                 }
             }
 
@@ -609,6 +680,29 @@ void *oracle_create(const oracle_config *cfg)
     }
     for (int w = 0; w < 6; w++)
         for (int a = 0; a < 3; a++) s->wall_u[w][a] = cfg->bc_u[w][a];
+    /* non-uniform mesh (reading R18): interface coordinates and extended centres */
+    for (int a = 0; a < s->D; a++) s->nonuni |= cfg->faces[a] != NULL;
+    for (int a = 0; ok && s->nonuni && a < s->D; a++) {
+        const int n = s->n[a];
+        s->xf[a] = (double *)calloc((size_t)n + 1, sizeof(double));
+        s->xc[a] = (double *)calloc((size_t)n + 2, sizeof(double));
+        ok = s->xf[a] && s->xc[a];
+        if (!ok) break;
+        for (int i = 0; i <= n; i++) s->xf[a][i] = cfg->faces[a] ? cfg->faces[a][i] : i * cfg->dx;
+        for (int i = 0; i < n; i++) {
+            if (!(s->xf[a][i + 1] > s->xf[a][i])) ok = 0;
+            s->xc[a][i + 1] = 0.5 * (s->xf[a][i] + s->xf[a][i + 1]);
+        }
+        if (!ok) break;
+        if (cfg->bc_type[2 * a] == BC_PERIODIC) { /* images one period away */
+            const double L = s->xf[a][n] - s->xf[a][0];
+            s->xc[a][0] = s->xc[a][n] - L;
+            s->xc[a][n + 1] = s->xc[a][1] + L;
+        } else { /* boundary centres mirrored in the walls */
+            s->xc[a][0] = 2.0 * s->xf[a][0] - s->xc[a][1];
+            s->xc[a][n + 1] = 2.0 * s->xf[a][n] - s->xc[a][n];
+        }
+    }
     if (!ok) {
         oracle_destroy(s);
         return NULL;
@@ -623,6 +717,7 @@ void oracle_destroy(void *p)
     free(s->F); free(s->fc); free(s->m); free(s->field);
     for (int d = 0; d < 3; d++) {
         free(s->fb[d]); free(s->Fb[d]); free(s->rhob[d]); free(s->ub[d]); free(s->fbc[d]);
+        free(s->xf[d]); free(s->xc[d]);
     }
     free(s);
 }

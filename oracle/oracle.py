@@ -36,6 +36,7 @@ class OracleConfig(C.Structure):
         ("bc_p", C.c_double * 6),
         ("model", C.c_int),
         ("bc_p_amp", C.c_double * 6),
+        ("faces", C.POINTER(C.c_double) * 3),
     ]
 
 
@@ -98,7 +99,7 @@ class Oracle:
     """
 
     def __init__(self, shape, q, nu, dt, dx=1.0, rt=1.0 / 3.0, rho0=1.0, g=(0.0, 0.0, 0.0),
-                 omega=0.0, bcs=None, field=None, complex_step=False, model=0):
+                 omega=0.0, bcs=None, field=None, complex_step=False, model=0, faces=None):
         dim = len(shape)
         nx, ny = int(shape[0]), int(shape[1])
         nz = int(shape[2]) if dim == 3 else 1
@@ -109,6 +110,13 @@ class Oracle:
             cfg.g[a] = float(g[a]) if a < len(g) else 0.0
         cfg.omega = omega
         cfg.model = int(model)
+        # non-uniform mesh: interface coordinates per axis (None: uniform spacing dx)
+        self._faces = []
+        for a, fa in enumerate(list(faces or [])[:3]):
+            if fa is not None:
+                arr = np.ascontiguousarray(fa, dtype=np.float64)
+                self._faces.append(arr)
+                cfg.faces[a] = arr.ctypes.data_as(C.POINTER(C.c_double))
         bcs = list(bcs or [])
         bcs += [(BC_PERIODIC, (0.0, 0.0, 0.0), 0.0)] * (6 - len(bcs))
         for w in range(6):

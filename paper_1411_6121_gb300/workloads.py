@@ -135,3 +135,12 @@ def random_state_fields(shape, seed, u_amp=0.05, p_amp=1e-3):
         u[a] = (u_amp * (0.8 * smooth + 0.2 * noise)).ravel()
     p = (p_amp * rng.standard_normal(n))
     return p, u
+
+
+def tanh_faces(n, length=1.0, k=2.5):
+    """Interface coordinates of the paper's non-uniform mesh (Sec. 3.4): zeta_i = 0.5 +
+    tanh(k (i/n - 0.5)) / (2 tanh(k/2)), i = 0 .. n, scaled to [0, length] (clustered at both
+    ends; cell centres are the midpoints of their interfaces)."""
+    import numpy as np
+    i = np.arange(n + 1)
+    return length * (0.5 + np.tanh(k * (i / n - 0.5)) / (2.0 * np.tanh(k / 2.0)))
