@@ -1062,6 +1062,7 @@ static int check_adjoint_support(dugks_t h) {
         return handle_fail(h, DUGKS_E_UNSUPPORTED, "record/adjoint: F32 or F64 storage only");
     if (h->model != DUGKS_MODEL_INCOMPRESSIBLE)
         return handle_fail(h, DUGKS_E_UNSUPPORTED, "record/adjoint: the incompressible model only");
+    if (h->d_metric) return handle_fail(h, DUGKS_E_UNSUPPORTED, "record/adjoint: uniform meshes only");
     return DUGKS_OK;
 }
 

@@ -10,9 +10,11 @@
 #include <string.h>
 #include <time.h>
 
+#include <algorithm>
 #include <map>
 #include <string>
 #include <utility>
+#include <vector>
 
 #include "../../include/dugks.h"
 #include "dugks_internal.h"
@@ -77,6 +79,12 @@ StepParams dugks::handle_params(const dugks_t h) {
     p.step_ctr = h->d_step;
     p.step_off = 0;
     p.model = h->model;
+    if (h->d_metric) {
+        p.metric[0] = h->d_metric;
+        p.metric[1] = h->d_metric + h->metric_off1;
+        for (int a = 0; a < 2; a++)
+            for (int sd = 0; sd < 2; sd++) p.eg[a][sd] = h->eg[a][sd];
+    }
     for (int w = 0; w < 6; w++) {
         p.bc[w] = h->bcs.face[w].type;
         for (int a = 0; a < 3; a++) p.bc_u[w][a] = h->bcs.face[w].u[a];
@@ -100,6 +108,39 @@ cudaError_t dugks::handle_launch_step(dugks_t h, StepParams &p) {
         case 27: return launch_step_q27(p, h->store, h->tile_x, h->tile_y, h->stream);
     }
     return cudaErrorNotSupported;
+}
+
+// Metrics of a non-uniform 2D mesh (Sec. 3.4; the same reading as the oracle): centres are
+// the midpoints of their interfaces; the ghost centres sit one period away on a periodic
+// axis and are the boundary centres mirrored in the wall otherwise. Per axis the device block
+// holds wf (n+1), idc (n+1) and idx (n) (see StepParams).
+static int build_metrics(dugks_t h, const dugks_mesh *mesh, const dugks_boundaries *bcs) {
+    const int64_t nn[2] = {h->nx, h->ny};
+    std::vector<double> all;
+    for (int a = 0; a < 2; a++) {
+        const int64_t n = nn[a];
+        std::vector<double> xf(n + 1), xc(n + 2);
+        for (int64_t i = 0; i <= n; i++) xf[i] = mesh->faces[a] ? mesh->faces[a][i] : (double)i * mesh->dx;
+        for (int64_t i = 0; i < n; i++) xc[i + 1] = 0.5 * (xf[i] + xf[i + 1]);
+        if (bcs->face[2 * a].type == DUGKS_BC_PERIODIC) {
+            const double L = xf[n] - xf[0];
+            xc[0] = xc[n] - L;
+            xc[n + 1] = xc[1] + L;
+        } else {
+            xc[0] = 2.0 * xf[0] - xc[1];
+            xc[n + 1] = 2.0 * xf[n] - xc[n];
+        }
+        const double *c = xc.data() + 1;  // c[i] for i = -1 .. n
+        if (a == 1) h->metric_off1 = (int64_t)all.size();
+        for (int64_t i = 0; i <= n; i++) all.push_back((xf[i] - c[i - 1]) / (c[i] - c[i - 1]));
+        for (int64_t i = 0; i <= n; i++) all.push_back(1.0 / (c[i] - c[i - 1]));
+        for (int64_t i = 0; i < n; i++) all.push_back(1.0 / (xf[i + 1] - xf[i]));
+        h->eg[a][0] = n >= 2 ? (c[-1] - c[0]) / (c[1] - c[0]) : -1.0;
+        h->eg[a][1] = n >= 2 ? (c[n] - c[n - 1]) / (c[n - 2] - c[n - 1]) : -1.0;
+    }
+    CUDA_TRY(h, cudaMalloc((void **)&h->d_metric, sizeof(double) * all.size()));
+    CUDA_TRY(h, cudaMemcpy(h->d_metric, all.data(), sizeof(double) * all.size(), cudaMemcpyHostToDevice));
+    return DUGKS_OK;
 }
 
 extern "C" {
@@ -144,8 +185,29 @@ int dugks_create(const dugks_mesh *mesh, int32_t lattice, double nu, double dt, 
         return handle_fail(NULL, DUGKS_E_INVAL, "bad model selector");
     if (o.model == DUGKS_MODEL_ORIGINAL) o.kernel = 1;  // the original model runs on the reference kernel
     const double c = sqrt(3.0 * o.rt);
-    if (dt > mesh->dx / c * (1.0 + 1e-12))
-        return handle_fail(NULL, DUGKS_E_CFL, "dt = %g exceeds dx/sqrt(3RT) = %g (CFL number > 1)", dt, mesh->dx / c);
+    // non-uniform mesh (Sec. 3.4): interface coordinates per axis; D2Q9 on the reference kernel
+    const bool nonuni = mesh->faces[0] || mesh->faces[1] || mesh->faces[2];
+    double hmin = mesh->dx;  // smallest cell width of the 2D axes (CFL)
+    if (nonuni) {
+        hmin = INFINITY;
+        if (!mesh->faces[0] || !mesh->faces[1]) hmin = mesh->dx;
+        if (dim != 2 || lattice != DUGKS_D2Q9 || mesh->faces[2])
+            return handle_fail(NULL, DUGKS_E_UNSUPPORTED, "non-uniform meshes: 2D D2Q9 only");
+        if (o.store == DUGKS_STORE_BF16 || o.store == DUGKS_STORE_F16)
+            return handle_fail(NULL, DUGKS_E_UNSUPPORTED, "non-uniform meshes: F32 or F64 storage");
+        const int64_t nn[2] = {mesh->nx, mesh->ny};
+        for (int a = 0; a < 2; a++) {
+            if (!mesh->faces[a]) continue;
+            for (int64_t i = 0; i < nn[a]; i++) {
+                const double w = mesh->faces[a][i + 1] - mesh->faces[a][i];
+                if (!(w > 0)) return handle_fail(NULL, DUGKS_E_INVAL, "interface coordinates must increase");
+                hmin = std::min(hmin, w);
+            }
+        }
+        o.kernel = 1;  // the reference kernel carries the metrics
+    }
+    if (dt > hmin / c * (1.0 + 1e-12))
+        return handle_fail(NULL, DUGKS_E_CFL, "dt = %g exceeds dx/sqrt(3RT) = %g (CFL number > 1)", dt, hmin / c);
     const int64_t n[3] = {mesh->nx, mesh->ny, mesh->nz};
     for (int d = 0; d < 3; d++) {
         const int lo = bcs->face[2 * d].type, hi = bcs->face[2 * d + 1].type;
@@ -249,6 +311,13 @@ int dugks_create(const dugks_mesh *mesh, int32_t lattice, double nu, double dt, 
         dugks_destroy(h);
         return rc;
     }
+    if (nonuni) {
+        rc = build_metrics(h, mesh, bcs);
+        if (rc != DUGKS_OK) {
+            dugks_destroy(h);
+            return rc;
+        }
+    }
     *out = h;
     return DUGKS_OK;
 }
@@ -265,6 +334,7 @@ void dugks_destroy(dugks_t h) {
     cudaFree(h->d_partials);
     cudaFree(h->d_res);
     cudaFree(h->d_mom);
+    cudaFree(h->d_metric);
     if (h->h_res) cudaFreeHost(h->h_res);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;

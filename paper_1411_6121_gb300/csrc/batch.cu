@@ -228,6 +228,8 @@ int dugks_batch_create(int32_t count, const dugks_mesh *meshes, const double *nu
     const double c = sqrt(3.0 * o.rt);
     for (int i = 0; i < count; i++) {
         const dugks_mesh &m = meshes[i];
+        if (m.faces[0] || m.faces[1] || m.faces[2])
+            return bfail(nullptr, DUGKS_E_UNSUPPORTED, "instance %d: the batch takes uniform meshes", i);
         if (m.dim != 2 || m.nz != 1 || m.nx < 1 || m.ny < 1 || m.nx > (1 << 30) || m.ny > (1 << 30) || !(m.dx > 0) ||
             !(nu[i] > 0))
             return bfail(nullptr, DUGKS_E_INVAL, "instance %d: bad 2D mesh or viscosity", i);

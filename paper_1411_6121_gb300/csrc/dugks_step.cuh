@@ -69,6 +69,32 @@ __device__ __forceinline__ T wall_drho(const StepParams &p, const Coef<T> &cf, i
     return (T)p.bc_drho[wid] + (T)p.bc_drho1[wid] * cf.cwh;
 }
 
+// Steps 3-4 on a non-uniform 2D mesh (Sec. 3.4, the same reading as the oracle): the
+// interface value interpolates linearly between the two centres (weight w of the high cell),
+// the normal gradient divides their difference by the centre distance, and the tangential
+// gradient divides the difference of the interface's two end points, each bilinear in the
+// four cells around it (weights wm, wp of the high row), by the interface length:
+//   F = M - hc e_d (R - L) idc - hc e_t (Vp - Vm) idt,  M = (1 - w) L + w R,
+//   Vp = (1 - wp) M + wp Mp,  Vm = (1 - wm) Mm + wm M.
+// hcn = h c idc and hct = h c idt. Pointers as in reconstruct (2D: the first tangential pair).
+template <int Q, int d, class T>
+__device__ __forceinline__ void reconstruct_nu(const T *L, const T *R, const T *L1m, const T *R1m, const T *L1p,
+                                               const T *R1p, T w, T wm, T wp, T hcn, T hct, T F[Q]) {
+    constexpr int t1 = d == 0 ? 1 : 0;
+    for (int k = 0; k < Q; k++) {
+        const T l = L[k], r = R[k];
+        const T mid = fmaT(w, r - l, l);
+        T v = mid;
+        if (Lat<Q>::e(k, d) != 0) v = fmaT(-hcn * (T)Lat<Q>::e(k, d), r - l, v);
+        if (Lat<Q>::e(k, t1) != 0) {
+            const T midp = fmaT(w, R1p[k] - L1p[k], L1p[k]), midm = fmaT(w, R1m[k] - L1m[k], L1m[k]);
+            const T vp = fmaT(wp, midp - mid, mid), vm = fmaT(wm, mid - midm, midm);
+            v = fmaT(-hct * (T)Lat<Q>::e(k, t1), vp - vm, v);
+        }
+        F[k] = v;
+    }
+}
+
 // The model switch of the reference path. For the incompressible model (eq. icfeq,
 // eq. macro_values) the momentum variable is m = rho0 u / c and f_eq, S divide by rho0;
 // returns 1/rho0. For the original DUGKS (p.model == 1: eq. feq, rho u = sum xi f~ + rho G w)
@@ -174,7 +200,7 @@ __device__ __forceinline__ void cell_G(const StepParams &p, int64_t cell, int64_
 
 // One tile of the fused step: cells [x0, x0+TX) x [y0, y0+TY) x [z0, z1) of the instance
 // described by p, with the CTA's TX*TY threads and its dynamic shared memory.
-template <int Q, class S, int TX, int TY>
+template <int Q, class S, int TX, int TY, bool NU = false>
 __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, int z0, int z1,
                                           unsigned char *smem_raw) {
     using T = typename Arith<S>::T;
@@ -204,6 +230,18 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
         ct = (T)(cos(p.omega * tn) * p.inv_c);
         cth = (T)(cos(p.omega * (tn + 0.5 * p.dt)) * p.inv_c);
     }
+
+    // Non-uniform 2D mesh metrics (Sec. 3.4): interpolation weight of the high cell at
+    // interface i, 1 / centre distance across it, 1 / width of cell i; hc = h c.
+    auto mptr = [&](int a) __attribute__((always_inline)) { return a ? p.metric[1] : p.metric[0]; };
+    auto mwf = [&](int a, int i) __attribute__((always_inline)) -> T { return (T)__ldg(mptr(a) + i); };
+    auto midc = [&](int a, int i) __attribute__((always_inline)) -> T {
+        return (T)__ldg(mptr(a) + (a ? ny : nx) + 1 + i);
+    };
+    auto midx = [&](int a, int i) __attribute__((always_inline)) -> T {
+        return (T)__ldg(mptr(a) + 2 * (a ? ny : nx) + 2 + i);
+    };
+    const T hc = NU ? (T)(0.5 * p.dt / p.inv_c) : T(0);
 
     auto slot_of = [](int pz) __attribute__((always_inline)) { return D == 3 ? (pz + 3) % 3 : 0; };
     auto cellp = [&](int slot, int ry, int rx) __attribute__((always_inline)) -> T * { return phi + slot * K::PLANE + (ry * RX + rx) * Q; };
@@ -249,8 +287,14 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
                 const int s1 = hi ? -1 : 1;
                 T *o = cellp(slot, ry, rx);
                 const T *a = cellp(slot, ry, rx + s1), *b = cellp(slot, ry, rx + 2 * s1);
+                if constexpr (NU) {  // linear through the two boundary centres (ghost centre mirrored)
+                    const T eg = (T)p.eg[0][hi];
 #pragma unroll
-                for (int k = 0; k < Q; k++) o[k] = ghost_value(a[k], b[k]);
+                    for (int k = 0; k < Q; k++) o[k] = fmaT(eg, b[k] - a[k], a[k]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < Q; k++) o[k] = ghost_value(a[k], b[k]);
+                }
             }
         }
         if (ywall) {
@@ -264,8 +308,14 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
                 const int s1 = hi ? -1 : 1;
                 T *o = cellp(slot, ry, rx);
                 const T *a = cellp(slot, ry + s1, rx), *b = cellp(slot, ry + 2 * s1, rx);
+                if constexpr (NU) {
+                    const T eg = (T)p.eg[1][hi];
 #pragma unroll
-                for (int k = 0; k < Q; k++) o[k] = ghost_value(a[k], b[k]);
+                    for (int k = 0; k < Q; k++) o[k] = fmaT(eg, b[k] - a[k], a[k]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < Q; k++) o[k] = ghost_value(a[k], b[k]);
+                }
             }
         }
     };
@@ -293,10 +343,15 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
         cl[d] = lo; ch[d] = hi;
         const int64_t il = (int64_t)cl[0] + (int64_t)nx * ((int64_t)cl[1] + (int64_t)ny * cl[2]);
         const int64_t ih = (int64_t)ch[0] + (int64_t)nx * ((int64_t)ch[1] + (int64_t)ny * ch[2]);
+        // non-uniform mesh: linear interpolation to the interface between distinct cells
+        const T wh = (NU && lo != hi) ? mwf(d, gfd) : T(0.5);
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             T v = (a < D) ? (T)p.g[a] : T(0);
-            if (p.field && a < D) v += T(0.5) * ((T)__ldg(p.field + a * ncell + il) + (T)__ldg(p.field + a * ncell + ih));
+            if (p.field && a < D) {
+                const T fl = (T)__ldg(p.field + a * ncell + il), fh = (T)__ldg(p.field + a * ncell + ih);
+                v += NU ? fmaT(wh, fh - fl, fl) : T(0.5) * (fl + fh);
+            }
             G[a] = v * cth;
         }
     };
@@ -357,21 +412,33 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
             const int gfx = x0 + fx, gy = y0 + fy;
             if (gy >= ny || gfx > nx) continue;
             T F[Q];
-            reconstruct<Q, 0, T>(cellp(s, fy + 1, fx), cellp(s, fy + 1, fx + 1), cellp(s, fy, fx), cellp(s, fy, fx + 1),
-                              cellp(s, fy + 2, fx), cellp(s, fy + 2, fx + 1), cellp(sm, fy + 1, fx),
-                              cellp(sm, fy + 1, fx + 1), cellp(sp, fy + 1, fx), cellp(sp, fy + 1, fx + 1), cf.kappa,
-                              F);
+            if constexpr (NU)
+                reconstruct_nu<Q, 0, T>(cellp(s, fy + 1, fx), cellp(s, fy + 1, fx + 1), cellp(s, fy, fx),
+                                        cellp(s, fy, fx + 1), cellp(s, fy + 2, fx), cellp(s, fy + 2, fx + 1),
+                                        mwf(0, gfx), mwf(1, gy), mwf(1, gy + 1), hc * midc(0, gfx), hc * midx(1, gy), F);
+            else
+                reconstruct<Q, 0, T>(cellp(s, fy + 1, fx), cellp(s, fy + 1, fx + 1), cellp(s, fy, fx),
+                                     cellp(s, fy, fx + 1), cellp(s, fy + 2, fx), cellp(s, fy + 2, fx + 1),
+                                     cellp(sm, fy + 1, fx), cellp(sm, fy + 1, fx + 1), cellp(sp, fy + 1, fx),
+                                     cellp(sp, fy + 1, fx + 1), cf.kappa, F);
             T Gb[3];
             face_G(0, gfx, gy, kz, gfx, Gb);
             const int wall = !perx && (gfx == 0 || gfx == nx);
             T Fc[Q], Gc[3] = {T(0), T(0), T(0)};
             if (wall) {
                 const int cx = gfx == 0 ? fx + 1 : fx - 1;  // x_c: interface 1 or nx-1
-                reconstruct<Q, 0, T>(cellp(s, fy + 1, cx), cellp(s, fy + 1, cx + 1), cellp(s, fy, cx),
-                                  cellp(s, fy, cx + 1), cellp(s, fy + 2, cx), cellp(s, fy + 2, cx + 1),
-                                  cellp(sm, fy + 1, cx), cellp(sm, fy + 1, cx + 1), cellp(sp, fy + 1, cx),
-                                  cellp(sp, fy + 1, cx + 1), cf.kappa, Fc);
-                face_G(0, gfx, gy, kz, gfx == 0 ? 1 : nx - 1, Gc);
+                const int gcx = gfx == 0 ? 1 : nx - 1;
+                if constexpr (NU)
+                    reconstruct_nu<Q, 0, T>(cellp(s, fy + 1, cx), cellp(s, fy + 1, cx + 1), cellp(s, fy, cx),
+                                            cellp(s, fy, cx + 1), cellp(s, fy + 2, cx), cellp(s, fy + 2, cx + 1),
+                                            mwf(0, gcx), mwf(1, gy), mwf(1, gy + 1), hc * midc(0, gcx),
+                                            hc * midx(1, gy), Fc);
+                else
+                    reconstruct<Q, 0, T>(cellp(s, fy + 1, cx), cellp(s, fy + 1, cx + 1), cellp(s, fy, cx),
+                                         cellp(s, fy, cx + 1), cellp(s, fy + 2, cx), cellp(s, fy + 2, cx + 1),
+                                         cellp(sm, fy + 1, cx), cellp(sm, fy + 1, cx + 1), cellp(sp, fy + 1, cx),
+                                         cellp(sp, fy + 1, cx + 1), cf.kappa, Fc);
+                face_G(0, gfx, gy, kz, gcx, Gc);
             }
             interface_f<Q, 0, T>(p, cf, F, Gb, wall, gfx == 0 ? 0 : 1, Fc, Gc, xf + (fy * (TX + 1) + fx) * K::SX);
         }
@@ -381,21 +448,33 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
             const int gx = x0 + fx, gfy = y0 + fy;
             if (gx >= nx || gfy > ny) continue;
             T F[Q];
-            reconstruct<Q, 1, T>(cellp(s, fy, fx + 1), cellp(s, fy + 1, fx + 1), cellp(s, fy, fx), cellp(s, fy + 1, fx),
-                              cellp(s, fy, fx + 2), cellp(s, fy + 1, fx + 2), cellp(sm, fy, fx + 1),
-                              cellp(sm, fy + 1, fx + 1), cellp(sp, fy, fx + 1), cellp(sp, fy + 1, fx + 1), cf.kappa,
-                              F);
+            if constexpr (NU)
+                reconstruct_nu<Q, 1, T>(cellp(s, fy, fx + 1), cellp(s, fy + 1, fx + 1), cellp(s, fy, fx),
+                                        cellp(s, fy + 1, fx), cellp(s, fy, fx + 2), cellp(s, fy + 1, fx + 2),
+                                        mwf(1, gfy), mwf(0, gx), mwf(0, gx + 1), hc * midc(1, gfy), hc * midx(0, gx), F);
+            else
+                reconstruct<Q, 1, T>(cellp(s, fy, fx + 1), cellp(s, fy + 1, fx + 1), cellp(s, fy, fx),
+                                     cellp(s, fy + 1, fx), cellp(s, fy, fx + 2), cellp(s, fy + 1, fx + 2),
+                                     cellp(sm, fy, fx + 1), cellp(sm, fy + 1, fx + 1), cellp(sp, fy, fx + 1),
+                                     cellp(sp, fy + 1, fx + 1), cf.kappa, F);
             T Gb[3];
             face_G(1, gx, gfy, kz, gfy, Gb);
             const int wall = !pery && (gfy == 0 || gfy == ny);
             T Fc[Q], Gc[3] = {T(0), T(0), T(0)};
             if (wall) {
                 const int cy = gfy == 0 ? fy + 1 : fy - 1;
-                reconstruct<Q, 1, T>(cellp(s, cy, fx + 1), cellp(s, cy + 1, fx + 1), cellp(s, cy, fx),
-                                  cellp(s, cy + 1, fx), cellp(s, cy, fx + 2), cellp(s, cy + 1, fx + 2),
-                                  cellp(sm, cy, fx + 1), cellp(sm, cy + 1, fx + 1), cellp(sp, cy, fx + 1),
-                                  cellp(sp, cy + 1, fx + 1), cf.kappa, Fc);
-                face_G(1, gx, gfy == 0 ? 1 : ny - 1, kz, gfy == 0 ? 1 : ny - 1, Gc);
+                const int gcy = gfy == 0 ? 1 : ny - 1;
+                if constexpr (NU)
+                    reconstruct_nu<Q, 1, T>(cellp(s, cy, fx + 1), cellp(s, cy + 1, fx + 1), cellp(s, cy, fx),
+                                            cellp(s, cy + 1, fx), cellp(s, cy, fx + 2), cellp(s, cy + 1, fx + 2),
+                                            mwf(1, gcy), mwf(0, gx), mwf(0, gx + 1), hc * midc(1, gcy),
+                                            hc * midx(0, gx), Fc);
+                else
+                    reconstruct<Q, 1, T>(cellp(s, cy, fx + 1), cellp(s, cy + 1, fx + 1), cellp(s, cy, fx),
+                                         cellp(s, cy + 1, fx), cellp(s, cy, fx + 2), cellp(s, cy + 1, fx + 2),
+                                         cellp(sm, cy, fx + 1), cellp(sm, cy + 1, fx + 1), cellp(sp, cy, fx + 1),
+                                         cellp(sp, cy + 1, fx + 1), cf.kappa, Fc);
+                face_G(1, gx, gcy, kz, gcy, Gc);
             }
             interface_f<Q, 1, T>(p, cf, F, Gb, wall, gfy == 0 ? 0 : 1, Fc, Gc, yf + (fy * TX + fx) * K::SY);
         }
@@ -411,9 +490,21 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
             const T *xm = xf + (ly * (TX + 1) + lx) * K::SX, *xp = xm + K::SX;
             const T *ym = yf + (ly * TX + lx) * K::SY, *yp = ym + TX * K::SY;
             const CellRandom rnd(seed, off);
+            // non-uniform mesh: the flux of each axis is divided by the cell's width along it
+            const T dcx = NU ? (T)(p.dt / p.inv_c) * midx(0, gx) : T(0);
+            const T dcy = NU ? (T)(p.dt / p.inv_c) * midx(1, gy) : T(0);
             sfor<Q>([&](auto kc) {
                 constexpr int k = kc;
                 T acc = T(0);
+                if constexpr (NU) {
+                    T ax = T(0), ay = T(0);
+                    if constexpr (Lat<Q>::e(k, 0) != 0) ax = (T)Lat<Q>::e(k, 0) * (xp[flux_index<Q>(0, k)] - xm[flux_index<Q>(0, k)]);
+                    if constexpr (Lat<Q>::e(k, 1) != 0) ay = (T)Lat<Q>::e(k, 1) * (yp[flux_index<Q>(1, k)] - ym[flux_index<Q>(1, k)]);
+                    const T gold = (T)Store<S>::ld(src + k * p.dstride + off);
+                    const T v = fmaT(T(1) / T(3), ph[k] - gold, ph[k]) - fmaT(dcx, ax, dcy * ay);
+                    store_state<S>(dst + k * p.dstride + off, v, sizeof(S) == 2 ? rnd.bits<k>() : 0u);
+                    return;
+                }
                 if constexpr (Lat<Q>::e(k, 0) != 0) {
                     constexpr int i = flux_index<Q>(0, k);
                     acc = fmaT((T)Lat<Q>::e(k, 0), xp[i] - xm[i], acc);
@@ -451,12 +542,13 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
     }
 }
 
-template <int Q, class S, int TX, int TY>
+// NU: a non-uniform 2D mesh (p.metric), D2Q9 only.
+template <int Q, class S, int TX, int TY, bool NU = false>
 __global__ void __launch_bounds__(TX *TY) fused_step(const __grid_constant__ StepParams p, int zchunk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int z0 = blockIdx.z * zchunk;
     const int z1 = min(p.nz, z0 + zchunk);
-    step_tile<Q, S, TX, TY>(p, blockIdx.x * TX, blockIdx.y * TY, z0, z1, smem_raw);
+    step_tile<Q, S, TX, TY, NU>(p, blockIdx.x * TX, blockIdx.y * TY, z0, z1, smem_raw);
 }
 
 // Batched form: many independent 2D instances in one persistent launch. params holds two

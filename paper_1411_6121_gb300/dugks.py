@@ -38,7 +38,8 @@ EXPORTS = [
 
 
 class Mesh(C.Structure):
-    _fields_ = [("dim", C.c_int32), ("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64), ("dx", C.c_double)]
+    _fields_ = [("dim", C.c_int32), ("nx", C.c_int64), ("ny", C.c_int64), ("nz", C.c_int64), ("dx", C.c_double),
+                ("faces", C.POINTER(C.c_double) * 3)]
 
 
 class FaceBC(C.Structure):
@@ -153,7 +154,7 @@ class Sim:
 
     def __init__(self, shape, q, nu, dt, dx=1.0, rt=1.0 / 3.0, rho0=1.0, g=(0.0, 0.0, 0.0), omega=0.0,
                  bcs=None, field=None, store=STORE_F32, stream=None, use_graph=True, tile=None, kernel=0,
-                 model=MODEL_INCOMPRESSIBLE):
+                 model=MODEL_INCOMPRESSIBLE, faces=None):
         lib = load()
         self.lib = lib
         dim = len(shape)
@@ -161,6 +162,12 @@ class Sim:
         self.shape = tuple(int(s) for s in shape)
         self.ncell = int(np.prod(self.shape))
         m = Mesh(dim, self.shape[0], self.shape[1], self.shape[2] if dim == 3 else 1, float(dx))
+        face_arrays = []  # non-uniform mesh: interface coordinates per axis (copied by create)
+        for a, fa in enumerate(list(faces or [])[:3]):
+            if fa is not None:
+                arr = np.ascontiguousarray(fa, dtype=np.float64)
+                face_arrays.append(arr)
+                m.faces[a] = arr.ctypes.data_as(C.POINTER(C.c_double))
         f = Force()
         for a in range(3):
             f.g[a] = float(g[a]) if a < len(g) else 0.0

@@ -4,6 +4,7 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_1411_6121_gb300 import dugks
@@ -32,12 +33,18 @@ def _create(**kw):
     args = dict(dim=2, nx=8, ny=8, nz=1, dx=1.0, q=9, nu=0.1, dt=0.5, rt=1.0 / 3.0, bcs=None)
     args.update(kw)
     m = dugks.Mesh(args["dim"], args["nx"], args["ny"], args["nz"], args["dx"])
+    keep = []
+    for ax, fa in enumerate(args.get("faces") or []):
+        if fa is not None:
+            keep.append(np.ascontiguousarray(fa, dtype=np.float64))
+            m.faces[ax] = keep[-1].ctypes.data_as(C.POINTER(C.c_double))
     f = dugks.Force()
     b = dugks.make_bcs(args["bcs"])
     o = dugks.Opts()
     lib.dugks_opts_default(C.byref(o))
     o.rt = args["rt"]
     o.model = args.get("model", 0)
+    o.store = args.get("store", 0)
     h = C.c_void_p()
     rc = lib.dugks_create(C.byref(m), args["q"], args["nu"], args["dt"], C.byref(f), C.byref(b), C.byref(o), C.byref(h))
     return rc, h, lib.dugks_last_error(None).decode()
@@ -56,6 +63,24 @@ def test_cfl_violation_rejected():
 def test_invalid_arguments_rejected(kw):
     rc, h, msg = _create(**kw)
     assert rc in (-1, -7) and not h.value and msg
+
+
+_TANH8 = np.array([0.0, 0.3, 0.9, 2.0, 4.0, 6.0, 7.1, 7.7, 8.0])  # 8 cells, widths 0.3 .. 2
+
+
+@pytest.mark.parametrize("kw,code", [
+    # a non-uniform mesh (Sec. 3.4) is D2Q9 with F32 or F64 storage; its coordinates increase
+    (dict(dim=3, q=19, nz=4, dt=0.1, faces=[_TANH8]), -7),
+    (dict(dim=3, q=19, nz=8, dt=0.1, faces=[None, None, _TANH8]), -7),
+    (dict(store=1, dt=0.1, faces=[None, _TANH8]), -7),
+    (dict(store=2, dt=0.1, faces=[_TANH8]), -7),
+    (dict(dt=0.1, faces=[None, _TANH8[::-1].copy()]), -1),
+    # the CFL condition takes the smallest width: 0.3 / sqrt(3 RT) = 0.3
+    (dict(dt=0.31, faces=[None, _TANH8]), -2),
+])
+def test_nonuniform_mesh_arguments_rejected(kw, code):
+    rc, h, msg = _create(**kw)
+    assert rc == code and not h.value and msg
 
 
 def test_null_handle_calls_fail_cleanly():
