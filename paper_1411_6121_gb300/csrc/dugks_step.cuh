@@ -99,11 +99,12 @@ __device__ __forceinline__ void reconstruct_nu(const T *L, const T *R, const T *
 // eq. macro_values) the momentum variable is m = rho0 u / c and f_eq, S divide by rho0;
 // returns 1/rho0. For the original DUGKS (p.model == 1: eq. feq, rho u = sum xi f~ + rho G w)
 // m = rho u / c: the force shift that moments() applied with rho0 is completed to
-// rho = rho0 + drho, and 1/rho is returned for f_eq and S.
-template <class T>
+// rho = rho0 + drho, and 1/rho is returned for f_eq and S. ORIG = false compiles the switch
+// out (kernels that only run the incompressible model).
+template <class T, bool ORIG = true>
 __device__ __forceinline__ T original_model(const StepParams &p, const Coef<T> &cf, const T Gh[3], T w, T drho,
                                             T m[3]) {
-    if (p.model != 1) return cf.inv_rho0;
+    if (!ORIG || p.model != 1) return cf.inv_rho0;
 #pragma unroll
     for (int a = 0; a < 3; a++) m[a] = fmaT(Gh[a], w * drho, m[a]);
     return rcp_rn(cf.rho0 + drho);
@@ -113,11 +114,12 @@ __device__ __forceinline__ T original_model(const StepParams &p, const Coef<T> &
 // wall condition, NEQ or bounce-back, when wall != 0). Fc: step-4 values at x_c, the boundary
 // cell's opposite interface (read only by NEQ). side: 0 for the low wall (outward normal -e_d),
 // 1 for the high wall. Writes the original f of eq. original_f for the velocities with
-// e_d != 0 into out[flux_index(d, k)] (stride 1).
-template <int Q, int d, class T>
+// e_d != 0 into out[flux_index(d, k)] (stride 1). ORIG as in original_model.
+template <int Q, int d, class T, bool ORIG = true>
 __device__ __forceinline__ void interface_f(const StepParams &p, const Coef<T> &cf, T F[Q], const T Gh[3], int wall,
                                             int side, const T *Fc, const T Ghc[3], T *out) {
     constexpr int D = Lat<Q>::D;
+    const bool orig = ORIG && p.model == 1;
     if (wall && p.bc[2 * d + side] == 3) {
         // Step 5, eq. BB: F_k = F_-k + 2 rho0 W_k xi_k.u_w / RT for xi . n < 0, i.e.
         // g_k = g_-k + 6 W_k e_k.m_w with m_w = rho0 u_w / c (deviations: W_k = W_-k)
@@ -146,22 +148,22 @@ __device__ __forceinline__ void interface_f(const StepParams &p, const Coef<T> &
         const int wid = 2 * d + side;
         T drc, mc[3];
         moments<Q, T>(Fc, Ghc, cf.wface * cf.rho0, drc, mc);
-        const T irc = original_model(p, cf, Ghc, cf.wface, drc, mc);
+        const T irc = original_model<T, ORIG>(p, cf, Ghc, cf.wface, drc, mc);
         T dra, ma[3];
         if (p.bc[wid] == 1) {  // velocity condition: u_a = u_w, rho_a = rho_c
             dra = drc;
             // m = rho u / c: rho0 u_w / c, or rho_a u_w / c in the original model
-            const double ra = p.model == 1 ? p.rho0 + (double)drc : p.rho0;
+            const double ra = orig ? p.rho0 + (double)drc : p.rho0;
             ma[0] = (T)(p.bc_u[wid][0] * ra * p.inv_c);
             ma[1] = (T)(p.bc_u[wid][1] * ra * p.inv_c);
             ma[2] = (T)(p.bc_u[wid][2] * ra * p.inv_c);
         } else {               // pressure condition: rho_a = rho0 + p_w/RT, u_a = u_c
             dra = wall_drho<T>(p, cf, wid);
             // m_a = rho0 u_c / c = m_c, or rho_a u_c / c = m_c rho_a / rho_c (original model)
-            const T sc = p.model == 1 ? (cf.rho0 + dra) * irc : T(1);
+            const T sc = orig ? (cf.rho0 + dra) * irc : T(1);
             ma[0] = mc[0] * sc; ma[1] = mc[1] * sc; ma[2] = mc[2] * sc;
         }
-        const T ira = p.model == 1 ? rcp_rn(cf.rho0 + dra) : cf.inv_rho0;
+        const T ira = orig ? rcp_rn(cf.rho0 + dra) : cf.inv_rho0;
         const T mma = dotD<D, T>(ma, ma);
         const T mmc = dotD<D, T>(mc, mc);
         const int sgn = side == 0 ? -1 : 1;
@@ -175,7 +177,7 @@ __device__ __forceinline__ void interface_f(const StepParams &p, const Coef<T> &
     // Step 6: interface moments (weight h/2 on G). Step 7: original distribution.
     T drb, mb[3];
     moments<Q, T>(F, Gh, cf.wface * cf.rho0, drb, mb);
-    const T irb = original_model(p, cf, Gh, cf.wface, drb, mb);
+    const T irb = original_model<T, ORIG>(p, cf, Gh, cf.wface, drb, mb);
     T t[Q];
     relax<Q, T>(F, drb, mb, Gh, cf.rho0, irb, cf.b7, cf.c7, t);
     sfor<Q>([&](auto kc) {

@@ -283,8 +283,8 @@ __device__ __forceinline__ void step2d_tile(const StepParams &p, unsigned char *
             else rec(row + sh, lane, Fc);
             if (FORCE) faceG(d, d == 0 ? gfd + sh : fx, d == 1 ? gfd + sh : fy, Gc);
         }
-        if (d == 0) interface_f<Q, 0, float>(p, cf, F, Gb, wall, gfd == 0 ? 0 : 1, Fc, Gc, out);
-        else interface_f<Q, 1, float>(p, cf, F, Gb, wall, gfd == 0 ? 0 : 1, Fc, Gc, out);
+        if (d == 0) interface_f<Q, 0, float, false>(p, cf, F, Gb, wall, gfd == 0 ? 0 : 1, Fc, Gc, out);
+        else interface_f<Q, 1, float, false>(p, cf, F, Gb, wall, gfd == 0 ? 0 : 1, Fc, Gc, out);
     };
 
     // central differences along t of the own cell: per velocity (diagonals only) and of

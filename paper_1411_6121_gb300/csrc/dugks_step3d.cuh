@@ -498,9 +498,9 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
             else rec(row, lane, gfd == 0 ? 0 : nz - 2, Fc);
             if (FORCE) faceG(d, d == 0 ? gfd + sh : fx, d == 1 ? gfd + sh : fy, d == 2 ? gfd + sh : fz, Gc);
         }
-        if (d == 0) interface_f<Q, 0, float>(p, cf, F, Gb, wall, gfd == 0 ? 0 : 1, Fc, Gc, out);
-        else if (d == 1) interface_f<Q, 1, float>(p, cf, F, Gb, wall, gfd == 0 ? 0 : 1, Fc, Gc, out);
-        else interface_f<Q, 2, float>(p, cf, F, Gb, wall, gfd == 0 ? 0 : 1, Fc, Gc, out);
+        if (d == 0) interface_f<Q, 0, float, false>(p, cf, F, Gb, wall, gfd == 0 ? 0 : 1, Fc, Gc, out);
+        else if (d == 1) interface_f<Q, 1, float, false>(p, cf, F, Gb, wall, gfd == 0 ? 0 : 1, Fc, Gc, out);
+        else interface_f<Q, 2, float, false>(p, cf, F, Gb, wall, gfd == 0 ? 0 : 1, Fc, Gc, out);
     };
 
     // per-velocity central differences of the own column at plane pz along t (edge
