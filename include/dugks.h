@@ -254,9 +254,10 @@ int dugks_batch_init(dugks_batch_t b, int32_t i, const double *p, const double *
 int dugks_batch_step(dugks_batch_t b, int64_t n);
 /* Moments of instance i: [3][ncell_i] floats (p, u_x, u_y); synchronous. */
 int dugks_batch_moments(dugks_batch_t b, int32_t i, float *out, int32_t out_is_device);
-/* Autotuner: times each built tile shape on a copy of the batch state (the state and clock
- * are restored), keeps the fastest and caches the choice per (instance sizes, storage, SM
- * count) for the process. Writes the chosen tile to tile_x/tile_y (may be NULL). */
+/* Autotuner: times each built tile shape (best of three interleaved 16-step trials) on a copy
+ * of the batch state (the state and clock are restored), keeps the fastest and caches the
+ * choice per (instance sizes, storage, SM count) for the process. Writes the chosen tile to
+ * tile_x/tile_y (may be NULL). */
 int dugks_batch_tune(dugks_batch_t b, int32_t *tile_x, int32_t *tile_y);
 int dugks_batch_sync(dugks_batch_t b);
 int64_t dugks_batch_launch_count(dugks_batch_t b);
