@@ -69,7 +69,7 @@ def hbm_peak():
 
 def kernel_source_hash():
     h = hashlib.sha1()
-    for name in ("dugks_step3d.cuh", "dugks_device.cuh", "step3d_q19.cu"):
+    for name in ("dugks_step3d.cuh", "dugks_step.cuh", "dugks_device.cuh", "step3d_q19.cu"):
         with open(os.path.join(ROOT, "paper_1411_6121_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]

@@ -119,7 +119,6 @@ template <int Q, int d, class T, bool ORIG = true>
 __device__ __forceinline__ void interface_f(const StepParams &p, const Coef<T> &cf, T F[Q], const T Gh[3], int wall,
                                             int side, const T *Fc, const T Ghc[3], T *out) {
     constexpr int D = Lat<Q>::D;
-    const bool orig = ORIG && p.model == 1;
     if (wall && p.bc[2 * d + side] == 3) {
         // Step 5, eq. BB: F_k = F_-k + 2 rho0 W_k xi_k.u_w / RT for xi . n < 0, i.e.
         // g_k = g_-k + 6 W_k e_k.m_w with m_w = rho0 u_w / c (deviations: W_k = W_-k)
@@ -153,17 +152,17 @@ __device__ __forceinline__ void interface_f(const StepParams &p, const Coef<T> &
         if (p.bc[wid] == 1) {  // velocity condition: u_a = u_w, rho_a = rho_c
             dra = drc;
             // m = rho u / c: rho0 u_w / c, or rho_a u_w / c in the original model
-            const double ra = orig ? p.rho0 + (double)drc : p.rho0;
+            const double ra = (ORIG && p.model == 1) ? p.rho0 + (double)drc : p.rho0;
             ma[0] = (T)(p.bc_u[wid][0] * ra * p.inv_c);
             ma[1] = (T)(p.bc_u[wid][1] * ra * p.inv_c);
             ma[2] = (T)(p.bc_u[wid][2] * ra * p.inv_c);
         } else {               // pressure condition: rho_a = rho0 + p_w/RT, u_a = u_c
             dra = wall_drho<T>(p, cf, wid);
             // m_a = rho0 u_c / c = m_c, or rho_a u_c / c = m_c rho_a / rho_c (original model)
-            const T sc = orig ? (cf.rho0 + dra) * irc : T(1);
+            const T sc = (ORIG && p.model == 1) ? (cf.rho0 + dra) * irc : T(1);
             ma[0] = mc[0] * sc; ma[1] = mc[1] * sc; ma[2] = mc[2] * sc;
         }
-        const T ira = orig ? rcp_rn(cf.rho0 + dra) : cf.inv_rho0;
+        const T ira = (ORIG && p.model == 1) ? rcp_rn(cf.rho0 + dra) : cf.inv_rho0;
         const T mma = dotD<D, T>(ma, ma);
         const T mmc = dotD<D, T>(mc, mc);
         const int sgn = side == 0 ? -1 : 1;
@@ -202,7 +201,7 @@ __device__ __forceinline__ void cell_G(const StepParams &p, int64_t cell, int64_
 
 // One tile of the fused step: cells [x0, x0+TX) x [y0, y0+TY) x [z0, z1) of the instance
 // described by p, with the CTA's TX*TY threads and its dynamic shared memory.
-template <int Q, class S, int TX, int TY, bool NU = false>
+template <int Q, class S, int TX, int TY, bool NU = false, bool ORIG = true>
 __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, int z0, int z1,
                                           unsigned char *smem_raw) {
     using T = typename Arith<S>::T;
@@ -272,7 +271,7 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
             T Gh[3], drho, m[3];
             cell_G<D, T>(p, cell, ncell, ct, Gh);
             moments<Q, T>(g, Gh, cf.wcell * cf.rho0, drho, m);
-            const T ir = original_model(p, cf, Gh, cf.wcell, drho, m);
+            const T ir = original_model<T, ORIG>(p, cf, Gh, cf.wcell, drho, m);
             relax<Q, T>(g, drho, m, Gh, cf.rho0, ir, cf.b1, cf.c1, out);
         }
         // Step 2 (reading: linear extrapolation ghost = 2 f0 - f1, axis by axis).
@@ -381,7 +380,7 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
                                   cellp(cR, ly + 2, lx + 1), cf.kappa, Fc);
                 face_G(2, gx, gy, 0, gfz == 0 ? 1 : nz - 1, Gc);
             }
-            interface_f<Q, 2, T>(p, cf, F, Gb, wall, gfz == 0 ? 0 : 1, Fc, Gc, out);
+            interface_f<Q, 2, T, ORIG>(p, cf, F, Gb, wall, gfz == 0 ? 0 : 1, Fc, Gc, out);
         }
     };
 
@@ -442,7 +441,7 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
                                          cellp(sp, fy + 1, cx + 1), cf.kappa, Fc);
                 face_G(0, gfx, gy, kz, gcx, Gc);
             }
-            interface_f<Q, 0, T>(p, cf, F, Gb, wall, gfx == 0 ? 0 : 1, Fc, Gc, xf + (fy * (TX + 1) + fx) * K::SX);
+            interface_f<Q, 0, T, ORIG>(p, cf, F, Gb, wall, gfx == 0 ? 0 : 1, Fc, Gc, xf + (fy * (TX + 1) + fx) * K::SX);
         }
         // ---- y interfaces of plane kz ----
         for (int f = tid; f < TX * (TY + 1); f += NT) {
@@ -478,7 +477,7 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
                                          cellp(sp, cy + 1, fx + 1), cf.kappa, Fc);
                 face_G(1, gx, gcy, kz, gcy, Gc);
             }
-            interface_f<Q, 1, T>(p, cf, F, Gb, wall, gfy == 0 ? 0 : 1, Fc, Gc, yf + (fy * TX + fx) * K::SY);
+            interface_f<Q, 1, T, ORIG>(p, cf, F, Gb, wall, gfy == 0 ? 0 : 1, Fc, Gc, yf + (fy * TX + fx) * K::SY);
         }
         // ---- z interface kz+1/2 of the own column ----
         if constexpr (D == 3) zface(kz, kz + 1, zf_hi);
