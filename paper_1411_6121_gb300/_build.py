@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdugks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-         "-I" + INCLUDE, "-I" + CSRC]
+         "-I" + INCLUDE, "-I" + CSRC, "-Xptxas", "-v"]
 
 
 def nvcc():
@@ -56,8 +56,9 @@ def build(force=False, verbose=False, extra_flags=()):
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))
-        if verbose and r.stderr.strip():
-            print(r.stderr, flush=True)
+        # ptxas's resource report (registers, spills, shared memory per kernel)
+        with open(obj[:-2] + ".ptxas.txt", "w") as f:
+            f.write(r.stderr)
         return obj
 
     srcs = sources()
@@ -72,6 +73,32 @@ def build(force=False, verbose=False, extra_flags=()):
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
     os.replace(tmp, LIB)
     return LIB
+
+
+def resources():
+    """Per-kernel resources from the last build's ptxas reports: {mangled name: {"regs": R,
+    "spill_stores": B, "spill_loads": B}} (entry functions only)."""
+    import re
+    out = {}
+    for path in sorted(glob.glob(os.path.join(BUILD, "*.ptxas.txt"))):
+        entry = props = None
+        for line in open(path):
+            m = re.search(r"Compiling entry function '(\S+)'", line)
+            if m:
+                entry = m.group(1)
+                continue
+            m = re.search(r"Function properties for (\S+)", line)
+            if m:
+                props = m.group(1)
+                continue
+            m = re.search(r"(\d+) bytes spill stores, (\d+) bytes spill loads", line)
+            if m and entry and props == entry:
+                out.setdefault(entry, {})["spill_stores"] = int(m.group(1))
+                out[entry]["spill_loads"] = int(m.group(2))
+            m = re.search(r"Used (\d+) registers", line)
+            if m and entry:
+                out.setdefault(entry, {})["regs"] = int(m.group(1))
+    return out
 
 
 if __name__ == "__main__":

@@ -1,0 +1,42 @@
+"""Register and spill budgets of the hot kernels, read from ptxas's resource report of the
+sm_103a build (no GPU needed). Each budget is what a measured speed depends on:
+  * the D3Q19 throughput kernel runs one 256-thread CTA per SM at <= 255 registers and must not
+    spill (its z march keeps the carried differences in registers);
+  * the batch's FP32 reference tiles run 4 CTAs of 256 threads (8 of 128) per SM only at
+    <= 64 registers; 72 registers cost the 64-channel batch 15%;
+  * the D2Q9 throughput kernel (FP32) must not spill.
+A change that breaks one of them shows here before any GPU run."""
+import pytest
+
+from paper_1411_6121_gb300 import _build
+
+
+@pytest.fixture(scope="module")
+def res():
+    _build.build()
+    r = _build.resources()
+    if not r:
+        pytest.skip("no ptxas reports in the build folder")
+    return r
+
+
+def _find(res, *parts):
+    hits = {k: v for k, v in res.items() if all(p in k for p in parts)}
+    assert hits, parts
+    return hits
+
+
+def test_d3q19_throughput_kernel_does_not_spill(res):
+    # fused_step3d<19, S, 8, FORCE> for S = float, bfloat16, half
+    for k, v in _find(res, "fused_step3dILi19E", "Li8ELb").items():
+        assert v["regs"] <= 255 and v["spill_stores"] == 0, (k, v)
+
+
+def test_batch_fp32_tiles_fit_four_ctas_per_sm(res):
+    for k, v in _find(res, "fused_step_batchILi9Ef").items():
+        assert v["regs"] <= 64 and v["spill_stores"] == 0, (k, v)
+
+
+def test_d2q9_throughput_kernel_fp32_does_not_spill(res):
+    for k, v in _find(res, "fused_step2dIf").items():
+        assert v["spill_stores"] == 0, (k, v)
