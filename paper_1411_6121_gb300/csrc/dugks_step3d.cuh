@@ -553,9 +553,12 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
     for (int i = 0; i < NF; i++) alz[i] = fzm[i] = 0.0f;
 #pragma unroll
     for (int i = 0; i < 4; i++) Az[i] = 0.0f;
-    // carried too, by the rows that own x interfaces: the x and y differences of the current
-    // plane (per velocity and of the moments), formed with the z parts of the previous
-    // iteration and used again by the x and y parts of this one
+    // carried too (D3Q19), by the rows that own x interfaces: the x and y differences of the
+    // current plane (per velocity and of the moments), formed with the z parts of the previous
+    // iteration and used again by the x and y parts of this one. With 27 velocities carrying
+    // them costs more registers than recomputing them (the kernel would spill), so there they
+    // are formed again where they are used.
+    constexpr bool CARRY = Q == 19;
     const bool xrow = row >= 1 && row <= K::TYI;  // warp-uniform
     float cAX[Q], cAY[Q], mAX[4], mAY[4];
     if (xrow) {
@@ -598,6 +601,10 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
         for (int i = 0; i < NF; i++) fxp[i] = 0.0f;
         if (xrow) {  // halo rows own no x interface
             float alx[NF], bex[NF], Ax[4], Bx[4];
+            if constexpr (!CARRY) {
+                cdiff(kz, AY, cAY);
+                mdiff(kz, AY, mAY);
+            }
             face_parts<Q, 0>(cur, cur + Q, cAY, Cz, mAY, dz, cf.kappa, alx, bex, Ax, Bx);
             float F[NF], jb[3];
 #pragma unroll
@@ -636,7 +643,7 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
         float aly[NF], Ay[4];
         if (ycol) {
             float bey[NF], By[4], Cx[Q], dx[4];
-            if (xrow) {
+            if (CARRY && xrow) {
 #pragma unroll
                 for (int k = 0; k < Q; k++) Cx[k] = cAX[k];
 #pragma unroll
