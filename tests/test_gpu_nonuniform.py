@@ -104,3 +104,36 @@ def test_nonuniform_couette_exact_on_gpu():
     yc = 0.5 * (yf[1:] + yf[:-1])
     u = s.moments()[1].reshape(ny, 8)[:, 0].astype(np.float64)
     assert np.abs(u - 0.05 * yc / ny).max() < 1e-7  # moments are FP32 output
+
+
+@pytest.mark.parametrize("store", [0, 3])
+def test_nonuniform_original_model(store):
+    """The original DUGKS (eq. feq) on the tanh mesh: the model switch and the mesh metrics
+    together, against the oracle with both."""
+    case = CASES["cavity"]
+    cfg = dict(q=9, nu=0.04, dt=_dt(case["faces"]), **case)
+    p, u = W.random_state_fields(cfg["shape"], seed=77, u_amp=0.08, p_amp=3e-3)
+    o = Oracle(model=1, **cfg)
+    o.init(p=p, u=u)
+    o.step(15)
+    s = _sim(store=store, model=1, **cfg)
+    s.init(p=p, u=u)
+    s.step(15)
+    ref = state_dev(o)
+    tol = 1e-11 if store == 3 else 2e-6
+    assert np.abs(s.get_state().astype(np.float64) - ref).max() < tol * np.abs(ref).max()
+    # the incompressible model gives a different state on the same input (about 1%)
+    o0 = Oracle(**cfg)
+    o0.init(p=p, u=u)
+    o0.step(15)
+    assert np.abs(state_dev(o0) - ref).max() > 100 * tol * np.abs(ref).max()
+
+
+def test_nonuniform_handle_has_no_adjoint():
+    from paper_1411_6121_gb300 import dugks
+    case = CASES["channel"]
+    s = _sim(q=9, nu=0.04, dt=_dt(case["faces"]), **case)
+    s.init()
+    with pytest.raises(dugks.DugksError) as e:
+        s.record(10, 5)
+    assert e.value.code == -7 and "uniform meshes only" in str(e.value)  # DUGKS_E_UNSUPPORTED
