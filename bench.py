@@ -307,7 +307,9 @@ def run_adjoint(torch, dev, count=64):
     every 100 steps; gradient w.r.t. the per-cell acceleration field through dugks_record +
     dugks_adjoint_async. Each instance runs on its own CUDA stream; the reverse sweeps of all
     instances are enqueued back to back and run concurrently, timed with CUDA events on a
-    stream that waits for all of them."""
+    stream that waits for all of them. The whole forward + reverse pass runs twice: the first
+    captures each instance's segment graphs, the second (reported) replays them, as repeated
+    gradient evaluations do."""
     import numpy as np
     from paper_1411_6121_gb300 import dugks
     from paper_1411_6121_gb300 import workloads as W
@@ -326,49 +328,54 @@ def run_adjoint(torch, dev, count=64):
         sims.append(sim)
         streams.append(st)
         cells_total += n
-    # warm-up of the code paths on the first instance
-    sims[0].init()
-    sims[0].record(2 * ADJ_EVERY, ADJ_EVERY)
-    sims[0].adjoint(torch.zeros((3, specs[0]["shape"][0] * specs[0]["shape"][1]), dtype=torch.float32, device=dev))
     master = torch.cuda.Stream(device=dev)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    torch.cuda.synchronize(dev)
-    l0 = sum(s.launch_count() for s in sims)
-    # forward rollouts with checkpoints, all instances
-    ev[0].record(master)
-    for sim, st in zip(sims, streams):
-        st.wait_event(ev[0])
-        sim.init()
-        sim.record(ADJ_STEPS, ADJ_EVERY)
-    for st in streams:
-        master.wait_stream(st)
-    ev[1].record(master)
-    torch.cuda.synchronize(dev)
-    for sim, sp in zip(sims, specs):
-        nx, ny = sp["shape"]
-        m = torch.empty((3, nx * ny), dtype=torch.float32, device=dev)
-        sim.moments(m)
-        yc = np.repeat(np.arange(ny) + 0.5, nx)
-        ut = torch.zeros((2, nx * ny), dtype=torch.float32, device=dev)
-        ut[0] = torch.tensor(1.1 * sp["g"][0] * yc * (ny - yc) / (2.0 * sp["nu"]), dtype=torch.float32, device=dev)
-        seed = torch.zeros_like(m)
-        seed[1:] = 2.0 * (m[1:] - ut)
-        seeds.append(seed)
-    torch.cuda.synchronize(dev)
-    # reverse sweeps of all instances, enqueued on their own streams and run concurrently
     grads = [torch.empty((2, sp["shape"][0] * sp["shape"][1]), dtype=torch.float32, device=dev) for sp in specs]
-    ev[2].record(master)
-    for st in streams:
-        st.wait_event(ev[2])
-    for sim, seed, gr in zip(sims, seeds, grads):
-        sim.adjoint_async(seed, dfield=gr)
-    for st in streams:
-        master.wait_stream(st)
-    ev[3].record(master)
-    torch.cuda.synchronize(dev)
-    for sim in sims:
-        sim.sync()
-    fwd_ms, bwd_ms = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+
+    def sweep():
+        """Forward rollouts with checkpoints of all instances, then their reverse sweeps,
+        each instance on its own stream; returns the two device times (ms)."""
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        torch.cuda.synchronize(dev)
+        ev[0].record(master)
+        for sim, st in zip(sims, streams):
+            st.wait_event(ev[0])
+            sim.init()
+            sim.record(ADJ_STEPS, ADJ_EVERY)
+        for st in streams:
+            master.wait_stream(st)
+        ev[1].record(master)
+        torch.cuda.synchronize(dev)
+        seeds.clear()
+        for sim, sp in zip(sims, specs):
+            nx, ny = sp["shape"]
+            m = torch.empty((3, nx * ny), dtype=torch.float32, device=dev)
+            sim.moments(m)
+            yc = np.repeat(np.arange(ny) + 0.5, nx)
+            ut = torch.zeros((2, nx * ny), dtype=torch.float32, device=dev)
+            ut[0] = torch.tensor(1.1 * sp["g"][0] * yc * (ny - yc) / (2.0 * sp["nu"]), dtype=torch.float32,
+                                 device=dev)
+            seed = torch.zeros_like(m)
+            seed[1:] = 2.0 * (m[1:] - ut)
+            seeds.append(seed)
+        torch.cuda.synchronize(dev)
+        ev[2].record(master)
+        for st in streams:
+            st.wait_event(ev[2])
+        for sim, seed, gr in zip(sims, seeds, grads):
+            sim.adjoint_async(seed, dfield=gr)
+        for st in streams:
+            master.wait_stream(st)
+        ev[3].record(master)
+        torch.cuda.synchronize(dev)
+        for sim in sims:
+            sim.sync()
+        return ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+
+    # the first sweep captures each instance's segment graphs (the library keeps them while
+    # the buffers and parameters are unchanged); the second is the reported, repeated use
+    _, cold_bwd_ms = sweep()
+    l0 = sum(s.launch_count() for s in sims)
+    fwd_ms, bwd_ms = sweep()
     launches = sum(s.launch_count() for s in sims) - l0
     # the largest instance alone (kernel-level figure at 132 algorithmic bytes per update)
     big = max(range(len(specs)), key=lambda k: specs[k]["shape"][0] * specs[k]["shape"][1])
@@ -390,7 +397,9 @@ def run_adjoint(torch, dev, count=64):
     return {"value": upd / (bwd_ms * 1e-3) / 1e6, "unit": "MLUPS",
             "forward_with_checkpoints_mlups": upd / (fwd_ms * 1e-3) / 1e6,
             "forward_plus_adjoint_mlups": upd / ((fwd_ms + bwd_ms) * 1e-3) / 1e6,
-            "reverse_ms": bwd_ms, "forward_ms": fwd_ms, "instances": len(specs), "cells": cells_total,
+            "reverse_ms": bwd_ms, "forward_ms": fwd_ms,
+            "first_sweep_reverse_mlups": upd / (cold_bwd_ms * 1e-3) / 1e6,
+            "instances": len(specs), "cells": cells_total,
             "steps": ADJ_STEPS, "checkpoint_every": ADJ_EVERY, "dtype": "f32", "gpu_launches": launches,
             "largest_instance": {"shape": list(specs[big]["shape"]), "adjoint_mlups": big_mlups,
                                  "bytes_per_cell_update": ADJ_BYTES,
@@ -398,7 +407,9 @@ def run_adjoint(torch, dev, count=64):
                                               "peak": peak, "unit": "GB/s",
                                               "frac": ADJ_BYTES * big_mlups * 1e6 / 1e9 / peak}},
             "note": "reverse sweep = recompute of each 100-step segment from its checkpoint + 2000 "
-                    "transposed steps, per instance on its own stream, all instances concurrently"}
+                    "transposed steps, per instance on its own stream, all instances concurrently; "
+                    "second forward + reverse pass (the first captures the segment graphs, "
+                    "first_sweep_reverse_mlups)"}
 
 
 def run_case(torch, case, size, steps, warmup, dev):

@@ -220,7 +220,11 @@ void dugks_destroy(dugks_t h);
  * The acceleration, wall velocities and viscosity must be those of the recorded rollout.
  * Synchronous. DUGKS_E_UNSUPPORTED for 3D lattices or BF16/F16 storage; DUGKS_E_INVAL
  * without a recorded rollout. Memory: (ceil(nsteps/every) + every) x the state size plus
- * about 7 state sizes of work buffers. */
+ * about 7 state sizes of work buffers. With use_graph, a time-independent acceleration and
+ * at least 3 segments, each segment's work is captured once as a CUDA graph and kept by the
+ * handle across calls (and across records of the same length) while the buffers and
+ * parameters it was captured with are unchanged; a later call with any of them changed
+ * captures again. */
 int dugks_record(dugks_t h, int64_t nsteps, int32_t every);
 int dugks_adjoint(dugks_t h, const float *dL_dmom, float *dL_dfield, double *dL_dwall, void *dL_dstate0);
 /* Asynchronous form of dugks_adjoint for running the reverse sweeps of several handles

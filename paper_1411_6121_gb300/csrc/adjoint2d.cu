@@ -966,11 +966,26 @@ int enqueue_adjoint(dugks_t h, const float *dL_dmom, float *dL_dfield, void *dL_
     // parity is the same sequence of launches on the same buffers: capture it once as a
     // CUDA graph and replay it per segment.
     const bool graphs = h->use_graph && h->force.omega == 0.0 && nseg >= 3;
-    // graphs of the previous call (its work has completed: the caller synchronised the
-    // handle's stream before this call)
-    for (cudaGraphExec_t g : t.graphs) cudaGraphExecDestroy(g);
-    t.graphs.clear();
-    std::map<std::pair<int64_t, int>, std::pair<cudaGraphExec_t, int64_t>> cache;  // graph, its launches
+    // What a captured segment bakes in besides its length and parity: the forward step's and
+    // the adjoint's parameter records (with omega = 0 neither depends on the segment's
+    // time), the segment state buffers and the kernel selection. A graph of an earlier call
+    // is reused while all of these are unchanged (its work has completed: the caller's
+    // stream was synchronised before this call).
+    std::vector<unsigned char> sig;
+    if (graphs) {
+        StepParams p0 = handle_params(h);
+        p0.src = p0.dst = nullptr;
+        p0.step_ctr = t.zero;
+        auto put = [&](const void *q, size_t n) {
+            const unsigned char *c = (const unsigned char *)q;
+            sig.insert(sig.end(), c, c + n);
+        };
+        put(&p0, sizeof p0);
+        put(&a, sizeof a);
+        const int sel[4] = {h->kernel, h->tile_x, h->tile_y, h->store};
+        put(sel, sizeof sel);
+        for (void *q : t.seg) put(&q, sizeof q);
+    }
     int rc = DUGKS_OK;
     for (int64_t sg = nseg - 1; sg >= 0 && rc == DUGKS_OK; sg--) {
         const int64_t start = sg * every;
@@ -979,9 +994,16 @@ int enqueue_adjoint(dugks_t h, const float *dL_dmom, float *dL_dfield, void *dL_
         if (e != cudaSuccess) { rc = handle_fail(h, DUGKS_E_CUDA, "adjoint: %s", cudaGetErrorString(e)); break; }
         int64_t nl = 0;
         if (graphs) {
-            const auto key = std::make_pair(len, cur);
-            auto it = cache.find(key);
-            if (it == cache.end()) {
+            AdjointTape::SegGraph *hit = nullptr;
+            for (auto &gr : t.graphs)
+                if (gr.len == len && gr.cur == cur) hit = &gr;
+            if (hit && hit->sig != sig) {  // captured with other buffers or parameters
+                cudaGraphExecDestroy(hit->exec);
+                *hit = t.graphs.back();
+                t.graphs.pop_back();
+                hit = nullptr;
+            }
+            if (!hit) {
                 cudaGraph_t g;
                 e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
                 if (e == cudaSuccess) {
@@ -995,11 +1017,11 @@ int enqueue_adjoint(dugks_t h, const float *dL_dmom, float *dL_dfield, void *dL_
                     cudaGraphDestroy(g);
                 }
                 if (e != cudaSuccess) { rc = handle_fail(h, DUGKS_E_CUDA, "adjoint graph: %s", cudaGetErrorString(e)); break; }
-                it = cache.emplace(key, std::make_pair(ge, nl)).first;
-                t.graphs.push_back(ge);
+                t.graphs.push_back(AdjointTape::SegGraph{len, cur, sig, ge, nl});
+                hit = &t.graphs.back();
             }
-            nl = it->second.second;
-            e = cudaGraphLaunch(it->second.first, st);
+            nl = hit->launches;
+            e = cudaGraphLaunch(hit->exec, st);
         } else {
             e = enqueue_segment<T>(h, a, B, start, len, cur, &nl);
         }
@@ -1043,7 +1065,7 @@ void adjoint_release(dugks_t h) {
     cudaFree(t.zero);
     cudaFree(t.dW_face);
     if (t.h_wall) cudaFreeHost(t.h_wall);
-    for (cudaGraphExec_t g : t.graphs) cudaGraphExecDestroy(g);
+    for (auto &gr : t.graphs) cudaGraphExecDestroy(gr.exec);
     t.graphs.clear();
     t.scratch = nullptr;
     t.dG = t.dW = t.dW_face = t.h_wall = nullptr;

@@ -26,7 +26,18 @@ struct AdjointTape {
     long long *zero = nullptr;   // device counter fixed at 0 (recompute clock)
     double *dW_face = nullptr;   // [6][3] dL/du_w per face (device), reduced in fixed order
     double *h_wall = nullptr;    // [6][3] pinned copy of dW_face
-    std::vector<cudaGraphExec_t> graphs;  // reverse-sweep graphs of the last adjoint call
+    // Captured reverse-sweep segments, kept across calls: one per (segment length, lambda
+    // parity), valid while every pointer and value that the capture baked in is unchanged
+    // (sig holds them: the step and adjoint parameter records, the segment buffers, the
+    // kernel and tile selection).
+    struct SegGraph {
+        int64_t len;
+        int cur;
+        std::vector<unsigned char> sig;
+        cudaGraphExec_t exec;
+        int64_t launches;
+    };
+    std::vector<SegGraph> graphs;
 };
 
 }  // namespace dugks

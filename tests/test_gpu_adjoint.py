@@ -313,3 +313,37 @@ def test_async_adjoint_on_two_streams_matches_sync():
         s.sync()
         assert torch.equal(o, dref)
         assert np.array_equal(s.adjoint_wall(), wref)
+
+
+def test_segment_graphs_reused_only_while_valid():
+    """Segment graphs survive across adjoint calls and records of the same length. A second
+    record + adjoint on the same handle, and one after the acceleration field was replaced
+    (a new pointer baked into the old graphs), give bitwise the results of fresh handles."""
+    torch = _torch()
+    from paper_1411_6121_gb300 import dugks
+    cfg = dict(CASES["channel_wide"], omega=0.0)  # graphs need a time-independent force
+    p, u, field, w = _inputs(cfg, seed=17)
+    tf = torch.tensor(field, dtype=torch.float32, device="cuda")
+    tf2 = torch.tensor(1.5 * field, dtype=torch.float32, device="cuda")
+    wt = torch.tensor(w, dtype=torch.float32, device="cuda")
+
+    def fresh(fld):
+        s = dugks.Sim(field=fld, store=0, **cfg)
+        s.init(p=p, u=u)
+        s.record(40, 7)  # 6 segments: captured as graphs
+        return s.adjoint(wt)
+
+    d1, w1, _ = fresh(tf)
+    d2, w2, _ = fresh(tf2)
+    s = dugks.Sim(field=tf, store=0, **cfg)
+    for _ in range(2):  # the second pass replays the graphs of the first
+        s.init(p=p, u=u)
+        s.record(40, 7)
+        d, wg, _ = s.adjoint(wt)
+        assert torch.equal(d, d1) and np.array_equal(wg, w1)
+    s.set_force_field(tf2)
+    s.init(p=p, u=u)
+    s.record(40, 7)
+    d, wg, _ = s.adjoint(wt)
+    assert torch.equal(d, d2) and np.array_equal(wg, w2)
+    assert not torch.equal(d1, d2)
