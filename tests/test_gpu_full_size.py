@@ -1,0 +1,85 @@
+"""Parity at the benchmark's full size: the D3Q19 lid-driven cube of 256^3 cells, FP32
+storage, the throughput kernel in the launch configuration the benchmark times. The oracle
+cannot step 16.8 M cells, but one step of a cell depends only on cells at most two away
+(interface reconstruction with tangential cross points, the wall ghosts and x_c). So the test
+takes the GPU's state after a few steps and runs ONE oracle step on sampled windows of it:
+  * windows at the domain's corners, edges, faces (with the true walls there) and inside;
+  * on a window side that is not a domain boundary the oracle sees an artificial rest wall
+    (or a periodic seam), so only cells at least three away from such sides are compared;
+and compares those cells with the GPU's next state, element by element."""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_1411_6121_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+N = 256
+WIN = 11          # window edge (cells)
+MARGIN = 3        # cells compared are at least this far from an artificial window side
+
+
+def _window_bcs(lo, true_bcs):
+    """Boundary faces of a window starting at lo (per axis): the cube's own face where the
+    window touches it, a rest wall on the other side of that axis, periodic otherwise."""
+    bcs = []
+    for a in range(3):
+        at_lo, at_hi = lo[a] == 0, lo[a] + WIN == N
+        if at_lo:
+            bcs += [true_bcs[2 * a], W.wall()]
+        elif at_hi:
+            bcs += [W.wall(), true_bcs[2 * a + 1]]
+        else:
+            bcs += [W.periodic(), W.periodic()]
+    return bcs
+
+
+def _compared(lo):
+    """Per axis, the window cells whose result does not depend on an artificial side."""
+    sl = []
+    for a in range(3):
+        if lo[a] == 0:
+            sl.append(slice(0, WIN - MARGIN))
+        elif lo[a] + WIN == N:
+            sl.append(slice(MARGIN, WIN))
+        else:
+            sl.append(slice(MARGIN, WIN - MARGIN))
+    return sl
+
+
+def test_d3q19_256_cube_sampled_windows():
+    from paper_1411_6121_gb300 import dugks
+    cfg = W.cavity3d(n=N, re=1000.0, lid_u=0.1, q=19)
+    s = dugks.Sim(store=dugks.STORE_F32, use_graph=False, **cfg)
+    p, u = W.random_state_fields(cfg["shape"], seed=256, u_amp=0.03, p_amp=1e-3)
+    s.init(p=p, u=u)
+    del p, u
+    s.step(3)
+    g0 = s.get_state().reshape(19, N, N, N)  # [Q][z][y][x]
+    s.step(1)
+    g1 = s.get_state().reshape(19, N, N, N)
+    o_tmp = Oracle((4, 4, 4), 19, nu=cfg["nu"], dt=cfg["dt"])
+    _, Wt = o_tmp.lattice()
+    E = N - WIN
+    rng = np.random.default_rng(7)
+    starts = [(0, 0, 0), (E, E, E), (0, E, 0), (E, 0, E),          # corners (E on y: the lid)
+              (E // 2, E, E // 2), (0, E // 3, E // 2),            # lid face, x wall
+              (E // 3, 0, E), (E // 2, E // 2, E // 2)]            # edge, interior
+    starts += [tuple(int(v) for v in rng.integers(1, E, 3)) for _ in range(2)]
+    for lo in starts:
+        zs, ys, xs = slice(lo[2], lo[2] + WIN), slice(lo[1], lo[1] + WIN), slice(lo[0], lo[0] + WIN)
+        win0 = g0[:, zs, ys, xs].astype(np.float64)
+        o = Oracle((WIN, WIN, WIN), 19, nu=cfg["nu"], dt=cfg["dt"], rt=cfg["rt"], rho0=cfg["rho0"],
+                   bcs=_window_bcs(lo, cfg["bcs"]))
+        o.set_state(win0.reshape(19, -1) + Wt[:, None] * cfg["rho0"], t=3 * cfg["dt"], step=3)
+        o.step(1)
+        ref = (o.get_state() - Wt[:, None] * cfg["rho0"]).reshape(19, WIN, WIN, WIN)
+        sx, sy, sz = _compared(lo)
+        r = ref[:, sz, sy, sx]
+        got = g1[:, zs, ys, xs][:, sz, sy, sx].astype(np.float64)
+        scale = np.abs(g1).max()
+        err = np.abs(got - r).max()
+        assert err < 2e-6 * scale, (lo, err, scale)
+        # the step changed these cells far beyond the tolerance (the check is not vacuous)
+        assert np.abs(r - win0[:, sz, sy, sx]).max() > 100 * 2e-6 * scale, lo
