@@ -1,8 +1,9 @@
 """Parity at the benchmark's full size: the lid-driven cube of 256^3 cells through the
 throughput kernel in the launch configuration the benchmark times, for each leg of the
 benchmark (D3Q19 with FP32, BF16 and FP16 storage, D3Q27 with FP32). The oracle
-cannot step 16.8 M cells, but one step of a cell depends only on cells at most two away
-(interface reconstruction with tangential cross points, the wall ghosts and x_c). So the test
+cannot step 16.8 M cells, but one step of a cell reads only its neighbours (interface
+reconstruction with tangential cross points; ghosts and x_c of a true wall lie inside a window
+touching it; pinned on the CPU in test_windows.py). So the test
 takes the GPU's state after a few steps and runs ONE oracle step on sampled windows of it:
   * windows at the domain's corners, edges, faces (with the true walls there) and inside;
   * on a window side that is not a domain boundary the oracle sees an artificial rest wall
@@ -16,37 +17,10 @@ from paper_1411_6121_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
+from tests.windows import compared, starts, window_bcs
+
 N = 256
 WIN = 11          # window edge (cells)
-MARGIN = 3        # cells compared are at least this far from an artificial window side
-
-
-def _window_bcs(lo, true_bcs):
-    """Boundary faces of a window starting at lo (per axis): the cube's own face where the
-    window touches it, a rest wall on the other side of that axis, periodic otherwise."""
-    bcs = []
-    for a in range(3):
-        at_lo, at_hi = lo[a] == 0, lo[a] + WIN == N
-        if at_lo:
-            bcs += [true_bcs[2 * a], W.wall()]
-        elif at_hi:
-            bcs += [W.wall(), true_bcs[2 * a + 1]]
-        else:
-            bcs += [W.periodic(), W.periodic()]
-    return bcs
-
-
-def _compared(lo):
-    """Per axis, the window cells whose result does not depend on an artificial side."""
-    sl = []
-    for a in range(3):
-        if lo[a] == 0:
-            sl.append(slice(0, WIN - MARGIN))
-        elif lo[a] + WIN == N:
-            sl.append(slice(MARGIN, WIN))
-        else:
-            sl.append(slice(MARGIN, WIN - MARGIN))
-    return sl
 
 
 def _decode(a, store):
@@ -79,21 +53,15 @@ def test_256_cube_sampled_windows(q, store, ulp):
     s.close()
     o_tmp = Oracle((4, 4, 4), q, nu=cfg["nu"], dt=cfg["dt"])
     _, Wt = o_tmp.lattice()
-    E = N - WIN
-    rng = np.random.default_rng(7)
-    starts = [(0, 0, 0), (E, E, E), (0, E, 0), (E, 0, E),          # corners (E on y: the lid)
-              (E // 2, E, E // 2), (0, E // 3, E // 2),            # lid face, x wall
-              (E // 3, 0, E), (E // 2, E // 2, E // 2)]            # edge, interior
-    starts += [tuple(int(v) for v in rng.integers(1, E, 3)) for _ in range(2)]
-    for lo in starts:
+    for lo in starts(N, WIN, np.random.default_rng(7)):
         zs, ys, xs = slice(lo[2], lo[2] + WIN), slice(lo[1], lo[1] + WIN), slice(lo[0], lo[0] + WIN)
         win0 = g0[:, zs, ys, xs]
         o = Oracle((WIN, WIN, WIN), q, nu=cfg["nu"], dt=cfg["dt"], rt=cfg["rt"], rho0=cfg["rho0"],
-                   bcs=_window_bcs(lo, cfg["bcs"]))
+                   bcs=window_bcs(lo, WIN, N, cfg["bcs"]))
         o.set_state(win0.reshape(q, -1) + Wt[:, None] * cfg["rho0"], t=3 * cfg["dt"], step=3)
         o.step(1)
         ref = (o.get_state() - Wt[:, None] * cfg["rho0"]).reshape(q, WIN, WIN, WIN)
-        sx, sy, sz = _compared(lo)
+        sx, sy, sz = compared(lo, WIN, N)
         r = ref[:, sz, sy, sx]
         got = g1[:, zs, ys, xs][:, sz, sy, sx]
         scale = np.abs(g1).max()
