@@ -14,10 +14,9 @@ import pytest
 
 from oracle import Oracle
 from paper_1411_6121_gb300 import workloads as W
+from tests.windows import compared, starts, window_bcs
 
 pytestmark = pytest.mark.gpu
-
-from tests.windows import compared, starts, window_bcs
 
 N = 256
 WIN = 11          # window edge (cells)
