@@ -96,3 +96,40 @@ def test_header_constants_match_binding():
     consts = dict((k, int(v)) for k, v in re.findall(r"#define DUGKS_(BC_[A-Z_]+|STORE_[A-Z0-9_]+)\s+(-?\d+)", src))
     for name, value in consts.items():
         assert getattr(dugks, name) == value, name
+
+
+def _batch_create(count=2, faces=None, store=0, model=0, dt=0.5, bc_type=None):
+    lib = dugks.load()
+    meshes = (dugks.Mesh * count)()
+    nus = (C.c_double * count)()
+    forces = (dugks.Force * count)()
+    bcs = (dugks.Boundaries * count)()
+    keep = []
+    for i in range(count):
+        meshes[i] = dugks.Mesh(2, 16, 8, 1, 1.0)
+        nus[i] = 0.05
+        bcs[i] = dugks.make_bcs([(0, (0, 0, 0), 0.0), (0, (0, 0, 0), 0.0),
+                                 (bc_type if bc_type is not None else 1, (0, 0, 0), 0.0), (1, (0.05, 0, 0), 0.0)])
+    if faces is not None:
+        keep.append(np.ascontiguousarray(faces, dtype=np.float64))
+        meshes[count - 1].faces[1] = keep[-1].ctypes.data_as(C.POINTER(C.c_double))
+    o = dugks.Opts()
+    lib.dugks_opts_default(C.byref(o))
+    o.store, o.model = store, model
+    h = C.c_void_p()
+    rc = lib.dugks_batch_create(count, meshes, C.cast(nus, C.POINTER(C.c_double)), dt, forces, bcs, C.byref(o),
+                                C.byref(h))
+    return rc, h, lib.dugks_batch_last_error(None).decode()
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(faces=np.linspace(0.0, 8.0, 9)), -7),   # graded meshes are not batched
+    (dict(model=1), -7),                           # the batch runs the incompressible model
+    (dict(store=3), -7),                           # F32/BF16/F16 storage only
+    (dict(dt=1.01), -2),                           # CFL
+    (dict(bc_type=0), -1),                         # a periodic face paired with a wall
+    (dict(count=0), -1),
+])
+def test_batch_arguments_rejected(kw, code):
+    rc, h, msg = _batch_create(**kw)
+    assert rc == code and not h.value and msg
