@@ -46,10 +46,17 @@
  *      corner velocities removed and the standard weights 1/3, 1/18, 1/36; it has the
  *      same moments up to fourth order, which is all eq. icfeq uses.
  *  R9  Pressure p = (rho - rho0) RT (the paper initialises rho = rho0 + p/RT).
+ *  R14 Bounce-back (Sec. 2.4, eq. BB) is applied, like NEQ, to fbar at the wall interface
+ *      in the Appendix's step 5: for xi_k . n < 0, fbar_k = fbar_(-k) + 2 rho_w W_k
+ *      xi_k . u_w / RT, with the opposite velocity's step-4 value at the same interface
+ *      and rho_w = rho0 (the incompressible limit the paper names).
  *  R16 The original DUGKS (the comparison model of Sec. 2.1 and 2.2, model = 1): eq. feq
  *      in place of eq. icfeq everywhere f_eq appears (step 1, the NEQ equilibria, step 7,
  *      the force term S, the initial state), with rho u = sum xi f~ + rho G dt/2 at cells
  *      and the same with h at interfaces; the incompressible model is model = 0.
+ *  R17 Oscillating wall pressure (the pressure-driven Womersley flow of Sec. 3.3): a
+ *      pressure wall holds p_w(t) = p + p_amp cos(omega t), with the force's omega, and the
+ *      NEQ pressure condition takes it at the interface time t_n + h.
  *  R18 Non-uniform mesh (Sec. 3.4, the tanh mesh): the mesh is given by its interface
  *      coordinates per axis; cell centres are the midpoints of their two interfaces. Step 3
  *      interpolates linearly in each axis between the two centres around the interface
@@ -59,10 +66,6 @@
  *      centre mirrored in the wall; periodic ghosts sit one period away), the interface G
  *      is interpolated like fbar+, and step 8 uses each cell's interface areas and volume.
  *      On a uniform mesh every one of these reduces to the uniform formula.
- *  R14 Bounce-back (Sec. 2.4, eq. BB) is applied, like NEQ, to fbar at the wall interface
- *      in the Appendix's step 5: for xi_k . n < 0, fbar_k = fbar_(-k) + 2 rho_w W_k
- *      xi_k . u_w / RT, with the opposite velocity's step-4 value at the same interface
- *      and rho_w = rho0 (the incompressible limit the paper names).
  *
  * Complex-step build: compiled with -DORACLE_COMPLEX_STEP the same code runs on
  * double _Complex values. The scheme only adds, subtracts and multiplies state values, so
