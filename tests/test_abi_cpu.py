@@ -133,3 +133,31 @@ def _batch_create(count=2, faces=None, store=0, model=0, dt=0.5, bc_type=None):
 def test_batch_arguments_rejected(kw, code):
     rc, h, msg = _batch_create(**kw)
     assert rc == code and not h.value and msg
+
+
+def test_product_package_never_imports_the_oracle():
+    """The oracle is test infrastructure: no module of the package imports it (the CUDA path
+    has no CPU fallback)."""
+    import ast
+    pkg = os.path.join(ROOT, "paper_1411_6121_gb300")
+    for name in sorted(os.listdir(pkg)):
+        if not name.endswith(".py"):
+            continue
+        tree = ast.parse(open(os.path.join(pkg, name)).read())
+        for node in ast.walk(tree):
+            if isinstance(node, ast.Import):
+                mods = [a.name for a in node.names]
+            elif isinstance(node, ast.ImportFrom):
+                mods = [node.module or ""]
+            else:
+                continue
+            assert not any(m == "oracle" or m.startswith("oracle.") for m in mods), (name, mods)
+
+
+def test_missing_library_fails_loudly():
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "-c",
+                        "from paper_1411_6121_gb300 import dugks; dugks.load('/nonexistent/libdugks.so')"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0 and "OSError" in r.stderr
