@@ -4,7 +4,7 @@ NumPy model of tests/fp32_model.py (D2Q9, deviation variables):
     validates it;
   * in plain FP32 it drifts by the amount the GPU kernels show (measured after 1000 steps:
     channel 4.9e-6 / 6.0e-6, cavity 3.2e-6 / 3.1e-6 for the two kernels), far above what one
-    FP32 rounding of the stored state per step costs (< 1e-7, test_oracle_fp32_storage.py);
+    FP32 rounding of the stored state per step costs (< 1e-7, test_oracle_storage_precision.py);
   * with the cell stage formed with one rounding at the scale of the equilibrium's odd term
     (compensated moments, exact e.m, one fused multiply-add), the all-FP32 model meets the
     1e-6 bar. This is the form the kernels' step 1 should take."""
