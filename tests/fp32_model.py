@@ -16,7 +16,9 @@ y (the channel), or NEQ walls on all four sides with a moving +y lid (the cavity
 `cell="one_rounding"` replaces the FP32 cell stage by a form with one rounding at the scale
 of the equilibrium's odd term: moments by compensated (two-sum) summation, e.m kept as an
 exact two-term sum, the small terms of W (q + 3 e.m) added first and a single fused
-multiply-add with 3W last, and the relaxation itself as one fused multiply-add."""
+multiply-add with 3W last, and the relaxation itself as one fused multiply-add.
+`cell="moments_only"` / `"equilibrium_only"` apply one half of it (the other half as in the
+kernels: plain sums; e.m rounded, then fma(e.m, 3, q) and W x)."""
 import numpy as np
 
 F32, F64 = np.float32, np.float64
@@ -86,19 +88,36 @@ _WH = WT.astype(F32)
 _WL = (WT - _WH.astype(F64)).astype(F32)
 
 
-def _cell_one_rounding(g, Gx, Gy, b1, c1, dt):
+def _nsum(terms):
+    """Plain left-to-right FP32 sum."""
+    s = np.zeros_like(terms[0])
+    for t in terms:
+        s = (s + t.astype(F32)).astype(F32)
+    return s
+
+
+def _cell_one_rounding(g, Gx, Gy, b1, c1, dt, compensated=True, one_rounding=True):
+    """The FP32 cell stage with compensated moments and/or the one-rounding equilibrium
+    (otherwise: plain sums, and e.m rounded, fma(e.m, 3, q) and W x as in the kernels)."""
     w = dt / 2
-    d = _csum([g[k] for k in range(9)])
-    mx = _csum([F32(E[k, 0]) * g[k] for k in range(9) if E[k, 0]] + [np.full_like(g[0], F32(w) * F32(Gx))])
-    my = _csum([F32(E[k, 1]) * g[k] for k in range(9) if E[k, 1]] + [np.full_like(g[0], F32(w) * F32(Gy))])
+    sm = _csum if compensated else _nsum
+    d = sm([g[k] for k in range(9)])
+    mx = sm([F32(E[k, 0]) * g[k] for k in range(9) if E[k, 0]] + [np.full_like(g[0], F32(w) * F32(Gx))])
+    my = sm([F32(E[k, 1]) * g[k] for k in range(9) if E[k, 1]] + [np.full_like(g[0], F32(w) * F32(Gy))])
     mm = _fma(mx, mx, (my * my).astype(F32))
     base = _fma(F32(-1.5), mm, d)                     # drho - 1.5 m.m (small)
     ge = np.empty_like(g)
     for k in range(9):
-        emh, eml = _two_sum((F32(E[k, 0]) * mx).astype(F32), (F32(E[k, 1]) * my).astype(F32))
-        q = _fma((F32(4.5) * emh).astype(F32), emh, base)  # even part (small)
-        small = (_WH[k] * q + _WL[k] * q + _W3L[k] * emh + _W3H[k] * eml).astype(F32)
-        ge[k] = _fma(_W3H[k], emh, small)                 # the one rounding at the odd term's scale
+        a, b = (F32(E[k, 0]) * mx).astype(F32), (F32(E[k, 1]) * my).astype(F32)
+        if one_rounding:
+            emh, eml = _two_sum(a, b)
+            q = _fma((F32(4.5) * emh).astype(F32), emh, base)  # even part (small)
+            small = (_WH[k] * q + _WL[k] * q + _W3L[k] * emh + _W3H[k] * eml).astype(F32)
+            ge[k] = _fma(_W3H[k], emh, small)                 # the one rounding at the odd term's scale
+        else:
+            em = (a + b).astype(F32)
+            x = _fma(em, F32(3), _fma((F32(4.5) * em).astype(F32), em, base))
+            ge[k] = _fma(_WL[k], x, (_WH[k] * x).astype(F32))
     v = _fma(F32(b1), (ge - g).astype(F32), g)
     if Gx or Gy:
         eG = (EX * Gx + EY * Gy).astype(F32)
@@ -130,8 +149,9 @@ class Model:
         b1, c1 = 3 * h / (2 * tau + dt), 3 * tau * h / (2 * tau + dt)
         b7, c7 = h / (2 * tau + h), tau * h / (2 * tau + h)
         g = self.g
-        if self.cell == "one_rounding" and T == F32:
-            fp = _cell_one_rounding(g, Gx, Gy, b1, c1, dt)
+        if self.cell != "plain" and T == F32:
+            fp = _cell_one_rounding(g, Gx, Gy, b1, c1, dt, compensated=self.cell != "equilibrium_only",
+                                    one_rounding=self.cell != "moments_only")
         else:
             d, mx, my = _moments(g, Gx, Gy, dt / 2, T)
             fp = _relax(g, d, mx, my, Gx, Gy, b1, c1, T)

@@ -7,7 +7,8 @@ NumPy model of tests/fp32_model.py (D2Q9, deviation variables):
     FP32 rounding of the stored state per step costs (< 1e-7, test_oracle_storage_precision.py);
   * with the cell stage formed with one rounding at the scale of the equilibrium's odd term
     (compensated moments, exact e.m, one fused multiply-add), the all-FP32 model meets the
-    1e-6 bar. This is the form the kernels' step 1 should take."""
+    1e-6 bar, and neither half of it (compensated moments, one-rounding equilibrium) does so
+    alone. This is the form the kernels' step 1 should take."""
 import numpy as np
 import pytest
 
@@ -55,3 +56,8 @@ def test_plain_fp32_drifts_like_the_kernels(name, oracle_u):
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_one_rounding_cell_stage_meets_the_bar(name, oracle_u):
     assert _err(name, oracle_u[name], T=F32, cell="one_rounding") < 1e-6
+
+
+@pytest.mark.parametrize("half", ["moments_only", "equilibrium_only"])
+def test_either_half_alone_is_not_enough(half, oracle_u):
+    assert _err("channel", oracle_u["channel"], T=F32, cell=half) > 2e-6
