@@ -17,6 +17,8 @@ y (the channel), or NEQ walls on all four sides with a moving +y lid (the cavity
 of the equilibrium's odd term: moments by compensated (two-sum) summation, e.m kept as an
 exact two-term sum, the small terms of W (q + 3 e.m) added first and a single fused
 multiply-add with 3W last, and the relaxation itself as one fused multiply-add.
+`cell="lean"` is its cheaper form: only the momentum sums compensated, e.m a single rounded
+value, the odd term still one final fused multiply-add with 3W.
 `cell="moments_only"` / `"equilibrium_only"` apply one half of it (the other half as in the
 kernels: plain sums; e.m rounded, then fma(e.m, 3, q) and W x)."""
 import numpy as np
@@ -96,12 +98,13 @@ def _nsum(terms):
     return s
 
 
-def _cell_one_rounding(g, Gx, Gy, b1, c1, dt, compensated=True, one_rounding=True):
+def _cell_one_rounding(g, Gx, Gy, b1, c1, dt, compensated=True, one_rounding=True, lean=False):
     """The FP32 cell stage with compensated moments and/or the one-rounding equilibrium
-    (otherwise: plain sums, and e.m rounded, fma(e.m, 3, q) and W x as in the kernels)."""
+    (otherwise: plain sums, and e.m rounded, fma(e.m, 3, q) and W x as in the kernels).
+    lean: only the momentum sums compensated, and e.m a single rounded value."""
     w = dt / 2
     sm = _csum if compensated else _nsum
-    d = sm([g[k] for k in range(9)])
+    d = (_nsum if lean else sm)([g[k] for k in range(9)])
     mx = sm([F32(E[k, 0]) * g[k] for k in range(9) if E[k, 0]] + [np.full_like(g[0], F32(w) * F32(Gx))])
     my = sm([F32(E[k, 1]) * g[k] for k in range(9) if E[k, 1]] + [np.full_like(g[0], F32(w) * F32(Gy))])
     mm = _fma(mx, mx, (my * my).astype(F32))
@@ -110,7 +113,7 @@ def _cell_one_rounding(g, Gx, Gy, b1, c1, dt, compensated=True, one_rounding=Tru
     for k in range(9):
         a, b = (F32(E[k, 0]) * mx).astype(F32), (F32(E[k, 1]) * my).astype(F32)
         if one_rounding:
-            emh, eml = _two_sum(a, b)
+            emh, eml = _two_sum(a, b) if not lean else ((a + b).astype(F32), np.zeros_like(a))
             q = _fma((F32(4.5) * emh).astype(F32), emh, base)  # even part (small)
             small = (_WH[k] * q + _WL[k] * q + _W3L[k] * emh + _W3H[k] * eml).astype(F32)
             ge[k] = _fma(_W3H[k], emh, small)                 # the one rounding at the odd term's scale
@@ -151,7 +154,7 @@ class Model:
         g = self.g
         if self.cell != "plain" and T == F32:
             fp = _cell_one_rounding(g, Gx, Gy, b1, c1, dt, compensated=self.cell != "equilibrium_only",
-                                    one_rounding=self.cell != "moments_only")
+                                    one_rounding=self.cell != "moments_only", lean=self.cell == "lean")
         else:
             d, mx, my = _moments(g, Gx, Gy, dt / 2, T)
             fp = _relax(g, d, mx, my, Gx, Gy, b1, c1, T)

@@ -53,9 +53,10 @@ def test_plain_fp32_drifts_like_the_kernels(name, oracle_u):
     assert 1e-6 < _err(name, oracle_u[name], T=F32) < 2e-5
 
 
+@pytest.mark.parametrize("cell", ["one_rounding", "lean"])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_one_rounding_cell_stage_meets_the_bar(name, oracle_u):
-    assert _err(name, oracle_u[name], T=F32, cell="one_rounding") < 1e-6
+def test_one_rounding_cell_stage_meets_the_bar(name, cell, oracle_u):
+    assert _err(name, oracle_u[name], T=F32, cell=cell) < 1e-6
 
 
 @pytest.mark.parametrize("half", ["moments_only", "equilibrium_only"])
