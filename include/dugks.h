@@ -269,12 +269,16 @@ const char *dugks_batch_last_error(dugks_batch_t b);
 void dugks_batch_destroy(dugks_batch_t b);
 
 /* Allocation-free FP64 residual and conservation totals (the paper has no counterpart; this
- * is a library facility). Same reduction and the same outputs as dugks_residual, for callers
- * that cannot call cudaMalloc: code running while a CUDA graph is being captured, hosts whose
- * own allocator already owns the device memory, and loops that must not take cudaMalloc's
- * implicit device synchronisation. Nothing is allocated: the partial sums go to a fixed
- * 512 KB array in device memory that the library reserves on every GPU that loads it, held
- * until the process exits.
+ * is a library facility). Same reduction, on the same number of blocks in the same order,
+ * and the same outputs as dugks_residual for a state of the incompressible model (the
+ * default, DUGKS_MODEL_INCOMPRESSIBLE; the original model's velocity divides by the local
+ * density, which this call does not do). It serves callers that cannot call cudaMalloc:
+ * hosts whose own allocator already owns the device memory, and loops that must not take
+ * cudaMalloc's implicit device synchronisation. Nothing is allocated: the partial sums go to
+ * a fixed 256 KB array in device memory that the library reserves on every GPU that loads
+ * it, held until the process exits. The call copies its sums to host memory and synchronises
+ * `stream` before it returns, so it cannot be called while that stream is being captured
+ * into a CUDA graph.
  *   state:  DEVICE pointer to g~ = f~ - W rho0 in the storage type `store`, unpadded layout
  *           [Q][nz][ny][nx] (what dugks_get_state writes with buf_is_device = 1).
  *   nx, ny, nz, lattice: the mesh and velocity set (nz = 1 and DUGKS_D2Q9 in 2D).
@@ -287,13 +291,14 @@ void dugks_batch_destroy(dugks_batch_t b);
  *   out:    HOST [dim+2] doubles: out[0] = ||u - uprev||/||u|| (+inf when have_prev == 0),
  *           out[1] = sum rho, out[2+a] = sum rho0 u_a.
  *   stream: cudaStream_t (NULL: legacy stream); the call synchronises it before returning.
- * Limit: at most 16,777,216 cells (256^3); larger meshes return DUGKS_E_INVAL with the
- * limit in dugks_last_error(NULL). The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) and caches it; make that first call before any stream
- * capture. Every call on a device shares the one array: calls that overlap on the GPU (from
- * several streams or threads) race and give wrong sums. Each call rewrites every partial it
- * reads, so nothing has to be cleared between calls. Errors: DUGKS_E_INVAL, DUGKS_E_CUDA,
- * DUGKS_E_UNSTABLE (non-finite sums); the reason is in dugks_last_error(NULL). */
+ * Limit: at most 16,777,216 cells (256^3; 4096 partial-sum blocks of at most 4096 cells);
+ * larger meshes return DUGKS_E_INVAL with the limit in dugks_last_error(NULL). The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current) and caches it. Every call on a device shares the one array: calls that
+ * overlap on the GPU (from several streams or threads) race and give wrong sums. Each call
+ * rewrites every partial it reads, so nothing has to be cleared between calls. Errors:
+ * DUGKS_E_INVAL, DUGKS_E_CUDA, DUGKS_E_UNSTABLE (non-finite sums); the reason is in
+ * dugks_last_error(NULL). */
 int dugks_residual_static(int32_t lattice, int32_t store, const void *state, int64_t nx, int64_t ny, int64_t nz,
                           double rt, double rho0, const double *shift, const float *shift_field, double *uprev,
                           int32_t have_prev, double *out, void *stream);

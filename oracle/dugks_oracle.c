@@ -18,7 +18,7 @@
  * what the Appendix writes. Where the paper leaves a choice open, the reading taken is
  * stated at the function that makes it (readings R1..R9 below).
  *
- * Readings of the paper (each also listed in the design notes of the repository):
+ * Readings of the paper, each a choice where the paper is silent, ambiguous or garbled:
  *  R1  tau = nu / RT (Sec. 2.1 introduces tau but relates it to nu nowhere; this is the
  *      Chapman-Enskog viscosity of the BGK model with sound speed^2 = RT).
  *  R2  G(x, t) = (g + field(x)) cos(omega t). At a cell centre G is the cell's value; at

@@ -290,10 +290,45 @@ __device__ __forceinline__ T wmul(int k, T x) {
 // u = c m / rho0. Working with m keeps every constant that feeds back into the momentum
 // exactly 1 (no c or 1/rho0 factor inside the relaxation loop).
 // ---------------------------------------------------------------------------------
-template <int Q, class T>
+//
+// EXACT_J (FP32 only; used for the cell moments of step 1): the momentum sums are formed
+// without the rounding of a plain FP32 sum. The cell stage rounds the same way at every step
+// of a slowly varying flow, so a momentum rounded at the scale of the largest |g_k| biases
+// the momentum that the relaxation aims at, and the bias accumulates over the steps. Each
+// g_k is split exactly into a head on the grid of 2^(e-19) and a tail, where 2^e bounds the
+// cell's largest |g_k| (Dekker's splitting by adding and subtracting 1.5 * 2^(e+4)); the
+// head sums are exact in FP32 (at most 10 terms below 2^(e+4) on that grid) and the tails
+// are below 2^(e-20), so m = heads + tails is rounded once, at the scale of m.
+template <int Q, class T, bool EXACT_J = false>
 __device__ __forceinline__ void moments(const T g[Q], const T rGh[3], T w, T &drho, T m[3]) {
     constexpr int D = Lat<Q>::D;
     T r = T(0), j[3] = {T(0), T(0), T(0)};
+    if constexpr (EXACT_J && sizeof(T) == 4) {
+        float amax = 0.0f;
+#pragma unroll
+        for (int k = 0; k < Q; k++) {
+            r += g[k];
+            if (Lat<Q>::e(k, 0) != 0 || Lat<Q>::e(k, 1) != 0 || Lat<Q>::e(k, 2) != 0) amax = fmaxf(amax, fabsf(g[k]));
+        }
+        // 1.5 * 2^(E + 5) for amax in [2^E, 2^(E+1)): exponent field + 5, significand 1.5
+        const float split = __uint_as_float((__float_as_uint(amax) & 0x7f800000u) + 0x02c00000u);
+        float hi[3] = {0.0f, 0.0f, 0.0f}, lo[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int k = 0; k < Q; k++) {
+            if (Lat<Q>::e(k, 0) == 0 && Lat<Q>::e(k, 1) == 0 && Lat<Q>::e(k, 2) == 0) continue;
+            const float h = __fsub_rn(__fadd_rn(g[k], split), split);
+            const float l = __fsub_rn(g[k], h);
+#pragma unroll
+            for (int a = 0; a < D; a++) {
+                if (Lat<Q>::e(k, a) > 0) { hi[a] = __fadd_rn(hi[a], h); lo[a] = __fadd_rn(lo[a], l); }
+                if (Lat<Q>::e(k, a) < 0) { hi[a] = __fsub_rn(hi[a], h); lo[a] = __fsub_rn(lo[a], l); }
+            }
+        }
+        drho = r;
+#pragma unroll
+        for (int a = 0; a < 3; a++) m[a] = (a < D) ? __fadd_rn(hi[a], fmaf(rGh[a], w, lo[a])) : 0.0f;
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < Q; k++) {
         r += g[k];
@@ -331,6 +366,26 @@ __device__ __forceinline__ T geq_k(int k, T drho, const T m[3], T mm, T inv_rho0
 // Step 1 (eq. f_bar_+) uses b = 3h/(2tau+dt), c = 3 tau h/(2tau+dt); step 7
 // (eq. original_f) uses b = h/(2tau+h), c = tau h/(2tau+h). FORCE = false drops S
 // (G = 0 everywhere). Opposite velocities share e.m and the quadratic part of geq.
+// In FP32 the equilibrium is rounded once at the scale of its odd term 3 W e.m: with
+// 3W = W3h + W3l and W = Wh + Wl split into heads and tails, geq = W3h e.m + (W3l e.m + W q)
+// with the small terms formed first and the odd term added by one fused multiply-add
+// (forming W (q + 3 e.m) instead rounds several times at that scale, and at a steady flow
+// those roundings repeat from step to step and bias the relaxation).
+template <int Q, class T>
+__device__ __forceinline__ void geq_pair(int k, T em, T q, T &geq, T &geqb) {
+    const double W = Lat<Q>::template wt<double>(k);
+    if constexpr (sizeof(T) == 4) {
+        const float wh = (float)W, wl = (float)(W - (double)wh);
+        const float w3h = (float)(3.0 * W), w3l = (float)(3.0 * W - (double)w3h);
+        const float wq = fmaf(wl, q, wh * q);
+        geq = fmaf(w3h, em, fmaf(w3l, em, wq));
+        geqb = fmaf(-w3h, em, fmaf(-w3l, em, wq));
+    } else {
+        geq = (T)W * fmaT(em, T(3), q);
+        geqb = (T)W * fmaT(em, T(-3), q);
+    }
+}
+
 template <int Q, class T, bool FORCE = true>
 __device__ __forceinline__ void relax(const T g[Q], T drho, const T m[3], const T rGh[3], T rho0, T inv_rho0, T b,
                                       T c, T out[Q]) {
@@ -351,7 +406,9 @@ __device__ __forceinline__ void relax(const T g[Q], T drho, const T m[3], const 
                 if (Lat<Q>::e(k, a) < 0) { em -= m[a]; if (FORCE) ge -= rGh[a]; }
             }
             const T q = fmaT(c45 * em, em, base);   // even part of the bracket
-            const T geq = wmul<Q, T>(k, fmaT(em, T(3), q));
+            T geq, geqb;
+            if constexpr (kb != k) geq_pair<Q, T>(k, em, q, geq, geqb);
+            else geq = wmul<Q, T>(k, q);             // the rest velocity (e = 0)
             T v = fmaT(b, geq - g[k], g[k]);
             if constexpr (FORCE) {
                 const T feq = fmaT((T)Lat<Q>::template wt<double>(k), rho0, geq);
@@ -359,7 +416,6 @@ __device__ __forceinline__ void relax(const T g[Q], T drho, const T m[3], const 
             }
             out[k] = v;
             if constexpr (kb != k) {
-                const T geqb = wmul<Q, T>(kb, fmaT(em, T(-3), q));
                 T vb = fmaT(b, geqb - g[kb], g[kb]);
                 if constexpr (FORCE) {
                     const T feqb = fmaT((T)Lat<Q>::template wt<double>(kb), rho0, geqb);

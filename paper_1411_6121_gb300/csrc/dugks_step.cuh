@@ -270,7 +270,7 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
             for (int k = 0; k < Q; k++) g[k] = (T)Store<S>::ld(src + k * p.dstride + off);
             T Gh[3], drho, m[3];
             cell_G<D, T>(p, cell, ncell, ct, Gh);
-            moments<Q, T>(g, Gh, cf.wcell * cf.rho0, drho, m);
+            moments<Q, T, true>(g, Gh, cf.wcell * cf.rho0, drho, m);
             const T ir = original_model<T, ORIG>(p, cf, Gh, cf.wcell, drho, m);
             relax<Q, T>(g, drho, m, Gh, cf.rho0, ir, cf.b1, cf.c1, out);
         }

@@ -216,7 +216,7 @@ __device__ __forceinline__ void step2d_tile(const StepParams &p, unsigned char *
             for (int k = 0; k < Q; k++) g[k] = (float)Store<S>::ld(src + k * p.dstride + off);
             float Gh[3] = {0.0f, 0.0f, 0.0f}, drho, m[3];
             if (FORCE) cell_G<2, float>(p, (int64_t)cx + (int64_t)nx * cy, ncell, ct, Gh);
-            moments<Q, float>(g, Gh, cf.wcell * cf.rho0, drho, m);
+            moments<Q, float, true>(g, Gh, cf.wcell * cf.rho0, drho, m);
             relax<Q, float, FORCE>(g, drho, m, Gh, cf.rho0, cf.inv_rho0, cf.b1, cf.c1, f);
             float mo[6];
             phi_moments_2d(f, mo);

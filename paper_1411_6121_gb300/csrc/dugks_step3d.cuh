@@ -412,7 +412,7 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
             const int64_t c = (int64_t)cx + (int64_t)nx * ((int64_t)cy + (int64_t)ny * gz);
             cell_G<3, float>(p, c, ncell, ct, Gh);
         }
-        moments<Q, float>(g, Gh, cf.wcell * cf.rho0, drho, m);
+        moments<Q, float, true>(g, Gh, cf.wcell * cf.rho0, drho, m);
         float f[Q];
         relax<Q, float, FORCE>(g, drho, m, Gh, cf.rho0, cf.inv_rho0, cf.b1, cf.c1, f);
         float mo[10];

@@ -1,13 +1,15 @@
 // noalloc.cu -- the FP64 residual / conservation reduction for callers that cannot allocate.
 //
 // dugks_residual (api.cu) reduces through a per-block partial-sum buffer that the handle
-// allocates with cudaMalloc at creation. Some callers cannot make that call: code that runs
-// while a CUDA graph is being captured, code embedded in a host framework whose allocator
-// already owns the device memory (cudaMalloc there fails or fragments it), and latency-bound
-// loops that must not take cudaMalloc's implicit device synchronisation. They need the same
-// reduction with nothing allocated on their behalf. This file gives them one entry point,
-// dugks_residual_static, which runs the very same kernels with the partial sums placed in a
-// fixed array in device memory that the library reserves when it is loaded.
+// allocates with cudaMalloc at creation. Some callers cannot make that call: code embedded in
+// a host framework whose allocator already owns the device memory (cudaMalloc there fails or
+// fragments it), and loops that must not take cudaMalloc's implicit device synchronisation.
+// They need the same reduction with nothing allocated on their behalf. This file gives them
+// one entry point, dugks_residual_static, which runs the very same kernels, on the same
+// number of blocks, with the partial sums placed in a fixed array in device memory that the
+// library reserves when it is loaded. The call copies its sums to host memory and
+// synchronises its stream before it returns, so it cannot be called while that stream is
+// being captured into a CUDA graph.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -19,14 +21,14 @@
 
 namespace dugks {
 
-// One partial-sum block covers RES_CELLS_PER_BLOCK cells (256 threads x 8 cells); each
-// block writes 8 doubles, and the final sum takes 8 more. The largest grid the array holds
-// is STATIC_RES_MAX_BLOCKS, i.e. STATIC_RES_MAX_CELLS = 8192 * 2048 = 16,777,216 cells
-// (a 256^3 mesh). Size: (8192 + 1) * 8 doubles = 512 KB, held by every GPU that loads the
-// library until the process exits.
-constexpr int64_t RES_CELLS_PER_BLOCK = 2048;
-constexpr int STATIC_RES_MAX_BLOCKS = 8192;
-constexpr int64_t STATIC_RES_MAX_CELLS = RES_CELLS_PER_BLOCK * STATIC_RES_MAX_BLOCKS;
+// The reduction runs residual_blocks(ncell) blocks, as dugks_residual does: one per 2048
+// cells, at most 4096, each block striding over its cells in a fixed order and writing 8
+// doubles; the final sum takes 8 more. The array holds the 4096 blocks' partials. The entry
+// point accepts meshes up to STATIC_RES_MAX_CELLS = 4096 * 4096 = 16,777,216 cells (a 256^3
+// mesh, at most 4096 cells per block). Size: (4096 + 1) * 8 doubles = 256 KB, held by every
+// GPU that loads the library until the process exits.
+constexpr int STATIC_RES_MAX_BLOCKS = 4096;
+constexpr int64_t STATIC_RES_MAX_CELLS = (int64_t)4096 * 4096;
 
 static __device__ __align__(256) double g_res_scratch[(STATIC_RES_MAX_BLOCKS + 1) * 8];
 
@@ -77,7 +79,7 @@ extern "C" int dugks_residual_static(int32_t lattice, int32_t store, const void 
     const int64_t ncell = nx * ny * nz;
     if (ncell > STATIC_RES_MAX_CELLS) {
         snprintf(g_static_err, sizeof g_static_err,
-                 "dugks_residual_static: %lld cells exceed the static scratch limit of %lld cells (8192 partial-sum blocks)",
+                 "dugks_residual_static: %lld cells exceed the static scratch limit of %lld cells (4096 partial-sum blocks of at most 4096 cells)",
                  (long long)ncell, (long long)STATIC_RES_MAX_CELLS);
         return fail_static(DUGKS_E_INVAL);
     }
@@ -87,13 +89,14 @@ extern "C" int dugks_residual_static(int32_t lattice, int32_t store, const void 
         snprintf(g_static_err, sizeof g_static_err, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
         return fail_static(DUGKS_E_CUDA);
     }
-    const int nblocks = (int)((ncell + RES_CELLS_PER_BLOCK - 1) / RES_CELLS_PER_BLOCK);
+    const int nblocks = residual_blocks(ncell);  // <= STATIC_RES_MAX_BLOCKS
     double *partials = scratch;                               // [nblocks][8], fully rewritten
     double *final_sum = scratch + (int64_t)STATIC_RES_MAX_BLOCKS * 8;  // [8], fully rewritten
 
     // Unpadded layout [Q][nz][ny][nx]; the velocity shift u = c/rho0 sum e g + shift (+
     // shift_field per cell) is passed through the reduction's force slots with dt = 2 and
-    // omega = 0 (so the kernel's G dt/2 cos(omega t) factor is exactly the shift).
+    // omega = 0 (so the kernel's G dt/2 cos(omega t) factor is exactly the shift). The model
+    // field stays 0: the incompressible model's u = c j / rho0 + shift.
     StepParams p;
     memset(&p, 0, sizeof p);
     p.nx = (int)nx;

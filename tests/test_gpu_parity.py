@@ -7,10 +7,17 @@ Tolerances:
   * FP64 storage and arithmetic (the same fused kernel instantiated on double): velocity
     and pressure within relative L2 1e-6 of the oracle after 1000 steps (measured ~1e-12),
     and element-wise state agreement to 1e-10 of the state's scale.
-  * FP32: each step rounds every stored value once (relative 2^-24 of |g~|) and smooth
-    flows round coherently, so the error grows about linearly with the step count:
-    n * 2^-24 * (a few) ~ 2e-5 after 1000 steps bounds it (measured 1.6e-6 to 1.3e-5);
-    element-wise after 20 steps: 2e-6 of the state's scale.
+  * FP32: velocity and pressure within relative L2 1e-6 of the oracle after 1000 steps, on
+    the throughput and the reference kernels. Random roundings of the stored state are damped
+    by the scheme (one FP32 rounding of the state per step costs < 1e-7 on the oracle); what
+    does accumulate is a rounding that repeats at every step of a slowly varying flow. The
+    cell stage (step 1) therefore forms the momentum sums exactly and the equilibrium's odd
+    term with one rounding (dugks_device.cuh); without that the kernels drifted to 1.6e-6 to
+    6e-6 after 1000 steps. Element-wise after 8 to 20 steps: 2e-6 of the state's scale.
+    The pressure misses 1e-6: it is about 30 times smaller than the stored values, so 1e-6 of
+    it is about half a unit in the last place of the state, and FP32 storage alone already
+    costs 1e-7 to 5e-7 of it (test_oracle_storage_precision.py). Measured after 1000 steps:
+    2.1e-6 to 3.3e-6 (2D), 8.0e-6 (D3Q19 cube); asserted below 1e-5.
   * F16 / BF16 deviation storage (11 / 8 significant bits, stochastic rounding): F16 within
     1e-3 after 1000 steps; BF16 at the level its 8 bits allow (2e-3 to 6e-3, stated per test).
 """
@@ -113,19 +120,22 @@ def test_d2q9_1000_steps(name):
     assert d < 1e-10, d
     got = s64.moments()
     assert rel_l2(got[1:], ref[1:]) < 1e-6
-    s32 = _sim(store=0, **cfg)
-    s32.init()
-    s32.step(1000)
-    got = s32.moments()
-    assert rel_l2(got[1:], ref[1:]) < 2e-5
-    if name != "channel":  # the force-driven channel from rest has p ~ 0
-        assert rel_l2(got[0], ref[0]) < 2e-5
+    for kernel in (0, 1):  # throughput and reference kernel, FP32
+        s32 = _sim(store=0, kernel=kernel, **cfg)
+        s32.init()
+        s32.step(1000)
+        got = s32.moments()
+        eu = rel_l2(got[1:], ref[1:])
+        assert eu < 1e-6, (name, kernel, "u", eu)
+        if name != "channel":  # the force-driven channel from rest has p ~ 0
+            ep = rel_l2(got[0], ref[0])
+            assert ep < 1e-5, (name, kernel, "p", ep)
 
 
 def test_d2q9_force_field_time_dependent():
     cfg = dict(shape=(33, 17), q=9, nu=0.05, dt=0.5, g=(2e-5, 0.0, 0.0), omega=0.01, bcs=W.channel_bcs(2))
     field = W.force_field(cfg["shape"], 1e-5, seed=9, rel=1.0)
-    for store, tol in ((3, 1e-10), (0, 1e-5)):
+    for store, tol in ((3, 1e-10), (0, 1e-6)):
         o, s = run_pair(cfg, 300, field=field, store=store)
         ref, got = o.moments(), s.moments()
         assert rel_l2(got[1:], ref[1:]) < max(tol, 1e-7), (store, rel_l2(got[1:], ref[1:]))
@@ -205,7 +215,8 @@ def test_d3q19_cavity_1000_steps():
     ref = o.moments()
     # 16-bit storage (stochastic rounding), both kernels: F16 (measured u 2.2e-4, p 9.9e-4),
     # BF16 (8 significant bits; measured u 1.8e-3, p 7.7e-3)
-    for store, kernel, tol, ptol in ((3, 0, 1e-6, 1e-6), (0, 0, 2e-5, 2e-5), (2, 0, 1e-3, 2e-3), (2, 1, 1e-3, 2e-3),
+    for store, kernel, tol, ptol in ((3, 0, 1e-6, 1e-6), (0, 0, 1e-6, 1e-5), (0, 1, 1e-6, 1e-5),
+                                     (2, 0, 1e-3, 2e-3), (2, 1, 1e-3, 2e-3),
                                      (1, 0, 3e-3, 1.5e-2), (1, 1, 3e-3, 1.5e-2)):
         s = _sim(store=store, kernel=kernel, **cfg)
         s.init()
@@ -216,14 +227,15 @@ def test_d3q19_cavity_1000_steps():
 
 
 def test_d3q27_cavity_300_steps():
-    """The paper's 3D velocity set through the throughput kernel, every storage: FP32 within the
-    FP32 drift, the 16-bit stores within the bounds of the D3Q19 cube test."""
+    """The paper's 3D velocity set through the throughput kernel, every storage: FP32 velocity
+    within 1e-6 on both kernels (pressure as in the D3Q19 cube), the 16-bit stores within the
+    bounds of the D3Q19 cube test."""
     cfg = dict(shape=(24, 20, 18), q=27, nu=0.05, dt=0.5, bcs=W.cavity_bcs(3, 0.1))
     o = Oracle(**cfg)
     o.init()
     o.step(300)
     ref = o.moments()
-    for store, kernel, tol, ptol in ((0, 0, 2e-5, 2e-5), (0, 1, 2e-5, 2e-5), (2, 0, 1e-3, 2e-3), (1, 0, 3e-3, 1.5e-2)):
+    for store, kernel, tol, ptol in ((0, 0, 1e-6, 1e-5), (0, 1, 1e-6, 1e-5), (2, 0, 1e-3, 2e-3), (1, 0, 3e-3, 1.5e-2)):
         s = _sim(store=store, kernel=kernel, **cfg)
         s.init()
         s.step(300)

@@ -258,8 +258,18 @@ def _table1():
 
 def test_table1_convergence_order():
     """Table 1 (Sec. 3.1): the velocity error of the periodic flow falls at second order
-    between N = 16 and N = 32 (paper: 2.015). The oracle's error constants are about five
-    times the printed ones (see the design notes); the order is what is pinned here."""
+    between N = 16 and N = 32 (paper: 2.015).
+
+    The error constant is pinned by a closed form instead of the printed value. This run has
+    dt = 1e-4 against tau = nu / RT = 2e-3, so h is tiny and the step-4 interface value is the
+    plain mean of the two cells: the scheme then discretises the BGK equation with central
+    differences, and the non-equilibrium part that carries the viscous stress is itself a
+    central difference, so the viscous operator is the Laplacian of width 2 dx. For the mode
+    sin(2 pi x) sin(2 pi y) it has the eigenvalue -2 sin^2(k dx) / dx^2 instead of -2 k^2
+    (k = 2 pi), and the steady velocity balancing the force is too large by the factor
+    (k dx)^2 / sin^2(k dx): E(u) = 5.30% at N = 16 and 1.30% at N = 32. The oracle must sit
+    within 5% of that (it does to 2.5%). The printed constants (0.974%, 0.241%) are of the size
+    of the compact Laplacian's (1.30%, 0.32%), which a step with h comparable to tau gives."""
     t = _table1()
     e16, p16 = _table1_run(16)
     e32, p32 = _table1_run(32)
@@ -267,8 +277,15 @@ def test_table1_convergence_order():
     order_p = np.log2(p16 / p32)
     assert abs(order_u - 2.015) < 0.1, order_u
     assert abs(order_p - 2.027) < 0.25, order_p  # oracle: 1.86
-    # same order of magnitude as the printed errors, and below 10%
-    assert t[16][0] < e16 < 10 * t[16][0]
+    for n, e in ((16, e16), (32, e32)):
+        kd = 2 * np.pi / n
+        wide = kd ** 2 / np.sin(kd) ** 2 - 1.0
+        assert abs(e / wide - 1.0) < 0.05, (n, e, wide)
+    # the printed error at N = 16 is of the compact stencil's size (0.75 of it), far below the
+    # wide stencil's
+    kd = 2 * np.pi / 16
+    compact = (kd / 2) ** 2 / np.sin(kd / 2) ** 2 - 1.0
+    assert 0.5 * compact < t[16][0] < compact < 0.5 * e16
 
 
 @pytest.mark.slow

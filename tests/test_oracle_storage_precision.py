@@ -2,7 +2,10 @@
 rounded after every step, stored as the deviation from the rest equilibrium like the CUDA path:
   * FP32: within 1e-7 of the exact oracle after 1000 steps (velocity, relative L2) on the
     channel, cavity and pressure-driven cases, so the 1e-6 bar is within reach of FP32 storage
-    and a larger FP32 error comes from the arithmetic;
+    and a larger FP32 error comes from the arithmetic. The pressure, about 30 times smaller
+    than the stored values, already moves by 1e-7 to 1e-6 (measured 4.6e-7 and 4.8e-7 on the
+    cavity and the pressure-driven case): FP32 storage alone takes about half of a 1e-6
+    pressure budget;
   * BF16: above 1e-3 even with stochastic rounding, so that bar is out of reach of the format."""
 import numpy as np
 import pytest
@@ -32,9 +35,12 @@ def test_fp32_storage_rounding_alone(name):
         r.step(1)
         g = (r.get_state() - rest).astype(np.float32).astype(np.float64)
         r.set_state(g + rest)
-    u, ue = r.moments()[1:], exact.moments()[1:]
-    err = np.linalg.norm(u - ue) / np.linalg.norm(ue)
+    m, me = r.moments(), exact.moments()
+    err = np.linalg.norm(m[1:] - me[1:]) / np.linalg.norm(me[1:])
     assert 0.0 < err < 1e-7, err
+    if name != "channel":  # the force-driven channel from rest has p ~ 0
+        ep = np.linalg.norm(m[0] - me[0]) / np.linalg.norm(me[0])
+        assert 1e-7 < ep < 1e-6, ep
 
 
 def _bf16(x, rng=None):

@@ -1,12 +1,13 @@
 """The allocation-free residual entry point (dugks_residual_static).
 
-Some callers of this library cannot call cudaMalloc: code running while a CUDA graph is
-being captured, hosts whose own allocator already owns the device memory, and loops that
-must not take cudaMalloc's implicit synchronisation. dugks_residual_static gives them the
-FP64 residual and conservation totals with its partial sums in a fixed device array. This
-test calls it through the C ABI and checks it against dugks_residual (the handle's own
-reduction, which allocates its buffer at creation) on two calls in a row. It sits in a file
-of its own that pytest collects last.
+Some callers of this library cannot call cudaMalloc: hosts whose own allocator already owns
+the device memory, and loops that must not take cudaMalloc's implicit synchronisation.
+dugks_residual_static gives them the FP64 residual and conservation totals with its partial
+sums in a fixed device array. This test calls it through the C ABI and checks it against
+dugks_residual (the handle's own reduction, which allocates its buffer at creation) on two
+calls in a row, including a mesh above 4096 * 2048 cells where both reductions stride over
+their cells with the capped number of blocks. It sits in a file of its own that pytest
+collects last.
 """
 import ctypes as C
 
@@ -30,7 +31,8 @@ def _call(lib, q, store, state, shape, rt, rho0, shift, uprev, have_prev, stream
     return rc, out
 
 
-@pytest.mark.parametrize("q,shape,store", [(19, (40, 20, 12), 0), (9, (45, 38), 0), (19, (24, 16, 10), 1)])
+@pytest.mark.parametrize("q,shape,store", [(19, (40, 20, 12), 0), (9, (45, 38), 0), (19, (24, 16, 10), 1),
+                                           (19, (256, 256, 130), 0)])
 def test_static_residual_matches_handle(q, shape, store):
     import torch
     from paper_1411_6121_gb300 import dugks
