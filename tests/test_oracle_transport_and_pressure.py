@@ -1,0 +1,135 @@
+"""Pins of two parts of the oracle that the flow tests leave loose.
+
+1. Steps 3-4 in 3D (eq. gradient with the cross points of step 3), through free transport.
+   With tau -> infinity the collision coefficients of steps 1 and 7 vanish (b1 = 3h/(2 tau +
+   dt) and b7 = h/(2 tau + h)), so one step moves every velocity independently:
+   f~(n+1) = f~ - dt/dx xi_k . (flux difference) with the step-4 interface value. For a plane
+   wave exp(i theta . n) on a periodic mesh that is a multiplication by
+
+       G_k(theta) = 1 - 2 kappa sum_d e_dk (1 - exp(-i theta_d)) F_d,
+       F_d = (1 + z_d)/2 - kappa e_dk (z_d - 1) - (kappa/4) sum_{t != d} e_tk (1 + z_d) 2i sin(theta_t),
+
+   z_d = exp(i theta_d), kappa = h c / dx: the interface mean, the normal difference, and the
+   tangential difference of the two cross points, each the mean of the four cells around
+   it, read as a plane wave. Every velocity of D2Q9, D3Q19 and D3Q27, with its own wave
+   vector, must reproduce G_k to rounding. A dropped or mis-signed tangential gradient, or a
+   cross point of two cells instead of four, moves the result by 0.2 to 1 of the wave's
+   amplitude. Independently of the oracle, G_k agrees with exact transport
+   exp(-i 2 kappa e_k . theta) to third order in theta (the scheme is second order).
+
+2. The NEQ pressure condition of Sec. 2.4 (eq. NEQ with rho_a = rho0 + p_w / RT, u_a = u_c).
+   A channel between a pressure inlet and outlet (p = +-dp/2) and NEQ no-slip walls has the
+   steady solution u = dp / (2 rho0 nu L) y (H - y) with p linear in x. The oracle reproduces
+   the linear pressure exactly (to rounding), the parabola at second order under refinement,
+   and D3Q19 on the same flow, uniform along z, reproduces D2Q9 (D3Q19 projected onto the
+   x-y plane is D2Q9: weights 1/3 + 2/18 = 4/9, 1/18 + 2/36 = 1/9, 1/36)."""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from oracle.oracle import rel_change
+from paper_1411_6121_gb300 import workloads as W
+
+DT = 0.5
+KAPPA = 0.5 * DT  # h c / dx with RT = 1/3 (c = 1), dx = 1
+
+
+def transport_factor(e, theta, kappa=KAPPA):
+    """G_k(theta) of the module docstring for the integer velocity e."""
+    D = len(theta)
+    tot = 0j
+    for d in range(D):
+        if e[d] == 0:
+            continue
+        z = np.exp(1j * theta[d])
+        F = 0.5 * (1 + z) - kappa * e[d] * (z - 1)
+        for t in range(D):
+            if t != d and e[t] != 0:
+                F -= 0.25 * kappa * e[t] * (1 + z) * 2j * np.sin(theta[t])
+        tot += e[d] * F * (1 - np.conj(z))
+    return 1 - 2 * kappa * tot
+
+
+MODES = [(1, 1, 1), (2, -1, 2), (3, 2, -1), (1, -2, 2)]
+
+
+@pytest.mark.parametrize("q,shape", [(9, (8, 6)), (19, (8, 6, 5)), (27, (8, 6, 5))])
+def test_free_transport_plane_waves(q, shape):
+    rng = np.random.default_rng(q)
+    D = len(shape)
+    o = Oracle(shape, q, nu=1e12 / 3.0, dt=DT, bcs=W.all_periodic())  # tau = 1e12
+    o.init()
+    e, Wt = o.lattice()
+    idx = np.meshgrid(*[np.arange(n) for n in reversed(shape)], indexing="ij")
+    pos = [idx[D - 1 - a].ravel() for a in range(D)]  # x fastest
+    eps = 1e-3
+    f0 = np.zeros((q, o.ncell))
+    pred = np.zeros_like(f0)
+    for k in range(q):
+        m = MODES[rng.integers(len(MODES))]
+        theta = [2 * np.pi * m[a] / shape[a] for a in range(D)]
+        amp = np.exp(2j * np.pi * rng.random())
+        wave = np.exp(1j * sum(theta[a] * pos[a] for a in range(D)))
+        f0[k] = eps * np.real(amp * wave)
+        pred[k] = eps * np.real(amp * transport_factor(e[k][:D], theta) * wave)
+    o.set_state(f0 + Wt[:, None])
+    o.step(1)
+    got = o.get_state() - Wt[:, None]
+    assert np.abs(got - pred).max() < 1e-10 * eps, np.abs(got - pred).max() / eps
+    # the waves really move: the step changes them at the size of the wave
+    assert np.abs(got - f0).max() > 0.1 * eps
+
+
+def test_free_transport_factor_is_second_order():
+    """G_k against exact transport: the error falls 8x per halving of theta (third order in
+    theta, i.e. a second-order scheme), for an axis, an edge and a corner velocity."""
+    for e in ((1, 0, 0), (1, -1, 0), (0, 1, 1), (1, 1, -1)):
+        errs = []
+        for s in (0.1, 0.05, 0.025):
+            th = np.array([s, 0.7 * s, -0.4 * s])
+            errs.append(abs(transport_factor(e, th) - np.exp(-2j * KAPPA * np.dot(e, th))))
+        ratios = np.array(errs[:-1]) / np.array(errs[1:])
+        assert np.all(np.abs(ratios - 8.0) < 0.6), (e, ratios)
+
+
+def _pressure_channel(H, q, nu=0.1, umax=0.01):
+    L = 2 * H
+    dp = 8 * nu * L * umax / H ** 2  # u_max = dp H^2 / (8 rho0 nu L)
+    shape = (L, H) if q == 9 else (L, H, 2)
+    bcs = [W.pressure(dp / 2), W.pressure(-dp / 2), W.wall(), W.wall()]
+    if q != 9:
+        bcs += [W.periodic(), W.periodic()]
+    o = Oracle(shape, q, nu=nu, dt=DT, bcs=bcs)
+    g = np.indices(tuple(reversed(shape)))
+    yy, xx = g[-2].ravel() + 0.5, g[-1].ravel() + 0.5
+    u = np.zeros((len(shape), o.ncell))
+    u[0] = dp / (2 * nu * L) * yy * (H - yy)
+    p = dp / 2 - dp * xx / L
+    o.init(p=p, u=u)
+    prev = o.moments()[1:]
+    for _ in range(100):
+        o.step(1000)
+        m = o.moments()
+        if rel_change(m[1:], prev) < 1e-11:
+            break
+        prev = m[1:]
+    eu = np.linalg.norm(m[1:] - u) / np.linalg.norm(u[0])
+    ep = np.linalg.norm(m[0] - p) / np.linalg.norm(p)
+    return eu, ep, m
+
+
+def test_neq_pressure_poiseuille():
+    e8, p8, m8 = _pressure_channel(8, 9)
+    e16, p16, _ = _pressure_channel(16, 9)
+    # the pressure is linear in x to rounding, the velocity converges at second order
+    assert p8 < 1e-10 and p16 < 1e-10, (p8, p16)
+    assert abs(np.log2(e8 / e16) - 2.0) < 0.1, (e8, e16)
+    assert e16 < 0.02, e16
+    # a pressure of p_w instead of p_w / RT at the walls, or u_a = 0, is far off
+    assert e8 < 0.1
+    # D3Q19 on the same flow, uniform along z, is D2Q9
+    e19, p19, m19 = _pressure_channel(8, 19)
+    m19 = m19.reshape(4, 2, -1)
+    assert np.abs(m19[:, 0] - m19[:, 1]).max() < 1e-14
+    assert np.abs(m19[[0, 1, 2], 0] - m8).max() < 1e-10 * np.abs(m8).max()
+    assert np.abs(m19[3]).max() < 1e-14
