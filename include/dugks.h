@@ -187,7 +187,9 @@ int dugks_set_force_field(dugks_t h, const float *field);
 int dugks_set_boundaries(dugks_t h, const dugks_boundaries *bcs);
 
 /* Wait for the handle's stream, polling for at most timeout_s seconds (<= 0: no limit).
- * DUGKS_E_TIMEOUT if the work has not finished by then (the work keeps running). */
+ * DUGKS_E_TIMEOUT if the work has not finished by then (the work keeps running), or if a
+ * 3D step found that a state copy into shared memory did not land within two seconds (that
+ * CTA left its step undone; the state is then invalid). */
 int dugks_sync(dugks_t h, double timeout_s);
 
 /* Number of kernel launches the handle enqueued since creation (diagnostics). */

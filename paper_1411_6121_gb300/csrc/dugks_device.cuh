@@ -327,20 +327,20 @@ __device__ __forceinline__ void moments(const T g[Q], const T rGh[3], T w, T &dr
         drho = r;
 #pragma unroll
         for (int a = 0; a < 3; a++) m[a] = (a < D) ? __fadd_rn(hi[a], fmaf(rGh[a], w, lo[a])) : 0.0f;
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int k = 0; k < Q; k++) {
-        r += g[k];
+        for (int k = 0; k < Q; k++) {
+            r += g[k];
 #pragma unroll
-        for (int a = 0; a < D; a++) {
-            if (Lat<Q>::e(k, a) > 0) j[a] += g[k];
-            if (Lat<Q>::e(k, a) < 0) j[a] -= g[k];
+            for (int a = 0; a < D; a++) {
+                if (Lat<Q>::e(k, a) > 0) j[a] += g[k];
+                if (Lat<Q>::e(k, a) < 0) j[a] -= g[k];
+            }
         }
-    }
-    drho = r;
+        drho = r;
 #pragma unroll
-    for (int a = 0; a < 3; a++) m[a] = (a < D) ? fmaT(rGh[a], w, j[a]) : T(0);
+        for (int a = 0; a < 3; a++) m[a] = (a < D) ? fmaT(rGh[a], w, j[a]) : T(0);
+    }
 }
 
 // Equilibrium deviation of eq. icfeq in the variables above:

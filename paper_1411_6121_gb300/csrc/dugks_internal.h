@@ -25,6 +25,10 @@ cudaError_t launch_step2d_q9(const StepParams &p, int store, int ry, cudaStream_
 cudaError_t launch_step2d_batch(const StepParams *params, const int4 *items, int nitems, int parity, int store,
                                 int ry, bool force, cudaStream_t stream);
 
+// Whether a TMA wait of the 3D throughput kernel gave up since the last call (the kernel then
+// skipped its step); clears the flag. 1: yes, 0: no, -1: the flag could not be read.
+int tma_wait_failures();
+
 // Auxiliary kernels (aux.cu).
 cudaError_t launch_init(int q, int store, const StepParams &p, const double *pres, const double *vel, double rt,
                         cudaStream_t stream);

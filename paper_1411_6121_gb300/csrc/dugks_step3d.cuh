@@ -31,6 +31,7 @@
 #pragma once
 
 #include "dugks_step.cuh"
+#include "tma.cuh"
 
 namespace dugks {
 
@@ -55,13 +56,22 @@ struct Shape3 {
     static constexpr int FS = NF | 1;                 // y exchange: f at +y
     static constexpr int PLANE = RY * RX * CS;
     static constexpr int US = Q | 1;                  // u0 of a plane (own column), two planes
-    // FP32 storage: the next plane's state is staged in shared memory by cp.async while the
-    // current plane is computed (two buffers, [Q][NT] each: conflict-free per direction)
     static constexpr size_t BASE_FLOATS = 3 * (size_t)PLANE + (size_t)NT * (BS + FS + 2 * US);
-    static constexpr bool STAGE = sizeof(S) == 4 && (BASE_FLOATS + 2 * (size_t)Q * NT) * 4 <= 227 * 1024;
-    static constexpr size_t STAGE_FLOATS = STAGE ? 2 * (size_t)Q * NT : 0;
-    static constexpr size_t smem_floats = BASE_FLOATS + STAGE_FLOATS;
-    static constexpr size_t smem_bytes = smem_floats * sizeof(float);
+    // The state of the tile's planes arrives by TMA into NSTAGE shared-memory stages of
+    // [Q][RY][BX] elements: BX covers the 32 columns from x0 - 1 after rounding the box's
+    // start down to a 16-byte boundary (3 floats or 7 16-bit values at most). Three stages
+    // keep two planes in flight while the third is read. Where the stages do not fit beside
+    // the ring (27 velocities), every plane is loaded directly.
+    static constexpr int BX = 32 + (sizeof(S) == 4 ? 4 : 8);
+    static constexpr int NSTAGE = 3;
+    static constexpr size_t STAGE_BYTES = (size_t)Q * RY * BX * sizeof(S);
+    // stages start at the first 128-byte boundary after the other arrays (aligned at run
+    // time; 128 bytes are reserved for it), the barriers follow them
+    static constexpr size_t STAGE_OFF = BASE_FLOATS * 4;
+    static constexpr size_t BAR_OFF = NSTAGE * STAGE_BYTES;  // from the aligned stage start
+    static constexpr size_t TMA_BYTES = STAGE_OFF + 128 + BAR_OFF + NSTAGE * 8;
+    static constexpr bool TMA = sizeof(S) <= 4 && TMA_BYTES <= 227 * 1024;
+    static constexpr size_t smem_bytes = TMA ? TMA_BYTES : BASE_FLOATS * 4;
 };
 
 // Moment slots in the ring: 0 M0, 1..3 M_x,y,z, 4..6 M_xx,yy,zz, 7 M_xy, 8 M_xz, 9 M_yz.
@@ -276,24 +286,45 @@ __device__ __forceinline__ void neq_wall(const StepParams &p, const Coef<float> 
 
 // One segment of work: the z planes [z0, z1) of the tile whose inner columns start at
 // (x0, y0). The kernel below walks a contiguous run of (tile, plane) units.
+// A stored state value in a TMA stage (shared memory), as FP32 (FP16 holds g~ * 2^12).
+template <class S>
+__device__ __forceinline__ float stage_value(const S *p) {
+    if constexpr (std::is_same<S, __nv_bfloat16>::value) return __bfloat162float(*p);
+    else if constexpr (std::is_same<S, __half>::value) return __half2float(*p) * F16_UNSCALE;
+    else return (float)*p;
+}
+
+// Exit path after a copy that never landed: thread 0 gives the copies that may still be in
+// flight (planes next - 3 .. next - 1 of the stage sequence) a bounded time to land before the
+// CTA leaves, so no copy writes into the shared memory of a finished CTA.
+__device__ __forceinline__ void drain_stages(int tid, uint64_t *bars, int first, int lastp, int next) {
+    if (tid != 0) return;
+    for (int pz = max(first, next - 3); pz <= min(lastp, next - 1); pz++) {
+        const int n = pz - first;
+        mbar_wait(bars + n % 3, (uint32_t)((n / 3) & 1));
+    }
+}
+
 template <int Q, class S, int RY, bool FORCE>
-__device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned char *smem_raw, int x0, int y0, int z0,
-                                               int z1);
+__device__ __forceinline__ void step3d_segment(const StepParams &p, const CUtensorMap *tmap, unsigned char *smem_raw,
+                                               int x0, int y0, int z0, int z1);
 
 // Grid: (tiles along x, tiles along y, z chunks); neighbouring CTAs stream the same z
-// planes of neighbouring tiles together, so the halo columns they share hit in L2.
+// planes of neighbouring tiles together, so the halo columns they share hit in L2. tmap: the
+// tensor map of p.src with the box [Q][RY][BX] (read only where Shape3::TMA).
 template <int Q, class S, int RY, bool FORCE>
-__global__ void __launch_bounds__(32 * RY, 1) fused_step3d(const __grid_constant__ StepParams p, int zchunk) {
+__global__ void __launch_bounds__(32 * RY, 1)
+    fused_step3d(const __grid_constant__ StepParams p, const __grid_constant__ CUtensorMap tmap, int zchunk) {
     using K = Shape3<Q, RY, S>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int z0 = blockIdx.z * zchunk;
     const int z1 = min(p.nz, z0 + zchunk);
-    step3d_segment<Q, S, RY, FORCE>(p, smem_raw, blockIdx.x * K::TXI, blockIdx.y * K::TYI, z0, z1);
+    step3d_segment<Q, S, RY, FORCE>(p, &tmap, smem_raw, blockIdx.x * K::TXI, blockIdx.y * K::TYI, z0, z1);
 }
 
 template <int Q, class S, int RY, bool FORCE>
-__device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned char *smem_raw, int x0, int y0, int z0,
-                                               int z1) {
+__device__ __forceinline__ void step3d_segment(const StepParams &p, const CUtensorMap *tmap, unsigned char *smem_raw,
+                                               int x0, int y0, int z0, int z1) {
     using K = Shape3<Q, RY, S>;
     constexpr int NF = K::NF;
     constexpr int CS = K::CS;
@@ -364,32 +395,52 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
         }
     };
 
-    // ---- staging of plane pz's state (FP32 storage): one 4-byte cp.async per direction
-    //      into the buffer of pz's parity, completed by the cp.async.wait_group in
-    //      make_phi; each thread reads back only what it copied itself ----
-    float *stg = reinterpret_cast<float *>(smem_raw) + (K::smem_floats - K::STAGE_FLOATS);
+    // ---- TMA stages: the real planes first .. lastp of this chunk (planes z0 - 1 .. z1, less
+    //      the ghost planes beyond non-periodic z walls) go in order to stage n % 3 with
+    //      phase (n / 3) & 1, n = pz - first; thread 0 issues each copy once its stage has
+    //      been read by every thread (a barrier lies between) ----
     const int tid = row * 32 + lane;
-    auto prefetch = [&](int pz) __attribute__((always_inline)) {
-        if constexpr (K::STAGE) {
-            if (load) {
-                const int64_t off = (int64_t)wrap_idx(pz, nz) * p.plane + (int64_t)cy * p.px + cx;
-                float *sb = stg + (pz & 1) * Q * K::NT + tid;
-#pragma unroll
-                for (int k = 0; k < Q; k++) {
-                    const unsigned sa = (unsigned)__cvta_generic_to_shared(sb + k * K::NT);
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src + k * p.dstride + off)
-                                 : "memory");
-                }
+    unsigned char *stages = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw + K::STAGE_OFF) + 127) & ~(uintptr_t)127);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stages + K::BAR_OFF);
+    const int first = (!perz && z0 - 1 < 0) ? z0 : z0 - 1;
+    const int lastp = (!perz && z1 >= nz) ? nz - 1 : z1;
+    constexpr int XA = 16 / (int)sizeof(S);                       // box start: multiple of 16 bytes
+    const int xs = (x0 - 1 >= 0) ? (x0 - 1) / XA * XA : -XA;       // x0 - 1 >= -1
+    const int xcol = (x0 - 1) - xs + lane;                         // this lane's column in the box
+    const bool boxed = load && cx == gx && cy == gy;               // not a periodic image
+    auto issue = [&](int pz) __attribute__((always_inline)) {
+        if constexpr (K::TMA) {
+            if (tid == 0 && pz >= first && pz <= lastp) {
+                const int s = (pz - first) % 3;
+                mbar_arrive_expect_tx(bars + s, (uint32_t)K::STAGE_BYTES);
+                tma_load_4d(stages + s * K::STAGE_BYTES, tmap, bars + s, xs, y0 - 1, wrap_idx(pz, nz), 0);
             }
-            asm volatile("cp.async.commit_group;\n" ::: "memory");
         }
     };
+    if constexpr (K::TMA) {
+        if (tid == 0) {
+#pragma unroll
+            for (int s = 0; s < 3; s++) mbar_init(bars + s, 1);
+            mbar_fence_init();
+        }
+        __syncthreads();
+        issue(first);
+        issue(first + 1);
+        issue(first + 2);
+    }
+    bool wait_ok = true;  // false once a copy did not land (the CTA then leaves, see below)
 
     // ---- step 1 for the own column at plane pz into the ring; u0 = fbar+ + (fbar+ - f~)/3
-    //      (the cell's part of eq. f_tilde_+, applied in increment form) is returned.
-    //      staged: the state was prefetched into the staging buffer ----
-    auto make_phi = [&](int pz, float *u0, bool staged) __attribute__((always_inline)) {
+    //      (the cell's part of eq. f_tilde_+, applied in increment form) is returned ----
+    auto make_phi = [&](int pz, float *u0) __attribute__((always_inline)) {
         float *o = R(slot_of(pz), row, lane);
+        const S *sb = nullptr;
+        if constexpr (K::TMA) {
+            const int n = pz - first;
+            wait_ok = wait_ok && mbar_wait(bars + n % 3, (uint32_t)((n / 3) & 1));
+            sb = reinterpret_cast<const S *>(stages + (n % 3) * K::STAGE_BYTES) + row * K::BX + xcol;
+        }
         if (!load) {
 #pragma unroll
             for (int k = 0; k < CS; k++) o[k] = 0.0f;
@@ -398,11 +449,9 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
         const int gz = wrap_idx(pz, nz);
         const int64_t off = (int64_t)gz * p.plane + (int64_t)cy * p.px + cx;
         float g[Q];
-        if (K::STAGE && staged) {
-            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-            const float *sb = stg + (pz & 1) * Q * K::NT + tid;
+        if (K::TMA && boxed) {
 #pragma unroll
-            for (int k = 0; k < Q; k++) g[k] = sb[k * K::NT];
+            for (int k = 0; k < Q; k++) g[k] = stage_value(sb + k * (RY * K::BX));
         } else {
 #pragma unroll
             for (int k = 0; k < Q; k++) g[k] = (float)Store<S>::ld(src + k * p.dstride + off);
@@ -532,17 +581,24 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
 
     // ---------------- prologue: planes z0-1, z0, z0+1 ----------------
     // plane z0+2 is made at the first iteration of the loop below, if there is one
-    const bool need_next0 = z0 + 1 < z1 && (perz || z0 + 2 < nz);
-    if (need_next0) prefetch(z0 + 2);
+    int consumed = 0;
     for (int pz = z0 - 1; pz <= z0 + 1; pz++) {
         if (!perz && (pz < 0 || pz >= nz)) continue;
-        make_phi(pz, US(pz), false);  // (plane z0+1 overwrites the u0 of plane z0-1: same parity)
+        make_phi(pz, US(pz));  // (plane z0+1 overwrites the u0 of plane z0-1: same parity)
+        consumed++;
     }
     for (int pz = z0 - 1; pz <= z0 + 1; pz++) {
         if (!perz && (pz < 0 || pz >= nz)) continue;
         ghosts_xy(pz);
     }
-    __syncthreads();
+    // a copy that never landed: every thread leaves together (after thread 0 gave the copies
+    // in flight a bounded time to land)
+    if (__syncthreads_or(!wait_ok)) {
+        if constexpr (K::TMA) drain_stages(tid, bars, first, lastp, first + 3);
+        return;
+    }
+    // the stages read above are free again
+    for (int i = 0; i < consumed; i++) issue(first + 3 + i);
     for (int pz = z0 - 1; pz <= z0 + 1; pz++)
         if (!perz && (pz < 0 || pz >= nz)) ghost_z(pz);
     __syncthreads();
@@ -582,13 +638,16 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, unsigned cha
         if (kz > z0) {
             const int pn = kz + 1;
             if (perz || pn < nz) {
-                make_phi(pn, US(pn), true);  // prefetched at the previous iteration
-                if (kz + 1 < z1 && (perz || kz + 2 < nz)) prefetch(kz + 2);
+                make_phi(pn, US(pn));  // copied by TMA two iterations ago
                 ghosts_xy(pn);
             } else if (pn == nz) {
                 ghost_z(pn);
             }
-            __syncthreads();
+            if (__syncthreads_or(!wait_ok)) {
+                if constexpr (K::TMA) drain_stages(tid, bars, first, lastp, kz + 4);
+                return;
+            }
+            issue(kz + 4);  // into the stage of plane kz + 1, read above
         }
         const float *cur = R(slot_of(kz), row, lane);
 

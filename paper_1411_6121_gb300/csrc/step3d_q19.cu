@@ -1,8 +1,57 @@
-// step3d_q19.cu -- instantiations of the D3Q19 throughput kernel (dugks_step3d.cuh).
+// step3d_q19.cu -- instantiations of the D3Q19 throughput kernel (dugks_step3d.cuh), the
+// tensor maps its TMA stages read through, and the flag of a copy that never landed.
+#include <string.h>
+
+#include <cudaTypedefs.h>
+
 #include "dugks_internal.h"
 #include "dugks_step3d.cuh"
 
 namespace dugks {
+
+int tma_wait_failures() {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tma_wait_failed, sizeof v) != cudaSuccess) return -1;
+    if (v) {
+        const int zero = 0;
+        cudaMemcpyToSymbol(g_tma_wait_failed, &zero, sizeof zero);
+    }
+    return v;
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (the library
+// links the runtime only).
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+        looked = true;
+    }
+    return fn;
+}
+
+cudaError_t encode_state_map(CUtensorMap *map, const void *base, int esize, bool bf16, int64_t px, int64_t ny,
+                             int64_t nz, int q, int bx, int ry) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    const CUtensorMapDataType dt = esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                              : (bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+    const cuuint64_t dims[4] = {(cuuint64_t)px, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)q};
+    const cuuint64_t strides[3] = {(cuuint64_t)(px * esize), (cuuint64_t)(px * ny * esize),
+                                   (cuuint64_t)(px * ny * nz * esize)};
+    const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)ry, 1u, (cuuint32_t)q};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    const CUresult r = fn(map, dt, 4, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
 
 template <int RY, class S, bool FORCE>
 static cudaError_t launch_ry(const StepParams &p, cudaStream_t stream) {
@@ -42,7 +91,14 @@ static cudaError_t launch_ry(const StepParams &p, cudaStream_t stream) {
     const int nchunks = (p.nz + zchunk - 1) / zchunk;
     dim3 grid(tiles_x, tiles_y, nchunks);
     dim3 block(32, RY);
-    fused_step3d<19, S, RY, FORCE><<<grid, block, K::smem_bytes, stream>>>(p, zchunk);
+    CUtensorMap map;
+    memset(&map, 0, sizeof map);
+    if (K::TMA) {
+        const cudaError_t e = encode_state_map(&map, p.src, (int)sizeof(S), std::is_same<S, __nv_bfloat16>::value, p.px,
+                                               p.ny, p.nz, 19, K::BX, RY);
+        if (e != cudaSuccess) return e;
+    }
+    fused_step3d<19, S, RY, FORCE><<<grid, block, K::smem_bytes, stream>>>(p, map, zchunk);
     return cudaGetLastError();
 }
 

@@ -1,7 +1,9 @@
 // step3d_q27.cu -- the throughput kernel of dugks_step3d.cuh instantiated for D3Q27 (the
 // paper's 3D velocity set, Sec. 2.3): 32 x 8 columns per CTA, F32/BF16/F16 storage. At
-// 27 velocities the two staging buffers do not fit beside the ring, so every plane is loaded
-// directly.
+// 27 velocities the TMA stages do not fit beside the ring, so every plane is loaded
+// directly (the kernel's tensor-map argument is unused).
+#include <string.h>
+
 #include "dugks_internal.h"
 #include "dugks_step3d.cuh"
 
@@ -38,7 +40,11 @@ static cudaError_t launch27(const StepParams &p, cudaStream_t stream) {
     }
     const int zchunk = (p.nz + best - 1) / best;
     const int nchunks = (p.nz + zchunk - 1) / zchunk;
-    fused_step3d<27, S, 8, FORCE><<<dim3(tiles_x, tiles_y, nchunks), dim3(32, 8), K::smem_bytes, stream>>>(p, zchunk);
+    static_assert(!K::TMA, "D3Q27 loads its planes directly");
+    CUtensorMap unused;
+    memset(&unused, 0, sizeof unused);
+    fused_step3d<27, S, 8, FORCE><<<dim3(tiles_x, tiles_y, nchunks), dim3(32, 8), K::smem_bytes, stream>>>(p, unused,
+                                                                                                          zchunk);
     return cudaGetLastError();
 }
 
