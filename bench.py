@@ -292,8 +292,16 @@ def run_batched(torch, steps, warmup, dev):
     torch.cuda.synchronize(dev)
     ms = t0.elapsed_time(t1) / steps
     b.close()
+    # algorithmic bytes per cell update: the FP32 D2Q9 state read and written (2 x 9 x 4) and the
+    # per-cell acceleration field read (2 x 4)
+    bpc = 2 * 9 * 4 + 2 * 4
+    peak, src = hbm_peak()
+    ach = bpc * cells / (ms * 1e-3) / 1e9
     return {"value": cells / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms, "instances": len(specs),
             "cells": cells, "tile": list(tile), "steps": steps,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "bytes_per_cell_update": bpc, "peak_source": src,
+                         "note": "events around the graph replay of all steps (one persistent launch each)"},
             "note": "64 D2Q9 channels, one persistent launch per step replayed as a CUDA graph"}
 
 
@@ -456,26 +464,68 @@ def run_case(torch, case, size, steps, warmup, dev):
             "mlups": nx * ny / ms / 1e3, "gbs_at_132B": nx * ny * ADJ_BYTES / ms / 1e6}
 
 
-def cpu_baseline(seconds=12.0):
-    """The FP64 oracle as it stands on a bounded sample of the same workload: a 40^3 cube
-    at the same Reynolds number (same lid speed, nu scaled with the size), single thread."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or "unknown"."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def _oracle_rate(args):
+    """One oracle process: MLUPS of the twin (q, n) over about `seconds` (worker of the
+    CPU baseline; runs in a spawned process)."""
+    q, n, seconds = args
     from oracle import Oracle
     from paper_1411_6121_gb300 import workloads as W
-    n = 40
-    cfg = W.cavity3d(n=n, re=RE, lid_u=LID, q=Q)
+    cfg = W.cavity3d(n=n, re=RE, lid_u=LID, q=q) if q != 9 else W.cavity2d(n=n, re=RE, lid_u=LID)
+    cfg = {k: v for k, v in cfg.items() if k not in ("rt", "rho0")}
     o = Oracle(**cfg)
     o.init()
     o.step(1)
-    steps = 0
-    t = time.perf_counter()
+    cells = n ** (3 if q != 9 else 2)
+    steps, t = 0, time.perf_counter()
     while True:
         o.step(1)
         steps += 1
         el = time.perf_counter() - t
         if el > seconds:
-            break
-    return {"value": n ** 3 * steps / el / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "D3Q19 cube %d^3 at Re=1000 (lid 0.1, nu=0.1*%d/1000), %d steps, FP64, 1 thread" % (n, n, steps)}
+            return cells * steps / el / 1e6, steps
+
+
+def cpu_baseline(seconds=6.0):
+    """The FP64 oracle as it stands on bounded samples of the workload's twins (the cube at the
+    same Reynolds number, nu scaled with the size), on the host cores:
+      * the 64^3 D3Q19 twin on one thread, and on all cores as one independent oracle process
+        per core (spawned; the oracle itself is serial), whose summed rate is `value`;
+      * the 128^2 D2Q9 cavity twin (Re = 1000) on one thread.
+    About 3 x `seconds` of wall time."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    r1, s1 = _oracle_rate((Q, 64, seconds))
+    r2, s2 = _oracle_rate((9, 128, seconds))
+    ctx = mp.get_context("spawn")  # the GPU is initialised in this process: never fork
+    with ctx.Pool(cores) as pool:
+        res = pool.map_async(_oracle_rate, [(Q, 64, seconds)] * cores).get(timeout=30.0 + 10.0 * seconds)
+    rall = sum(r for r, _ in res)
+    return {"value": rall, "unit": "MLUPS", "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+            "sample": "D3Q19 cube 64^3 at Re=1000 (lid 0.1, nu=0.1*64/1000), FP64: %d independent oracle "
+                      "processes, one per core, %.0f s each (%d to %d steps)" % (
+                          cores, seconds, min(s for _, s in res), max(s for _, s in res)),
+            "single_thread": {"value": r1, "unit": "MLUPS", "cores": 1,
+                              "sample": "the same 64^3 cube, %d steps, one thread" % s1},
+            "cavity2d_128_single_thread": {"value": r2, "unit": "MLUPS", "cores": 1,
+                                           "sample": "D2Q9 cavity 128^2 at Re=1000, %d steps, one thread" % s2}}
 
 
 def max_over_ranks(torch, dist, x, device):
