@@ -82,14 +82,15 @@ typedef struct {
     int64_t nx, ny;  /* cells per axis */
     int64_t nz;      /* 1 in 2D */
     double dx;       /* uniform spacing, dx = dy = dz */
-    const double *faces[3]; /* optional non-uniform mesh (Sec. 3.4's tanh mesh; 2D D2Q9, the
-                               reference kernel, no adjoint or batch): HOST arrays of the
-                               n+1 interface coordinates of x and y, copied at creation;
-                               NULL (default) means uniform spacing dx along that axis.
-                               F32 or F64 storage; faces[2], 3D, 16-bit storage: the
-                               handle is not created (DUGKS_E_UNSUPPORTED); coordinates
-                               that do not increase: DUGKS_E_INVAL. The time step must
-                               satisfy dt <= min width / sqrt(3RT) (DUGKS_E_CFL). */
+    const double *faces[3]; /* optional non-uniform mesh (Sec. 3.4's tanh mesh, which
+                               Sec. 3.5 also uses for the cube; 2D and 3D, the reference
+                               kernel, no adjoint or batch): HOST arrays of the n+1
+                               interface coordinates of x, y (and z in 3D), copied at
+                               creation; NULL (default) means uniform spacing dx along that
+                               axis. F32 or F64 storage; 16-bit storage: the handle is not
+                               created (DUGKS_E_UNSUPPORTED); coordinates that do not
+                               increase, or faces[2] in 2D: DUGKS_E_INVAL. The time step
+                               must satisfy dt <= min width / sqrt(3RT) (DUGKS_E_CFL). */
 } dugks_mesh;
 
 typedef struct {

@@ -80,10 +80,10 @@ StepParams dugks::handle_params(const dugks_t h) {
     p.step_off = 0;
     p.model = h->model;
     if (h->d_metric) {
-        p.metric[0] = h->d_metric;
-        p.metric[1] = h->d_metric + h->metric_off1;
-        for (int a = 0; a < 2; a++)
+        for (int a = 0; a < h->dim; a++) {
+            p.metric[a] = h->d_metric + h->metric_off[a];
             for (int sd = 0; sd < 2; sd++) p.eg[a][sd] = h->eg[a][sd];
+        }
     }
     for (int w = 0; w < 6; w++) {
         p.bc[w] = h->bcs.face[w].type;
@@ -110,14 +110,15 @@ cudaError_t dugks::handle_launch_step(dugks_t h, StepParams &p) {
     return cudaErrorNotSupported;
 }
 
-// Metrics of a non-uniform 2D mesh (Sec. 3.4; the same reading as the oracle): centres are
-// the midpoints of their interfaces; the ghost centres sit one period away on a periodic
-// axis and are the boundary centres mirrored in the wall otherwise. Per axis the device block
-// holds wf (n+1), idc (n+1) and idx (n) (see StepParams).
+// Metrics of a non-uniform mesh (Sec. 3.4; the same reading as the oracle): centres are the
+// midpoints of their interfaces; the ghost centres sit one period away on a periodic axis and
+// are the boundary centres mirrored in the wall otherwise. Per axis the device block holds
+// wf (n+1), idc (n+1) and idx (n) (see StepParams); a uniform axis gets the same block from
+// its spacing dx.
 static int build_metrics(dugks_t h, const dugks_mesh *mesh, const dugks_boundaries *bcs) {
-    const int64_t nn[2] = {h->nx, h->ny};
+    const int64_t nn[3] = {h->nx, h->ny, h->nz};
     std::vector<double> all;
-    for (int a = 0; a < 2; a++) {
+    for (int a = 0; a < h->dim; a++) {
         const int64_t n = nn[a];
         std::vector<double> xf(n + 1), xc(n + 2);
         for (int64_t i = 0; i <= n; i++) xf[i] = mesh->faces[a] ? mesh->faces[a][i] : (double)i * mesh->dx;
@@ -131,7 +132,7 @@ static int build_metrics(dugks_t h, const dugks_mesh *mesh, const dugks_boundari
             xc[n + 1] = 2.0 * xf[n] - xc[n];
         }
         const double *c = xc.data() + 1;  // c[i] for i = -1 .. n
-        if (a == 1) h->metric_off1 = (int64_t)all.size();
+        h->metric_off[a] = (int64_t)all.size();
         for (int64_t i = 0; i <= n; i++) all.push_back((xf[i] - c[i - 1]) / (c[i] - c[i - 1]));
         for (int64_t i = 0; i <= n; i++) all.push_back(1.0 / (c[i] - c[i - 1]));
         for (int64_t i = 0; i < n; i++) all.push_back(1.0 / (xf[i + 1] - xf[i]));
@@ -185,18 +186,19 @@ int dugks_create(const dugks_mesh *mesh, int32_t lattice, double nu, double dt, 
         return handle_fail(NULL, DUGKS_E_INVAL, "bad model selector");
     if (o.model == DUGKS_MODEL_ORIGINAL) o.kernel = 1;  // the original model runs on the reference kernel
     const double c = sqrt(3.0 * o.rt);
-    // non-uniform mesh (Sec. 3.4): interface coordinates per axis; D2Q9 on the reference kernel
-    const bool nonuni = mesh->faces[0] || mesh->faces[1] || mesh->faces[2];
-    double hmin = mesh->dx;  // smallest cell width of the 2D axes (CFL)
+    // non-uniform mesh (Sec. 3.4): interface coordinates per axis, on the reference kernel
+    if (dim == 2 && mesh->faces[2])
+        return handle_fail(NULL, DUGKS_E_INVAL, "a 2D mesh has no z interface coordinates");
+    const bool nonuni = mesh->faces[0] || mesh->faces[1] || (dim == 3 && mesh->faces[2]);
+    double hmin = mesh->dx;  // smallest cell width (CFL)
     if (nonuni) {
         hmin = INFINITY;
-        if (!mesh->faces[0] || !mesh->faces[1]) hmin = mesh->dx;
-        if (dim != 2 || lattice != DUGKS_D2Q9 || mesh->faces[2])
-            return handle_fail(NULL, DUGKS_E_UNSUPPORTED, "non-uniform meshes: 2D D2Q9 only");
+        for (int a = 0; a < dim; a++)
+            if (!mesh->faces[a]) hmin = mesh->dx;
         if (o.store == DUGKS_STORE_BF16 || o.store == DUGKS_STORE_F16)
             return handle_fail(NULL, DUGKS_E_UNSUPPORTED, "non-uniform meshes: F32 or F64 storage");
-        const int64_t nn[2] = {mesh->nx, mesh->ny};
-        for (int a = 0; a < 2; a++) {
+        const int64_t nn[3] = {mesh->nx, mesh->ny, mesh->nz};
+        for (int a = 0; a < dim; a++) {
             if (!mesh->faces[a]) continue;
             for (int64_t i = 0; i < nn[a]; i++) {
                 const double w = mesh->faces[a][i + 1] - mesh->faces[a][i];

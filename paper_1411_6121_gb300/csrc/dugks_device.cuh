@@ -236,11 +236,11 @@ struct StepParams {
     const long long *step_ctr; // device step counter: t_n = (*step_ctr + step_off) dt
     int step_off;
     int model;                 // 0: incompressible model (eq. icfeq); 1: original DUGKS (eq. feq)
-    // non-uniform 2D mesh (Sec. 3.4): per axis a, metric[a] = [wf (n+1) | idc (n+1) | idx (n)]:
+    // non-uniform mesh (Sec. 3.4): per axis a, metric[a] = [wf (n+1) | idc (n+1) | idx (n)]:
     // the weight of the high cell at interface i, 1 / (centre distance across i), 1 / (width
     // of cell i); eg[a][side]: the ghost extrapolation coefficient, ghost = f0 + eg (f1 - f0)
-    const double *metric[2];
-    double eg[2][2];
+    const double *metric[3];
+    double eg[3][2];
     int bc[6];                 // DUGKS_BC_* per face
     double bc_u[6][3];         // wall velocity
     double bc_drho[6];         // pressure condition: rho_a - rho0 = p_w / RT

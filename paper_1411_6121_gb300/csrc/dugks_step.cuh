@@ -69,18 +69,23 @@ __device__ __forceinline__ T wall_drho(const StepParams &p, const Coef<T> &cf, i
     return (T)p.bc_drho[wid] + (T)p.bc_drho1[wid] * cf.cwh;
 }
 
-// Steps 3-4 on a non-uniform 2D mesh (Sec. 3.4, the same reading as the oracle): the
-// interface value interpolates linearly between the two centres (weight w of the high cell),
-// the normal gradient divides their difference by the centre distance, and the tangential
-// gradient divides the difference of the interface's two end points, each bilinear in the
-// four cells around it (weights wm, wp of the high row), by the interface length:
-//   F = M - hc e_d (R - L) idc - hc e_t (Vp - Vm) idt,  M = (1 - w) L + w R,
+// Steps 3-4 on a non-uniform mesh (Sec. 3.4, the same reading as the oracle): the interface
+// value interpolates linearly between the two centres (weight w of the high cell), the normal
+// gradient divides their difference by the centre distance, and each tangential gradient
+// divides the difference of the interface's two cross points, each bilinear in the four cells
+// around it (weights wm, wp of the high row along that axis), by the interface's extent along it:
+//   F = M - hc e_d (R - L) idc - sum_t hc e_t (Vp - Vm) idt,  M = (1 - w) L + w R,
 //   Vp = (1 - wp) M + wp Mp,  Vm = (1 - wm) Mm + wm M.
-// hcn = h c idc and hct = h c idt. Pointers as in reconstruct (2D: the first tangential pair).
+// hcn = h c idc and hct1/hct2 = h c idt. Pointers as in reconstruct (first and, in 3D, second
+// tangential pair; the second pair is not read in 2D).
 template <int Q, int d, class T>
 __device__ __forceinline__ void reconstruct_nu(const T *L, const T *R, const T *L1m, const T *R1m, const T *L1p,
-                                               const T *R1p, T w, T wm, T wp, T hcn, T hct, T F[Q]) {
+                                               const T *R1p, const T *L2m, const T *R2m, const T *L2p,
+                                               const T *R2p, T w, T w1m, T w1p, T w2m, T w2p, T hcn, T hct1,
+                                               T hct2, T F[Q]) {
+    constexpr int D = Lat<Q>::D;
     constexpr int t1 = d == 0 ? 1 : 0;
+    constexpr int t2 = d == 2 ? 1 : 2;
     for (int k = 0; k < Q; k++) {
         const T l = L[k], r = R[k];
         const T mid = fmaT(w, r - l, l);
@@ -88,8 +93,13 @@ __device__ __forceinline__ void reconstruct_nu(const T *L, const T *R, const T *
         if (Lat<Q>::e(k, d) != 0) v = fmaT(-hcn * (T)Lat<Q>::e(k, d), r - l, v);
         if (Lat<Q>::e(k, t1) != 0) {
             const T midp = fmaT(w, R1p[k] - L1p[k], L1p[k]), midm = fmaT(w, R1m[k] - L1m[k], L1m[k]);
-            const T vp = fmaT(wp, midp - mid, mid), vm = fmaT(wm, mid - midm, midm);
-            v = fmaT(-hct * (T)Lat<Q>::e(k, t1), vp - vm, v);
+            const T vp = fmaT(w1p, midp - mid, mid), vm = fmaT(w1m, mid - midm, midm);
+            v = fmaT(-hct1 * (T)Lat<Q>::e(k, t1), vp - vm, v);
+        }
+        if (D == 3 && Lat<Q>::e(k, t2) != 0) {
+            const T midp = fmaT(w, R2p[k] - L2p[k], L2p[k]), midm = fmaT(w, R2m[k] - L2m[k], L2m[k]);
+            const T vp = fmaT(w2p, midp - mid, mid), vm = fmaT(w2m, mid - midm, midm);
+            v = fmaT(-hct2 * (T)Lat<Q>::e(k, t2), vp - vm, v);
         }
         F[k] = v;
     }
@@ -232,17 +242,21 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
         cth = (T)(cos(p.omega * (tn + 0.5 * p.dt)) * p.inv_c);
     }
 
-    // Non-uniform 2D mesh metrics (Sec. 3.4): interpolation weight of the high cell at
-    // interface i, 1 / centre distance across it, 1 / width of cell i; hc = h c.
-    auto mptr = [&](int a) __attribute__((always_inline)) { return a ? p.metric[1] : p.metric[0]; };
+    // Non-uniform mesh metrics (Sec. 3.4): interpolation weight of the high cell at interface i
+    // of axis a, 1 / centre distance across it, 1 / width of cell i; hc = h c.
+    auto mptr = [&](int a) __attribute__((always_inline)) { return a == 0 ? p.metric[0] : (a == 1 ? p.metric[1] : p.metric[2]); };
+    auto nax = [&](int a) __attribute__((always_inline)) { return a == 0 ? nx : (a == 1 ? ny : nz); };
     auto mwf = [&](int a, int i) __attribute__((always_inline)) -> T { return (T)__ldg(mptr(a) + i); };
     auto midc = [&](int a, int i) __attribute__((always_inline)) -> T {
-        return (T)__ldg(mptr(a) + (a ? ny : nx) + 1 + i);
+        return (T)__ldg(mptr(a) + nax(a) + 1 + i);
     };
     auto midx = [&](int a, int i) __attribute__((always_inline)) -> T {
-        return (T)__ldg(mptr(a) + 2 * (a ? ny : nx) + 2 + i);
+        return (T)__ldg(mptr(a) + 2 * nax(a) + 2 + i);
     };
     const T hc = NU ? (T)(0.5 * p.dt / p.inv_c) : T(0);
+    // z metrics of plane-level quantities (3D only; a 2D mesh has no z block)
+    auto zw = [&](int i) __attribute__((always_inline)) -> T { return D == 3 ? mwf(2, i) : T(0); };
+    auto zhc = [&](int i) __attribute__((always_inline)) -> T { return D == 3 ? hc * midx(2, i) : T(0); };
 
     auto slot_of = [](int pz) __attribute__((always_inline)) { return D == 3 ? (pz + 3) % 3 : 0; };
     auto cellp = [&](int slot, int ry, int rx) __attribute__((always_inline)) -> T * { return phi + slot * K::PLANE + (ry * RX + rx) * Q; };
@@ -324,8 +338,14 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
     auto ghost_plane = [&](int pz) __attribute__((always_inline)) {
         const int s = slot_of(pz);
         const int sa = slot_of(pz < 0 ? 0 : nz - 1), sb = slot_of(pz < 0 ? 1 : nz - 2);
-        for (int i = tid; i < K::PLANE; i += NT)
-            phi[s * K::PLANE + i] = ghost_value(phi[sa * K::PLANE + i], phi[sb * K::PLANE + i]);
+        if constexpr (NU) {  // linear through the two boundary centres (ghost centre mirrored)
+            const T eg = (T)p.eg[2][pz < 0 ? 0 : 1];
+            for (int i = tid; i < K::PLANE; i += NT)
+                phi[s * K::PLANE + i] = fmaT(eg, phi[sb * K::PLANE + i] - phi[sa * K::PLANE + i], phi[sa * K::PLANE + i]);
+        } else {
+            for (int i = tid; i < K::PLANE; i += NT)
+                phi[s * K::PLANE + i] = ghost_value(phi[sa * K::PLANE + i], phi[sb * K::PLANE + i]);
+        }
     };
     auto plane = [&](int pz) __attribute__((always_inline)) {  // real or periodic planes only
         make_plane(pz);
@@ -361,23 +381,34 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
     auto zface = [&](int pl, int gfz, T *out) __attribute__((always_inline)) {
         if constexpr (D == 3) {
             const int sL = slot_of(pl), sR = slot_of(pl + 1);
-            T F[Q];
-            reconstruct<Q, 2, T>(cellp(sL, ly + 1, lx + 1), cellp(sR, ly + 1, lx + 1), cellp(sL, ly + 1, lx),
-                              cellp(sR, ly + 1, lx), cellp(sL, ly + 1, lx + 2), cellp(sR, ly + 1, lx + 2),
-                              cellp(sL, ly, lx + 1), cellp(sR, ly, lx + 1), cellp(sL, ly + 2, lx + 1),
-                              cellp(sR, ly + 2, lx + 1), cf.kappa, F);
             const int gx = min(x0 + lx, nx - 1), gy = min(y0 + ly, ny - 1);
+            // the interface between planes a and a + 1 (its index along z is a + 1)
+            auto recz = [&](int a, T *out) __attribute__((always_inline)) {
+                const int cL = slot_of(a), cR = slot_of(a + 1);
+                if constexpr (NU)
+                    reconstruct_nu<Q, 2, T>(cellp(cL, ly + 1, lx + 1), cellp(cR, ly + 1, lx + 1), cellp(cL, ly + 1, lx),
+                                            cellp(cR, ly + 1, lx), cellp(cL, ly + 1, lx + 2), cellp(cR, ly + 1, lx + 2),
+                                            cellp(cL, ly, lx + 1), cellp(cR, ly, lx + 1), cellp(cL, ly + 2, lx + 1),
+                                            cellp(cR, ly + 2, lx + 1), mwf(2, a + 1), mwf(0, gx), mwf(0, gx + 1),
+                                            mwf(1, gy), mwf(1, gy + 1), hc * midc(2, a + 1), hc * midx(0, gx),
+                                            hc * midx(1, gy), out);
+                else
+                    reconstruct<Q, 2, T>(cellp(cL, ly + 1, lx + 1), cellp(cR, ly + 1, lx + 1), cellp(cL, ly + 1, lx),
+                                         cellp(cR, ly + 1, lx), cellp(cL, ly + 1, lx + 2), cellp(cR, ly + 1, lx + 2),
+                                         cellp(cL, ly, lx + 1), cellp(cR, ly, lx + 1), cellp(cL, ly + 2, lx + 1),
+                                         cellp(cR, ly + 2, lx + 1), cf.kappa, out);
+            };
+            T F[Q];
+            (void)sL;
+            (void)sR;
+            recz(pl, F);
             T Gb[3];
             face_G(2, gx, gy, 0, gfz, Gb);
             const int wall = !perz && (gfz == 0 || gfz == nz);
             T Fc[Q], Gc[3] = {T(0), T(0), T(0)};
             if (wall) {
                 const int pc = gfz == 0 ? 0 : nz - 2;  // x_c between planes pc and pc+1
-                const int cL = slot_of(pc), cR = slot_of(pc + 1);
-                reconstruct<Q, 2, T>(cellp(cL, ly + 1, lx + 1), cellp(cR, ly + 1, lx + 1), cellp(cL, ly + 1, lx),
-                                  cellp(cR, ly + 1, lx), cellp(cL, ly + 1, lx + 2), cellp(cR, ly + 1, lx + 2),
-                                  cellp(cL, ly, lx + 1), cellp(cR, ly, lx + 1), cellp(cL, ly + 2, lx + 1),
-                                  cellp(cR, ly + 2, lx + 1), cf.kappa, Fc);
+                recz(pc, Fc);
                 face_G(2, gx, gy, 0, gfz == 0 ? 1 : nz - 1, Gc);
             }
             interface_f<Q, 2, T, ORIG>(p, cf, F, Gb, wall, gfz == 0 ? 0 : 1, Fc, Gc, out);
@@ -416,7 +447,9 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
             if constexpr (NU)
                 reconstruct_nu<Q, 0, T>(cellp(s, fy + 1, fx), cellp(s, fy + 1, fx + 1), cellp(s, fy, fx),
                                         cellp(s, fy, fx + 1), cellp(s, fy + 2, fx), cellp(s, fy + 2, fx + 1),
-                                        mwf(0, gfx), mwf(1, gy), mwf(1, gy + 1), hc * midc(0, gfx), hc * midx(1, gy), F);
+                                        cellp(sm, fy + 1, fx), cellp(sm, fy + 1, fx + 1), cellp(sp, fy + 1, fx),
+                                        cellp(sp, fy + 1, fx + 1), mwf(0, gfx), mwf(1, gy), mwf(1, gy + 1),
+                                        zw(kz), zw(kz + 1), hc * midc(0, gfx), hc * midx(1, gy), zhc(kz), F);
             else
                 reconstruct<Q, 0, T>(cellp(s, fy + 1, fx), cellp(s, fy + 1, fx + 1), cellp(s, fy, fx),
                                      cellp(s, fy, fx + 1), cellp(s, fy + 2, fx), cellp(s, fy + 2, fx + 1),
@@ -432,8 +465,9 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
                 if constexpr (NU)
                     reconstruct_nu<Q, 0, T>(cellp(s, fy + 1, cx), cellp(s, fy + 1, cx + 1), cellp(s, fy, cx),
                                             cellp(s, fy, cx + 1), cellp(s, fy + 2, cx), cellp(s, fy + 2, cx + 1),
-                                            mwf(0, gcx), mwf(1, gy), mwf(1, gy + 1), hc * midc(0, gcx),
-                                            hc * midx(1, gy), Fc);
+                                            cellp(sm, fy + 1, cx), cellp(sm, fy + 1, cx + 1), cellp(sp, fy + 1, cx),
+                                            cellp(sp, fy + 1, cx + 1), mwf(0, gcx), mwf(1, gy), mwf(1, gy + 1),
+                                            zw(kz), zw(kz + 1), hc * midc(0, gcx), hc * midx(1, gy), zhc(kz), Fc);
                 else
                     reconstruct<Q, 0, T>(cellp(s, fy + 1, cx), cellp(s, fy + 1, cx + 1), cellp(s, fy, cx),
                                          cellp(s, fy, cx + 1), cellp(s, fy + 2, cx), cellp(s, fy + 2, cx + 1),
@@ -452,7 +486,9 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
             if constexpr (NU)
                 reconstruct_nu<Q, 1, T>(cellp(s, fy, fx + 1), cellp(s, fy + 1, fx + 1), cellp(s, fy, fx),
                                         cellp(s, fy + 1, fx), cellp(s, fy, fx + 2), cellp(s, fy + 1, fx + 2),
-                                        mwf(1, gfy), mwf(0, gx), mwf(0, gx + 1), hc * midc(1, gfy), hc * midx(0, gx), F);
+                                        cellp(sm, fy, fx + 1), cellp(sm, fy + 1, fx + 1), cellp(sp, fy, fx + 1),
+                                        cellp(sp, fy + 1, fx + 1), mwf(1, gfy), mwf(0, gx), mwf(0, gx + 1),
+                                        zw(kz), zw(kz + 1), hc * midc(1, gfy), hc * midx(0, gx), zhc(kz), F);
             else
                 reconstruct<Q, 1, T>(cellp(s, fy, fx + 1), cellp(s, fy + 1, fx + 1), cellp(s, fy, fx),
                                      cellp(s, fy + 1, fx), cellp(s, fy, fx + 2), cellp(s, fy + 1, fx + 2),
@@ -468,8 +504,9 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
                 if constexpr (NU)
                     reconstruct_nu<Q, 1, T>(cellp(s, cy, fx + 1), cellp(s, cy + 1, fx + 1), cellp(s, cy, fx),
                                             cellp(s, cy + 1, fx), cellp(s, cy, fx + 2), cellp(s, cy + 1, fx + 2),
-                                            mwf(1, gcy), mwf(0, gx), mwf(0, gx + 1), hc * midc(1, gcy),
-                                            hc * midx(0, gx), Fc);
+                                            cellp(sm, cy, fx + 1), cellp(sm, cy + 1, fx + 1), cellp(sp, cy, fx + 1),
+                                            cellp(sp, cy + 1, fx + 1), mwf(1, gcy), mwf(0, gx), mwf(0, gx + 1),
+                                            zw(kz), zw(kz + 1), hc * midc(1, gcy), hc * midx(0, gx), zhc(kz), Fc);
                 else
                     reconstruct<Q, 1, T>(cellp(s, cy, fx + 1), cellp(s, cy + 1, fx + 1), cellp(s, cy, fx),
                                          cellp(s, cy + 1, fx), cellp(s, cy, fx + 2), cellp(s, cy + 1, fx + 2),
@@ -494,15 +531,19 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
             // non-uniform mesh: the flux of each axis is divided by the cell's width along it
             const T dcx = NU ? (T)(p.dt / p.inv_c) * midx(0, gx) : T(0);
             const T dcy = NU ? (T)(p.dt / p.inv_c) * midx(1, gy) : T(0);
+            const T dcz = (NU && D == 3) ? (T)(p.dt / p.inv_c) * midx(2, kz) : T(0);
             sfor<Q>([&](auto kc) {
                 constexpr int k = kc;
                 T acc = T(0);
                 if constexpr (NU) {
-                    T ax = T(0), ay = T(0);
+                    T ax = T(0), ay = T(0), az = T(0);
                     if constexpr (Lat<Q>::e(k, 0) != 0) ax = (T)Lat<Q>::e(k, 0) * (xp[flux_index<Q>(0, k)] - xm[flux_index<Q>(0, k)]);
                     if constexpr (Lat<Q>::e(k, 1) != 0) ay = (T)Lat<Q>::e(k, 1) * (yp[flux_index<Q>(1, k)] - ym[flux_index<Q>(1, k)]);
+                    if constexpr (D == 3 && Lat<Q>::e(k, 2) != 0) az = (T)Lat<Q>::e(k, 2) * (zf_hi[flux_index<Q>(2, k)] - zf_lo[flux_index<Q>(2, k)]);
                     const T gold = (T)Store<S>::ld(src + k * p.dstride + off);
-                    const T v = fmaT(T(1) / T(3), ph[k] - gold, ph[k]) - fmaT(dcx, ax, dcy * ay);
+                    // the flux of each axis divided by the cell's width along it
+                    const T v = fmaT(T(1) / T(3), ph[k] - gold, ph[k]) -
+                                (D == 3 ? fmaT(dcx, ax, fmaT(dcy, ay, dcz * az)) : fmaT(dcx, ax, dcy * ay));
                     store_state<S>(dst + k * p.dstride + off, v, sizeof(S) == 2 ? rnd.bits<k>() : 0u);
                     return;
                 }
@@ -543,7 +584,7 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
     }
 }
 
-// NU: a non-uniform 2D mesh (p.metric), D2Q9 only.
+// NU: a non-uniform mesh (p.metric: interface coordinates per axis, Sec. 3.4).
 template <int Q, class S, int TX, int TY, bool NU = false>
 __global__ void __launch_bounds__(TX *TY) fused_step(const __grid_constant__ StepParams p, int zchunk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];

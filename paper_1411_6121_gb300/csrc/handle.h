@@ -52,9 +52,9 @@ struct dugks_s {
     int use_graph, tile_x, tile_y;
     int kernel;            // 0: throughput kernel where built, 1: reference kernel
     int model;             // DUGKS_MODEL_*
-    double *d_metric;      // non-uniform 2D mesh metrics (device; NULL: uniform), see StepParams
-    double eg[2][2];       // its ghost extrapolation coefficients
-    int64_t metric_off1;   // offset of the y-axis block in d_metric
+    double *d_metric;      // non-uniform mesh metrics (device; NULL: uniform), see StepParams
+    double eg[3][2];       // its ghost extrapolation coefficients
+    int64_t metric_off[3]; // offset of each axis' block in d_metric
     int ry3d;              // CTA rows of the 3D throughput kernel
     int own_stream;
     size_t esize;          // bytes per stored element

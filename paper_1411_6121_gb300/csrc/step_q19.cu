@@ -2,9 +2,11 @@
 #include "dugks_internal.h"
 #include "dugks_step.cuh"
 
+#include <type_traits>
+
 namespace dugks {
 
-template <int TX, int TY, class S>
+template <int TX, int TY, class S, bool NU = false>
 static cudaError_t launch_tile(const StepParams &p, cudaStream_t stream) {
     using K = StepShape<19, TX, TY, typename Arith<S>::T>;
     if (K::smem_bytes > 227 * 1024) return cudaErrorNotSupported;
@@ -12,7 +14,7 @@ static cudaError_t launch_tile(const StepParams &p, cudaStream_t stream) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (configured_dev != dev) {
-        cudaError_t e = cudaFuncSetAttribute(fused_step<19, S, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(fused_step<19, S, TX, TY, NU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)K::smem_bytes);
         if (e != cudaSuccess) return e;
         configured_dev = dev;
@@ -32,12 +34,21 @@ static cudaError_t launch_tile(const StepParams &p, cudaStream_t stream) {
     const int zchunk = (p.nz + nchunks - 1) / nchunks;
     nchunks = (p.nz + zchunk - 1) / zchunk;
     dim3 grid((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, nchunks);
-    fused_step<19, S, TX, TY><<<grid, TX * TY, K::smem_bytes, stream>>>(p, zchunk);
+    fused_step<19, S, TX, TY, NU><<<grid, TX * TY, K::smem_bytes, stream>>>(p, zchunk);
     return cudaGetLastError();
 }
 
 template <class S>
 static cudaError_t launch_store(const StepParams &p, int tx, int ty, cudaStream_t stream) {
+    if constexpr (std::is_same<S, float>::value || std::is_same<S, double>::value) {
+        if (p.metric[0]) {  // non-uniform mesh (FP32 and FP64 storage)
+            if (tx == 32 && ty == 8) return launch_tile<32, 8, S, true>(p, stream);
+            if (tx == 16 && ty == 8) return launch_tile<16, 8, S, true>(p, stream);
+            return cudaErrorNotSupported;
+        }
+    } else {
+        if (p.metric[0]) return cudaErrorNotSupported;
+    }
     if (tx == 32 && ty == 8) return launch_tile<32, 8, S>(p, stream);
     if (tx == 16 && ty == 8) return launch_tile<16, 8, S>(p, stream);
     return cudaErrorNotSupported;

@@ -69,14 +69,17 @@ _TANH8 = np.array([0.0, 0.3, 0.9, 2.0, 4.0, 6.0, 7.1, 7.7, 8.0])  # 8 cells, wid
 
 
 @pytest.mark.parametrize("kw,code", [
-    # a non-uniform mesh (Sec. 3.4) is D2Q9 with F32 or F64 storage; its coordinates increase
-    (dict(dim=3, q=19, nz=4, dt=0.1, faces=[_TANH8]), -7),
-    (dict(dim=3, q=19, nz=8, dt=0.1, faces=[None, None, _TANH8]), -7),
+    # a non-uniform mesh (Sec. 3.4) takes F32 or F64 storage; its coordinates increase; a 2D
+    # mesh has no z coordinates
+    (dict(dim=3, q=19, nz=8, dt=0.1, store=1, faces=[None, None, _TANH8]), -7),
+    (dict(dim=3, q=27, nz=8, dt=0.1, faces=[None, None, _TANH8[::-1].copy()]), -1),
+    (dict(dt=0.1, faces=[None, None, _TANH8]), -1),
     (dict(store=1, dt=0.1, faces=[None, _TANH8]), -7),
     (dict(store=2, dt=0.1, faces=[_TANH8]), -7),
     (dict(dt=0.1, faces=[None, _TANH8[::-1].copy()]), -1),
-    # the CFL condition takes the smallest width: 0.3 / sqrt(3 RT) = 0.3
+    # the CFL condition takes the smallest width: 0.3 / sqrt(3 RT) = 0.3 (also along z)
     (dict(dt=0.31, faces=[None, _TANH8]), -2),
+    (dict(dim=3, q=19, nz=8, dt=0.31, faces=[None, None, _TANH8]), -2),
 ])
 def test_nonuniform_mesh_arguments_rejected(kw, code):
     rc, h, msg = _create(**kw)
