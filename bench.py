@@ -69,7 +69,8 @@ def hbm_peak():
 
 def kernel_source_hash():
     h = hashlib.sha1()
-    for name in ("dugks_step3d.cuh", "dugks_step.cuh", "dugks_device.cuh", "step3d_q19.cu"):
+    for name in ("dugks_step3d.cuh", "dugks_step3d_ws.cuh", "tma.cuh", "dugks_step.cuh", "dugks_device.cuh",
+                 "step3d_q19.cu"):
         with open(os.path.join(ROOT, "paper_1411_6121_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]
@@ -81,6 +82,8 @@ def kernel_name(store, rows):
     t = {0: "float", 1: "__nv_bfloat16", 2: "__half", 3: "double"}[store]
     if store == 3:
         return "fused_step<19,double,16,8>"
+    if not rows:  # the library default for D3Q19: the warp-specialised kernel
+        return "fused_step3d_ws<19,%s,false>" % t
     return "fused_step3d<19,%s,%d,false>" % (t, rows)
 
 
@@ -623,7 +626,7 @@ def main():
     achieved = alg_bytes / (ms_kernel * 1e-3) / 1e9
     traffic = profiled_traffic() if (N == 256 and args.store == 0) else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_source": peak_kind, "kernel": kernel_name(args.store, args.rows or 8),
+                "traffic": traffic, "peak_source": peak_kind, "kernel": kernel_name(args.store, args.rows),
                 "bytes_per_cell_update": 2 * Q * BYTES_PER_VALUE[args.store], "kernel_ms": ms_kernel}
     extras = {}
     if not args.no_extras and rank == 0:

@@ -91,6 +91,7 @@ StepParams dugks::handle_params(const dugks_t h) {
         p.bc_drho[w] = (h->bcs.face[w].p / h->rt);
         p.bc_drho1[w] = (h->bcs.face[w].p_amp / h->rt);
     }
+    finish_step_params(p);
     p.src = h->buf[h->cur];
     p.dst = h->buf[h->cur ^ 1];
     return p;
@@ -224,10 +225,11 @@ int dugks_create(const dugks_mesh *mesh, int32_t lattice, double nu, double dt, 
     const bool thr3d = o.kernel == 0 && (lattice == DUGKS_D3Q19 || lattice == DUGKS_D3Q27) && o.store != DUGKS_STORE_F64;
     const bool thr2d = o.kernel == 0 && lattice == DUGKS_D2Q9 && o.store != DUGKS_STORE_F64;
     int tx = o.tile_x, ty = o.tile_y;
-    int ry3d = 8;  // CTA rows of the throughput kernels
+    int ry3d = 8;  // CTA rows of the throughput kernels (D3Q19: 0 selects the warp-specialised one)
     if (thr3d) {
         if (ty != 0) ry3d = ty;
-        if (!(ry3d == 8 || (ry3d == 10 && lattice == DUGKS_D3Q19)))
+        else if (lattice == DUGKS_D3Q19) ry3d = 0;
+        if (!(ry3d == 8 || (lattice == DUGKS_D3Q19 && (ry3d == 10 || ry3d == 0))))
             return handle_fail(NULL, DUGKS_E_UNSUPPORTED, "3D kernel rows %d not built", ry3d);
         tx = 32;
         ty = 8;

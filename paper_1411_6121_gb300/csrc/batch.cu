@@ -153,6 +153,7 @@ StepParams instance_params(const dugks_batch_t b, int i, int parity) {
         p.bc_drho[w] = b->bcs[i].face[w].p / b->rt;
         p.bc_drho1[w] = b->bcs[i].face[w].p_amp / b->rt;
     }
+    finish_step_params(p);
     const char *b0 = static_cast<const char *>(b->buf[parity]) + b->off[i] * b->esize;
     char *b1 = static_cast<char *>(b->buf[parity ^ 1]) + b->off[i] * b->esize;
     p.src = b0;

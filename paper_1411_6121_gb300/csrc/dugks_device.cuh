@@ -245,19 +245,49 @@ struct StepParams {
     double bc_u[6][3];         // wall velocity
     double bc_drho[6];         // pressure condition: rho_a - rho0 = p_w / RT
     double bc_drho1[6];        // its oscillating part: + bc_drho1 cos(omega t)
+    // The same wall data and acceleration rounded once to FP32 on the host
+    // (finish_step_params), for the FP32 kernels: GB300's FP64 rate is a small fraction of its
+    // FP32 rate, so no FP64 operation is left on their per-interface paths. Each is the FP32
+    // rounding of the FP64 value the FP64 kernels use.
+    float fwm[6][3];           // rho0 u_w / c
+    float fwu[6][3];           // u_w / c
+    float fdrho[6], fdrho1[6]; // bc_drho, bc_drho1
+    float fg[3];               // g
+    float fcoef[11];           // rho0, 1/rho0, 1/c, b1, c1, b7, c7, kappa, two_kappa, wcell, wface
     const void *src;
     void *dst;
 };
+
+// Fills the FP32 copies above from the FP64 fields (host).
+inline void finish_step_params(StepParams &p) {
+    for (int w = 0; w < 6; w++) {
+        for (int a = 0; a < 3; a++) {
+            p.fwm[w][a] = (float)(p.bc_u[w][a] * p.rho0 * p.inv_c);
+            p.fwu[w][a] = (float)(p.bc_u[w][a] * p.inv_c);
+        }
+        p.fdrho[w] = (float)p.bc_drho[w];
+        p.fdrho1[w] = (float)p.bc_drho1[w];
+    }
+    for (int a = 0; a < 3; a++) p.fg[a] = (float)p.g[a];
+    const double c[11] = {p.rho0, 1.0 / p.rho0, p.inv_c, p.b1, p.c1, p.b7, p.c7, p.kappa, p.two_kappa, p.wcell, p.wface};
+    for (int i = 0; i < 11; i++) p.fcoef[i] = (float)c[i];
+}
 
 // Coefficients in the arithmetic type T.
 template <class T>
 struct Coef {
     T rho0, inv_rho0, inv_c, b1, c1, b7, c7, kappa, two_kappa, wcell, wface;
     T cwh;  // cos(omega (t_n + h)): the time factor of an oscillating wall pressure
-    __device__ __forceinline__ explicit Coef(const StepParams &p)
-        : rho0((T)p.rho0), inv_rho0((T)(1.0 / p.rho0)), inv_c((T)p.inv_c), b1((T)p.b1), c1((T)p.c1), b7((T)p.b7),
-          c7((T)p.c7), kappa((T)p.kappa), two_kappa((T)p.two_kappa), wcell((T)p.wcell), wface((T)p.wface),
-          cwh(T(1)) {
+    __device__ __forceinline__ explicit Coef(const StepParams &p) : cwh(T(1)) {
+        if constexpr (sizeof(T) == 4) {  // rounded on the host (finish_step_params)
+            rho0 = p.fcoef[0]; inv_rho0 = p.fcoef[1]; inv_c = p.fcoef[2]; b1 = p.fcoef[3]; c1 = p.fcoef[4];
+            b7 = p.fcoef[5]; c7 = p.fcoef[6]; kappa = p.fcoef[7]; two_kappa = p.fcoef[8]; wcell = p.fcoef[9];
+            wface = p.fcoef[10];
+        } else {
+            rho0 = (T)p.rho0; inv_rho0 = (T)(1.0 / p.rho0); inv_c = (T)p.inv_c; b1 = (T)p.b1; c1 = (T)p.c1;
+            b7 = (T)p.b7; c7 = (T)p.c7; kappa = (T)p.kappa; two_kappa = (T)p.two_kappa; wcell = (T)p.wcell;
+            wface = (T)p.wface;
+        }
         if (p.omega != 0.0)
             cwh = (T)cos(p.omega * (((double)(*p.step_ctr) + (double)p.step_off) * p.dt + 0.5 * p.dt));
     }

@@ -66,7 +66,8 @@ __device__ __forceinline__ void reconstruct(const T *L, const T *R, const T *L1m
 // cf.cwh holds the cosine).
 template <class T>
 __device__ __forceinline__ T wall_drho(const StepParams &p, const Coef<T> &cf, int wid) {
-    return (T)p.bc_drho[wid] + (T)p.bc_drho1[wid] * cf.cwh;
+    if constexpr (sizeof(T) == 4) return p.fdrho[wid] + p.fdrho1[wid] * cf.cwh;
+    else return (T)p.bc_drho[wid] + (T)p.bc_drho1[wid] * cf.cwh;
 }
 
 // Steps 3-4 on a non-uniform mesh (Sec. 3.4, the same reading as the oracle): the interface
@@ -135,7 +136,7 @@ __device__ __forceinline__ void interface_f(const StepParams &p, const Coef<T> &
         const int wid = 2 * d + side;
         T mw[3];
 #pragma unroll
-        for (int a = 0; a < 3; a++) mw[a] = (T)(p.bc_u[wid][a] * p.rho0 * p.inv_c);
+        for (int a = 0; a < 3; a++) mw[a] = sizeof(T) == 4 ? (T)p.fwm[wid][a] : (T)(p.bc_u[wid][a] * p.rho0 * p.inv_c);
         const int sgn = side == 0 ? -1 : 1;
         sfor<Q>([&](auto kc) {
             constexpr int k = kc;
@@ -162,10 +163,20 @@ __device__ __forceinline__ void interface_f(const StepParams &p, const Coef<T> &
         if (p.bc[wid] == 1) {  // velocity condition: u_a = u_w, rho_a = rho_c
             dra = drc;
             // m = rho u / c: rho0 u_w / c, or rho_a u_w / c in the original model
-            const double ra = (ORIG && p.model == 1) ? p.rho0 + (double)drc : p.rho0;
-            ma[0] = (T)(p.bc_u[wid][0] * ra * p.inv_c);
-            ma[1] = (T)(p.bc_u[wid][1] * ra * p.inv_c);
-            ma[2] = (T)(p.bc_u[wid][2] * ra * p.inv_c);
+            if (ORIG && p.model == 1) {
+                const double ra = p.rho0 + (double)drc;
+                ma[0] = (T)(p.bc_u[wid][0] * ra * p.inv_c);
+                ma[1] = (T)(p.bc_u[wid][1] * ra * p.inv_c);
+                ma[2] = (T)(p.bc_u[wid][2] * ra * p.inv_c);
+            } else if constexpr (sizeof(T) == 4) {
+                ma[0] = p.fwm[wid][0];
+                ma[1] = p.fwm[wid][1];
+                ma[2] = p.fwm[wid][2];
+            } else {
+                ma[0] = (T)(p.bc_u[wid][0] * p.rho0 * p.inv_c);
+                ma[1] = (T)(p.bc_u[wid][1] * p.rho0 * p.inv_c);
+                ma[2] = (T)(p.bc_u[wid][2] * p.rho0 * p.inv_c);
+            }
         } else {               // pressure condition: rho_a = rho0 + p_w/RT, u_a = u_c
             dra = wall_drho<T>(p, cf, wid);
             // m_a = rho0 u_c / c = m_c, or rho_a u_c / c = m_c rho_a / rho_c (original model)
@@ -203,7 +214,7 @@ template <int D, class T>
 __device__ __forceinline__ void cell_G(const StepParams &p, int64_t cell, int64_t ncell, T ct_over_c, T G[3]) {
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        T v = (a < D) ? (T)p.g[a] : T(0);
+        T v = (a < D) ? (sizeof(T) == 4 ? (T)p.fg[a] : (T)p.g[a]) : T(0);
         if (p.field && a < D) v += (T)__ldg(p.field + a * ncell + cell);
         G[a] = v * ct_over_c;
     }
@@ -368,7 +379,7 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
         const T wh = (NU && lo != hi) ? mwf(d, gfd) : T(0.5);
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            T v = (a < D) ? (T)p.g[a] : T(0);
+            T v = (a < D) ? (sizeof(T) == 4 ? (T)p.fg[a] : (T)p.g[a]) : T(0);
             if (p.field && a < D) {
                 const T fl = (T)__ldg(p.field + a * ncell + il), fh = (T)__ldg(p.field + a * ncell + ih);
                 v += NU ? fmaT(wh, fh - fl, fl) : T(0.5) * (fl + fh);

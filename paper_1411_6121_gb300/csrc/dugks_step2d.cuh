@@ -181,7 +181,7 @@ __device__ __forceinline__ void step2d_tile(const StepParams &p, unsigned char *
 
     uint32_t seed = 0;  // stochastic rounding of 16-bit stores
     if constexpr (sizeof(S) == 2) seed = store_seed(*p.step_ctr + p.step_off);
-    float ct = (float)p.inv_c, cth = (float)p.inv_c;
+    float ct = p.fcoef[2], cth = p.fcoef[2];
     if (FORCE && p.omega != 0.0) {
         const double tn = ((double)(*p.step_ctr) + (double)p.step_off) * p.dt;
         ct = (float)(cos(p.omega * tn) * p.inv_c);
@@ -200,7 +200,7 @@ __device__ __forceinline__ void step2d_tile(const StepParams &p, unsigned char *
         const int64_t il = (int64_t)lo[0] + (int64_t)nx * lo[1], ih = (int64_t)hi[0] + (int64_t)nx * hi[1];
 #pragma unroll
         for (int a = 0; a < 2; a++) {
-            float v = (float)p.g[a];
+            float v = p.fg[a];
             if (p.field) v += 0.5f * (__ldg(p.field + a * ncell + il) + __ldg(p.field + a * ncell + ih));
             Gh[a] = v * cth;
         }

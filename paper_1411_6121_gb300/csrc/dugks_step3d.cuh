@@ -226,7 +226,7 @@ __device__ __forceinline__ void neq_wall(const StepParams &p, const Coef<float> 
         // interface's own values
         float mw[3];
 #pragma unroll
-        for (int a = 0; a < 3; a++) mw[a] = (float)(p.bc_u[wid][a] * p.rho0 * p.inv_c);
+        for (int a = 0; a < 3; a++) mw[a] = p.fwm[wid][a];
         sfor<Q>([&](auto kc) {
             constexpr int k = kc;
             constexpr int ed = Lat<Q>::e(k, d);
@@ -258,7 +258,7 @@ __device__ __forceinline__ void neq_wall(const StepParams &p, const Coef<float> 
     if (p.bc[wid] == 1) {  // velocity condition: u_a = u_w, rho_a = rho_c
         dra = drc;
 #pragma unroll
-        for (int a = 0; a < 3; a++) ma[a] = (float)(p.bc_u[wid][a] * p.rho0 * p.inv_c);
+        for (int a = 0; a < 3; a++) ma[a] = p.fwm[wid][a];
     } else {  // pressure condition: rho_a = rho0 + p_w / RT, u_a = u_c
         dra = wall_drho<float>(p, cf, wid);
 #pragma unroll
@@ -364,7 +364,7 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, const CUtens
 
     uint32_t seed = 0;  // stochastic rounding of 16-bit stores
     if constexpr (sizeof(S) == 2) seed = store_seed(*p.step_ctr + p.step_off);
-    float ct = (float)p.inv_c, cth = (float)p.inv_c;
+    float ct = p.fcoef[2], cth = p.fcoef[2];
     if (FORCE && p.omega != 0.0) {
         const double tn = ((double)(*p.step_ctr) + (double)p.step_off) * p.dt;
         ct = (float)(cos(p.omega * tn) * p.inv_c);
@@ -389,7 +389,7 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, const CUtens
         const int64_t ih = (int64_t)hi[0] + (int64_t)nx * ((int64_t)hi[1] + (int64_t)ny * hi[2]);
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            float v = (float)p.g[a];
+            float v = p.fg[a];
             if (p.field) v += 0.5f * (__ldg(p.field + a * ncell + il) + __ldg(p.field + a * ncell + ih));
             Gh[a] = v * cth;
         }

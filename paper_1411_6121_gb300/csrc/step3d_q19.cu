@@ -6,6 +6,7 @@
 
 #include "dugks_internal.h"
 #include "dugks_step3d.cuh"
+#include "dugks_step3d_ws.cuh"
 
 namespace dugks {
 
@@ -102,8 +103,55 @@ static cudaError_t launch_ry(const StepParams &p, cudaStream_t stream) {
     return cudaGetLastError();
 }
 
+// z chunks per tile column for one CTA per SM: maximise (useful waves / launched waves) /
+// (1 + 2 / chunk length) (each chunk makes two extra planes of fbar+ in its prologue).
+static int zchunk_for(int64_t tiles, int nz, int64_t slots) {
+    int best = 1;
+    double best_eff = -1.0;
+    for (int nc = 1; nc <= 16; nc++) {
+        const int zc = (nz + nc - 1) / nc;
+        if (nc > 1 && zc < 8) break;
+        const int ncr = (nz + zc - 1) / zc;
+        const double waves = (double)(tiles * ncr) / (double)slots;
+        const double eff = waves / ceil(waves) / (1.0 + 2.0 / zc);
+        if (eff > best_eff + 1e-9) { best_eff = eff; best = nc; }
+    }
+    return (nz + best - 1) / best;
+}
+
+// The warp-specialised kernel (dugks_step3d_ws.cuh): 4 producer + 8 consumer warps, one CTA
+// per SM, 32 x 8 columns per tile.
+template <class S, bool FORCE>
+static cudaError_t launch_ws(const StepParams &p, cudaStream_t stream) {
+    using K = ShapeWS<19, S>;
+    static int configured_dev = -1;
+    static int sms = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (configured_dev != dev) {
+        cudaError_t e = cudaFuncSetAttribute(fused_step3d_ws<19, S, FORCE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)K::smem_bytes);
+        if (e != cudaSuccess) return e;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        configured_dev = dev;
+    }
+    const int tiles_x = (p.nx + K::TXI - 1) / K::TXI;
+    const int tiles_y = (p.ny + K::TYI - 1) / K::TYI;
+    const int zchunk = zchunk_for((int64_t)tiles_x * tiles_y, p.nz, sms);
+    const int nchunks = (p.nz + zchunk - 1) / zchunk;
+    CUtensorMap map;
+    memset(&map, 0, sizeof map);
+    const cudaError_t e = encode_state_map(&map, p.src, (int)sizeof(S), std::is_same<S, __nv_bfloat16>::value, p.px,
+                                           p.ny, p.nz, 19, K::BX, K::RY);
+    if (e != cudaSuccess) return e;
+    fused_step3d_ws<19, S, FORCE><<<dim3(tiles_x, tiles_y, nchunks), K::NTHREADS, K::smem_bytes, stream>>>(p, map,
+                                                                                                          zchunk);
+    return cudaGetLastError();
+}
+
 template <class S>
 static cudaError_t launch_s(const StepParams &p, int ry, bool force, cudaStream_t stream) {
+    if (ry == 0) return force ? launch_ws<S, true>(p, stream) : launch_ws<S, false>(p, stream);
     if (ry == 10) return force ? launch_ry<10, S, true>(p, stream) : launch_ry<10, S, false>(p, stream);
     if (ry == 8) return force ? launch_ry<8, S, true>(p, stream) : launch_ry<8, S, false>(p, stream);
     return cudaErrorNotSupported;

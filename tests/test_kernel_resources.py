@@ -1,7 +1,8 @@
 """Register and spill budgets of the hot kernels, read from ptxas's resource report of the
 sm_103a build (no GPU needed). Each budget is what a measured speed depends on:
   * the D3Q19 throughput kernel runs one 256-thread CTA per SM at <= 255 registers and must not
-    spill (its z march keeps the carried differences in registers);
+    spill (its z march keeps the carried differences in registers); the warp-specialised one
+    launches 512 threads at 128 registers and must not spill under its register split;
   * the batch's FP32 reference tiles run 4 CTAs of 256 threads (8 of 128) per SM only at
     <= 64 registers; 72 registers cost the 64-channel batch 15%;
   * the D2Q9 throughput kernel (FP32) must not spill.
@@ -24,6 +25,13 @@ def _find(res, *parts):
     hits = {k: v for k, v in res.items() if all(p in k for p in parts)}
     assert hits, parts
     return hits
+
+
+def test_d3q19_warp_specialised_kernel_does_not_spill(res):
+    # fused_step3d_ws<19, S, false> (the benchmark's force-free instantiation) under its register
+    # split of 72 (producers) / 184 (consumers) registers
+    for k, v in _find(res, "fused_step3d_wsILi19E", "Lb0E").items():
+        assert v["regs"] == 128 and v["spill_stores"] == 0, (k, v)
 
 
 def test_d3q19_throughput_kernel_does_not_spill(res):
