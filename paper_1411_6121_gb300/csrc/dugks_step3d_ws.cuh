@@ -515,6 +515,37 @@ __global__ void __launch_bounds__(512, 1)
 #pragma unroll
             for (int i = 0; i < 4; i++) b[NF + i] = By[i];
         }
+        // ---- P2: z parts of plane kz+1 and the z interface kz+1/2, before the first consumer
+        //      barrier: they need nothing from the y exchange, so the x interfaces, the y parts
+        //      and the z interface form one barrier-free phase of independent chains ----
+        float alzn[NF], Azn[4], fzp[NF];
+        if (xrow) {
+            cdiff(kz + 1, AX, cAX);
+            cdiff(kz + 1, AY, cAY);
+            mdiff(kz + 1, AX, mAX);
+            mdiff(kz + 1, AY, mAY);
+        }
+        if (upd) {
+            float bezn[NF], Bzn[4];
+            const float *nxt = R(slot_of(kz + 1), row, lane);
+            face_parts<Q, 2>(nxt, nxt + Q, cAX, cAY, mAX, mAY, cf.kappa, alzn, bezn, Azn, Bzn);
+            if (!perz && kz + 1 == nz) {
+                float t[NF];
+                direct_face(2, kz, kz + 1, t);
+#pragma unroll
+                for (int i = 0; i < NF; i++) fzp[i] = t[i];
+            } else {
+                float F[NF], jb[3];
+#pragma unroll
+                for (int i = 0; i < NF; i++) F[i] = alz[i] + bezn[i];
+#pragma unroll
+                for (int a = 0; a < 3; a++) jb[a] = Az[1 + a] + Bzn[1 + a];
+                float Gb[3] = {0.0f, 0.0f, 0.0f};
+                if (FORCE) faceG(2, gx, gy, kz + 1, Gb);
+                face_relax<Q, 2, FORCE>(cf, F, Az[0] + Bzn[0], jb, Gb, fzp);
+            }
+        }
+
         // consumer barrier; a wait that gave up makes every consumer leave together
         if (cons_bar_or(!ok)) {
             release(kz - 1);
@@ -543,35 +574,6 @@ __global__ void __launch_bounds__(512, 1)
             for (int i = 0; i < NF; i++) o[i] = fyp[i];
         }
         cons_bar();
-
-        // ---- P2: z parts of plane kz+1 and the z interface kz+1/2 ----
-        float alzn[NF], Azn[4], fzp[NF];
-        if (xrow) {
-            cdiff(kz + 1, AX, cAX);
-            cdiff(kz + 1, AY, cAY);
-            mdiff(kz + 1, AX, mAX);
-            mdiff(kz + 1, AY, mAY);
-        }
-        if (upd) {
-            float bezn[NF], Bzn[4];
-            const float *nxt = R(slot_of(kz + 1), row, lane);
-            face_parts<Q, 2>(nxt, nxt + Q, cAX, cAY, mAX, mAY, cf.kappa, alzn, bezn, Azn, Bzn);
-            if (!perz && kz + 1 == nz) {
-                float t[NF];
-                direct_face(2, kz, kz + 1, t);
-#pragma unroll
-                for (int i = 0; i < NF; i++) fzp[i] = t[i];
-            } else {
-                float F[NF], jb[3];
-#pragma unroll
-                for (int i = 0; i < NF; i++) F[i] = alz[i] + bezn[i];
-#pragma unroll
-                for (int a = 0; a < 3; a++) jb[a] = Az[1 + a] + Bzn[1 + a];
-                float Gb[3] = {0.0f, 0.0f, 0.0f};
-                if (FORCE) faceG(2, gx, gy, kz + 1, Gb);
-                face_relax<Q, 2, FORCE>(cf, F, Az[0] + Bzn[0], jb, Gb, fzp);
-            }
-        }
 
         // ---- P5: steps 8-9, update of cell (gx, gy, kz) ----
         float fxm[NF];
