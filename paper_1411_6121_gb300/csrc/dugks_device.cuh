@@ -168,6 +168,9 @@ struct CellRandom {
         const uint32_t h = mix32(base + (uint32_t)(k >> 1));
         return (k & 1) ? (h >> 16) : h;
     }
+    // the whole word of velocities 2 i and 2 i + 1
+    template <int i>
+    __device__ __forceinline__ uint32_t word() const { return mix32(base + (uint32_t)i); }
 };
 
 // Stores a state value: round to nearest for FP32/FP64; stochastic rounding for BF16 and
@@ -183,6 +186,44 @@ __device__ __forceinline__ void store_state(S *p, typename std::conditional<size
         *p = __float2half_rz(__uint_as_float(__float_as_uint(v * F16_SCALE) + (r & 0x1fffu)));
     } else {
         Store<S>::st(p, v);
+    }
+}
+
+// Stores two state values, v0 at p0 and v1 at p1 (usually two velocities of one cell). For BF16
+// and FP16 one hardware conversion rounds both stochastically (cvt.rs.satfinite.{bf16,f16}x2:
+// the random bits r[31:16] round v0 and r[15:0] round v1, up with probability equal to the
+// discarded fraction); FP16 holds the value times 2^12 (its normal range then spans
+// [1.5e-8, 16], which the state never leaves). FP32 stores round to nearest.
+template <class S>
+__device__ __forceinline__ void store_state_pair(S *p0, float v0, S *p1, float v1, uint32_t r) {
+    if constexpr (std::is_same<S, __nv_bfloat16>::value) {
+        uint32_t d;
+        asm("cvt.rs.satfinite.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(v0), "f"(v1), "r"(r));
+        *p0 = __ushort_as_bfloat16((unsigned short)(d >> 16));
+        *p1 = __ushort_as_bfloat16((unsigned short)(d & 0xffffu));
+    } else if constexpr (std::is_same<S, __half>::value) {
+        uint32_t d;
+        asm("cvt.rs.satfinite.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(v0 * F16_SCALE), "f"(v1 * F16_SCALE), "r"(r));
+        *p0 = __ushort_as_half((unsigned short)(d >> 16));
+        *p1 = __ushort_as_half((unsigned short)(d & 0xffffu));
+    } else {
+        *p0 = v0;
+        *p1 = v1;
+    }
+}
+// The same for one value (the rounding takes r[31:16]).
+template <class S>
+__device__ __forceinline__ void store_state_one(S *p0, float v0, uint32_t r) {
+    if constexpr (std::is_same<S, __nv_bfloat16>::value) {
+        uint32_t d;
+        asm("cvt.rs.satfinite.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(v0), "f"(0.0f), "r"(r));
+        *p0 = __ushort_as_bfloat16((unsigned short)(d >> 16));
+    } else if constexpr (std::is_same<S, __half>::value) {
+        uint32_t d;
+        asm("cvt.rs.satfinite.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(v0 * F16_SCALE), "f"(0.0f), "r"(r));
+        *p0 = __ushort_as_half((unsigned short)(d >> 16));
+    } else {
+        *p0 = v0;
     }
 }
 

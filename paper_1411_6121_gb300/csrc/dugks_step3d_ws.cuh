@@ -586,6 +586,7 @@ __global__ void __launch_bounds__(512, 1)
             const float *u0 = U(kz);
             const int64_t off = (int64_t)kz * p.plane + (int64_t)gy * p.px + gx;
             const CellRandom rnd(seed, off);
+            float v[Q];
             sfor<Q>([&](auto kc) {
                 constexpr int k = kc;
                 float acc = 0.0f;
@@ -602,9 +603,16 @@ __global__ void __launch_bounds__(512, 1)
                     acc = fmaf((float)Lat<Q>::e(k, 2), fzp[i] - fzm[i], acc);
                 }
                 // eq. evolution_equation: f~(t+dt) = f~+ - dt/|V| flux
-                store_state<S>(dst + k * p.dstride + off, fmaf(-cf.two_kappa, acc, u0[k]),
-                               sizeof(S) == 2 ? rnd.bits<k>() : 0u);
+                v[k] = fmaf(-cf.two_kappa, acc, u0[k]);
             });
+            // velocities 2i and 2i+1 share one random word and one rounding instruction
+            sfor<Q / 2>([&](auto ic) {
+                constexpr int i = ic;
+                store_state_pair<S>(dst + (2 * i) * p.dstride + off, v[2 * i], dst + (2 * i + 1) * p.dstride + off,
+                                    v[2 * i + 1], sizeof(S) == 2 ? rnd.word<i>() : 0u);
+            });
+            if constexpr (Q % 2 == 1)
+                store_state_one<S>(dst + (Q - 1) * p.dstride + off, v[Q - 1], sizeof(S) == 2 ? rnd.word<Q / 2>() : 0u);
 #pragma unroll
             for (int i = 0; i < NF; i++) { fzm[i] = fzp[i]; alz[i] = alzn[i]; }
 #pragma unroll

@@ -411,9 +411,9 @@ def test_16bit_storage_does_not_stagnate():
     FP16 unit in the last place of the values around it: rounded to nearest, FP16 storage
     would lose the increment every step. With stochastic rounding the steady Poiseuille
     profile is reached: velocity within 1e-3 (F16) / 1e-2 (BF16) of the oracle, and for F16
-    the error against the analytic parabola G y (H - y) / (2 nu) within 10% of the FP32 run's.
-    BF16's storage noise (~5e-3 of the velocity) is as large as the discretisation error
-    itself (4.3e-3), so its analytic error is not banded."""
+    the error against the analytic parabola G y (H - y) / (2 nu) within 5% of the FP32 run's for
+    both formats (measured F16 +2.7%, BF16 -3.1%: BF16's storage noise, ~5e-3 of the velocity, is
+    as large as the discretisation error itself, 4.3e-3, but unbiased)."""
     cfg = dict(shape=(8, 32), q=9, nu=0.1, dt=0.5, g=(1e-4, 0.0, 0.0), bcs=W.channel_bcs(2))
     steps, H = 40000, 32
     o = Oracle(**cfg)
@@ -432,7 +432,7 @@ def test_16bit_storage_does_not_stagnate():
         return m, np.linalg.norm(ux - ua) / np.linalg.norm(ua)
 
     _, e32 = run(0)
-    for store, tol, band in ((2, 1e-3, 0.10), (1, 1e-2, None)):
+    for store, tol, band in ((2, 1e-3, 0.05), (1, 1e-2, 0.05)):
         m, e = run(store)
         assert rel_l2(m[1:], ref[1:]) < tol, (store, rel_l2(m[1:], ref[1:]))
         if band is not None:
