@@ -6,11 +6,14 @@
 //  * Producer warps (8, one cell column each) make step 1 for plane kz + 2 and
 //    beyond: the state of the tile's plane arrives by TMA into one shared-memory stage, each
 //    column forms fbar+, its moments and u0 = fbar+ + (fbar+ - f~)/3, then the ghost
-//    columns and rows (step 2) and, beyond non-periodic z walls, the ghost planes.
+//    columns and rows (step 2) and, beyond non-periodic z walls, the ghost planes. Having made
+//    plane p they form the x interfaces of plane p - 1 (steps 3-7), which need its x and y
+//    neighbours and their own column of planes p - 2 and p.
 //  * Consumer warps (8, one cell column each, the 32 x 8 layout of the non-specialised kernel)
-//    do steps 3-9 for plane kz: the per-cell interface parts, the x, y and z interfaces and the
-//    update, as dugks_step3d.cuh does them.
-//  * The planes pass through a ring of four slots (fbar+ and moments) and three u0 slots. Each
+//    do the rest of steps 3-9 for plane kz: the y and z interfaces and the update, as
+//    dugks_step3d.cuh does them. The split puts about as much work on each group.
+//  * The planes pass through a ring of four slots (fbar+ and moments), three u0 slots and two
+//    slots of f at the x interfaces. Each
 //    ring slot has a "full" mbarrier (every producer thread arrives after its last write of the
 //    plane) and an "empty" one (every consumer thread arrives after its last read), so neither
 //    group waits on a CTA-wide barrier: the producer runs up to two planes ahead and the
@@ -27,8 +30,8 @@
 // accesses free of bank conflicts.
 //
 // The 512 threads launch with 128 registers each; the producer warpgroups then give registers
-// back (setmaxnreg to PROD_REGS) and the consumer warpgroups take them (CONS_REGS): 256 x 72 +
-// 256 x 184 = 512 x 128. Every wait on an mbarrier gives up after about two seconds (a device
+// back (setmaxnreg to PROD_REGS) and the consumer warpgroups take them (CONS_REGS): 256 x 96 +
+// 256 x 160 = 512 x 128. Every wait on an mbarrier gives up after about two seconds (a device
 // flag, then the group leaves together; see tma.cuh).
 #pragma once
 
@@ -96,7 +99,7 @@ struct ShapeWS {
     static_assert(Q == 19, "the warp-specialised kernel is written for D3Q19");
     static constexpr int RX = 32, RY = 8, NC = RX * RY;  // cell columns of the tile, halo included
     static constexpr int NPROD = NC, NCONS = NC, NTHREADS = NPROD + NCONS;
-    static constexpr int PROD_REGS = 72, CONS_REGS = 184;
+    static constexpr int PROD_REGS = 96, CONS_REGS = 160;
     static_assert(NPROD * PROD_REGS + NCONS * CONS_REGS <= NTHREADS * 128, "register split above the launch's");
     static constexpr int TXI = RX - 2, TYI = RY - 2;  // inner columns
     static constexpr int CS = pr::CS;                 // ring floats per cell
@@ -106,9 +109,11 @@ struct ShapeWS {
     static constexpr int NSLOT = 4, NU0 = 3;
     static constexpr int NUC = TYI * RX;              // columns that update (rows 1 .. TYI)
     static constexpr int PLANE = RY * RX * CS;
-    // ring; beta_y of rows 1..RY-1; f_y of rows 0..RY-2; u0 pairs and rest of rows 1..TYI
+    // ring; beta_y of rows 1..RY-1; f_y of rows 0..RY-2; u0 pairs and rest of rows 1..TYI; f pairs
+    // at +x of rows 1..TYI for two planes
     static constexpr size_t FLOATS = (size_t)NSLOT * PLANE + (size_t)(RY - 1) * RX * BS +
-                                     (size_t)(RY - 1) * RX * FS + (size_t)NU0 * NUC * UP + (size_t)NU0 * NUC;
+                                     (size_t)(RY - 1) * RX * FS + (size_t)NU0 * NUC * UP + (size_t)NU0 * NUC +
+                                     (size_t)2 * NUC * FS;
     static_assert(FLOATS % 2 == 0 && PLANE % 2 == 0 && NUC % 2 == 0, "float2 arrays must stay 8-byte aligned");
     static constexpr int BX = 32 + (sizeof(S) == 4 ? 4 : 8);  // TMA box width (start rounded down)
     static constexpr size_t STAGE_BYTES = (size_t)Q * RY * BX * sizeof(S);
@@ -376,6 +381,7 @@ __global__ void __launch_bounds__(512, 1)
     float *xf = xb + (RY - 1) * 32 * K::BS;            // [rows 0..RY-2][32][FS]: f pairs at +y
     float *u0b = xf + (RY - 1) * 32 * K::FS;           // [NU0][rows 1..TYI][32][UP]
     float *u0r = u0b + K::NU0 * K::NUC * K::UP;        // [NU0][rows 1..TYI][32]: rest velocity
+    float *fxb = u0r + K::NU0 * K::NUC;                // [2][rows 1..TYI][32][FS]: f pairs at +x
     unsigned char *stage = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw + K::STAGE_OFF) + 127) & ~(uintptr_t)127);
     uint64_t *full = reinterpret_cast<uint64_t *>(stage + K::BAR_OFF);
@@ -416,186 +422,16 @@ __global__ void __launch_bounds__(512, 1)
     const bool xwall_tile = !perx && (x0 == 0 || x0 + K::TXI >= nx);
     const bool ywall_tile = !pery && (y0 == 0 || y0 + K::TYI >= ny);
 
-    if (tid < K::NPROD) {
-        // =============================== producer ===============================
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(K::PROD_REGS));
-        // real planes first .. lastp are copied in order into the one stage (phase m & 1 for the
-        // m-th); thread 0 issues the next copy once every producer thread has read the stage
-        const int first = (!perz && z0 - 1 < 0) ? z0 : z0 - 1;
-        const int lastp = (!perz && z1 >= nz) ? nz - 1 : z1;
-        constexpr int XA = 16 / (int)sizeof(S);
-        const int xs = (x0 - 1 >= 0) ? (x0 - 1) / XA * XA : -XA;
-        auto issue = [&](int pz) __attribute__((always_inline)) {
-            if (tid == 0 && pz >= first && pz <= lastp) {
-                mbar_arrive_expect_tx(sbar, (uint32_t)K::STAGE_BYTES);
-                tma_load_4d(stage, &tmap, sbar, xs, y0 - 1, wrap_idx(pz, nz), 0);
-            }
-        };
-        bool ok = true;
-        issue(first);
-        // the column of this thread
-        const int lane = tid & 31, row = tid >> 5;
-        const int gx = x0 - 1 + lane, gy = y0 - 1 + row;
-        int cx = gx, cy = gy;
-        bool load = true;
-        if (gx < 0 || gx >= nx) { if (perx && gx >= -1 && gx <= nx) cx = wrap_idx(gx, nx); else load = false; }
-        if (gy < 0 || gy >= ny) { if (pery && gy >= -1 && gy <= ny) cy = wrap_idx(gy, ny); else load = false; }
-        const bool boxed = load && cx == gx && cy == gy;
-        const bool yreal = (gy >= 0 && gy < ny) || (pery && gy >= -1 && gy <= ny);
-        const bool xghost = !perx && (gx == -1 || gx == nx) && yreal;
-        const bool yghost = !pery && (gy == -1 || gy == ny) && gx >= -1 && gx <= nx;
-        const bool urow = row >= 1 && row <= K::TYI;  // columns whose u0 the consumers read
-        int m = 0;  // real planes read from the stage so far
-        // step 1 for real plane pz into its ring and u0 slots
-        auto make_plane = [&](int pz) __attribute__((always_inline)) {
-            const int gz = wrap_idx(pz, nz);
-            float2 G[9];
-            float g9;
-            ok = ok && mbar_wait(sbar, (uint32_t)(m & 1));
-            m++;
-            {
-                const S *sb = reinterpret_cast<const S *>(stage) + row * K::BX + ((x0 - 1) - xs + lane);
-                if (boxed) {
-#pragma unroll
-                    for (int j = 0; j < 9; j++)
-                        G[j] = f2(stage_value(sb + j * (RY * K::BX)), stage_value(sb + (18 - j) * (RY * K::BX)));
-                    g9 = stage_value(sb + 9 * (RY * K::BX));
-                } else if (load) {
-                    const int64_t off = (int64_t)gz * p.plane + (int64_t)cy * p.px + cx;
-#pragma unroll
-                    for (int j = 0; j < 9; j++)
-                        G[j] = f2((float)Store<S>::ld(src + j * p.dstride + off),
-                                  (float)Store<S>::ld(src + (18 - j) * p.dstride + off));
-                    g9 = (float)Store<S>::ld(src + 9 * p.dstride + off);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 9; j++) G[j] = f2(0.0f, 0.0f);
-                    g9 = 0.0f;
-                }
-            }
-            named_bar(1, K::NPROD);  // the stage has been read: the next plane may land in it
-            // the next real plane in order
-            issue(pz + 1 <= lastp ? pz + 1 : lastp + 1);
-            float *o = R(slot_of(pz), row, lane);
-            const int us = (nidx(pz) % 3) * K::NUC + (row - 1) * 32 + lane;
-            if (!load) {
-#pragma unroll
-                for (int i = 0; i < CS / 2; i++) st2(o + 2 * i, f2(0.0f, 0.0f));
-                return;
-            }
-            float Gh[3] = {0.0f, 0.0f, 0.0f};
-            if (FORCE) {
-                const int64_t ci = (int64_t)cx + (int64_t)nx * ((int64_t)cy + (int64_t)ny * gz);
-                cell_G<3, float>(p, ci, ncell, ct, Gh);
-            }
-            float2 F[9], U[9];
-            float f9, u9, mo[10];
-            step1_pairs<FORCE>(G, g9, Gh, cf, F, f9, U, u9, mo);
-#pragma unroll
-            for (int j = 0; j < 9; j++) st2(o + 2 * j, F[j]);
-            st2(o + pr::REST, f2(f9, mo[0]));
-#pragma unroll
-            for (int a = 0; a < 3; a++) st2(o + pr::ma(a), f2(mo[1 + a], mo[4 + a]));
-            st2(o + pr::XY, f2(mo[7], mo[8]));
-            st2(o + pr::YZ, f2(mo[9], mo[8]));
-            if (urow) {
-#pragma unroll
-                for (int j = 0; j < 9; j++) st2(u0b + us * K::UP + 2 * j, U[j]);
-                u0r[us] = u9;
-            }
-        };
-        // step 2 (reading R3: ghost = 2 f0 - f1, x then y): fbar+ and, by linearity, its moments
-        auto ghosts_xy = [&](int pz) __attribute__((always_inline)) {
-            const int sl = slot_of(pz);
-            if (xwall_tile) {
-                named_bar(1, K::NPROD);
-                if (xghost) {
-                    const int d1 = gx < 0 ? 1 : -1;
-                    float *o = R(sl, row, lane);
-                    const float *a = R(sl, row, lane + d1), *b = R(sl, row, lane + 2 * d1);
-#pragma unroll
-                    for (int i = 0; i < CS / 2; i++) st2(o + 2 * i, ghost2(ld2(a + 2 * i), ld2(b + 2 * i)));
-                }
-            }
-            if (ywall_tile) {
-                named_bar(1, K::NPROD);
-                if (yghost) {
-                    const int d1 = gy < 0 ? 1 : -1;
-                    float *o = R(sl, row, lane);
-                    const float *a = R(sl, row + d1, lane), *b = R(sl, row + 2 * d1, lane);
-#pragma unroll
-                    for (int i = 0; i < CS / 2; i++) st2(o + 2 * i, ghost2(ld2(a + 2 * i), ld2(b + 2 * i)));
-                }
-            }
-        };
-        // a ghost plane beyond a non-periodic z wall (whole region)
-        auto ghost_z = [&](int pz) __attribute__((always_inline)) {
-            float *o = R(slot_of(pz), row, lane);
-            const float *a = R(slot_of(pz < 0 ? 0 : nz - 1), row, lane);
-            const float *b = R(slot_of(pz < 0 ? 1 : nz - 2), row, lane);
-#pragma unroll
-            for (int i = 0; i < CS / 2; i++) st2(o + 2 * i, ghost2(ld2(a + 2 * i), ld2(b + 2 * i)));
-        };
-        auto leave = [&]() __attribute__((always_inline)) {
-            if (tid == 0) mbar_wait(sbar, (uint32_t)(m & 1));  // a copy still in flight: bounded wait
-        };
-
-        // prologue: planes z0 - 1 .. z0 + 1 (a ghost plane below z = 0 after the planes it needs)
-        for (int pz = z0 - 1; pz <= z0 + 1; pz++) {
-            if (!perz && (pz < 0 || pz >= nz)) continue;
-            make_plane(pz);
-        }
-        for (int pz = z0 - 1; pz <= z0 + 1; pz++) {
-            if (!perz && (pz < 0 || pz >= nz)) continue;
-            ghosts_xy(pz);
-        }
-        if (named_bar_or(1, K::NPROD, !ok)) { leave(); return; }
-        for (int pz = z0 - 1; pz <= z0 + 1; pz++)
-            if (!perz && (pz < 0 || pz >= nz)) ghost_z(pz);
-        for (int pz = z0 - 1; pz <= z0 + 1; pz++) mbar_arrive(full + slot_of(pz));
-        // the rest of the chunk, each plane into a slot the consumers have released
-        for (int pz = z0 + 2; pz <= z1; pz++) {
-            const int n = nidx(pz);
-            if (n >= 4) ok = ok && mbar_wait(empty + (n & 3), (uint32_t)(((n >> 2) - 1) & 1));
-            if (perz || pz < nz) {
-                make_plane(pz);
-                ghosts_xy(pz);
-            } else if (pz == nz) {
-                ghost_z(pz);
-            }
-            if (named_bar_or(1, K::NPROD, !ok)) { leave(); return; }
-            mbar_arrive(full + (n & 3));
-        }
-        return;
-    }
-
-    // =============================== consumers ===============================
-    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(K::CONS_REGS));
-    const int ctid = tid - K::NPROD;
-    const int lane = ctid & 31, row = ctid >> 5;
+    // the cell column of a thread: producer thread c and consumer thread NPROD + c own column c
+    const int lane = tid & 31, row = (tid & (K::NC - 1)) >> 5;
     const int gx = x0 - 1 + lane, gy = y0 - 1 + row;
-    const bool inner = lane >= 1 && lane <= K::TXI && row >= 1 && row <= K::TYI;
-    const bool upd = inner && gx < nx && gy < ny;
-    const bool need_x = row >= 1 && row <= K::TYI && gy >= 0 && gy < ny && lane <= K::TXI && gx >= -1 && gx < nx;
-    const bool ycol = lane >= 1 && lane <= K::TXI && gx >= 0 && gx < nx && gy >= -1 && gy <= ny;
-    const bool need_y = ycol && row <= K::TYI && gy < ny;
-    uint32_t seed = 0;  // stochastic rounding of 16-bit stores
-    if constexpr (sizeof(S) == 2) seed = store_seed(*p.step_ctr + p.step_off);
+    const bool xrow = row >= 1 && row <= K::TYI;  // rows that own x interfaces (warp-uniform)
     const float kap = cf.kappa, qk = -0.25f * kap;
     // (1/2 + kappa e, 1/2 - kappa e) of a pair whose first member has e_d = +1 (PK) or -1 (MK);
     // the tangential weight -kappa/4 e_t with e_t = +1 (QP) or -1 (QM) for the first member
     const float2 PK = f2(fmaf(kap, 1.0f, 0.5f), fmaf(kap, -1.0f, 0.5f));
     const float2 MK = f2(PK.y, PK.x);
     const float2 QP = f2(qk, -qk), QM = f2(-qk, qk);
-    auto wait_full = [&](int pz) __attribute__((always_inline)) -> bool {
-        const int n = nidx(pz);
-        return mbar_wait(full + (n & 3), (uint32_t)((n >> 2) & 1));
-    };
-    auto release = [&](int pz) __attribute__((always_inline)) {
-        if (pz >= z0 - 1) mbar_arrive(empty + slot_of(pz));
-    };
-    auto cons_bar = [&]() __attribute__((always_inline)) { named_bar(2, K::NCONS); };
-    auto cons_bar_or = [&](bool v) __attribute__((always_inline)) { return named_bar_or(2, K::NCONS, v); };
     // interface G / c at time t+h between (x,y,z) - e_d and (x,y,z): mean of the two cells,
     // one cell at a wall (reading R2)
     auto faceG = [&](int d, int x, int y, int z, float Gh[3]) __attribute__((always_inline)) {
@@ -750,6 +586,236 @@ __global__ void __launch_bounds__(512, 1)
         });
     };
 
+    if (tid < K::NPROD) {
+        // =============================== producer ===============================
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(K::PROD_REGS));
+        // real planes first .. lastp are copied in order into the one stage (phase m & 1 for the
+        // m-th); thread 0 issues the next copy once every producer thread has read the stage
+        const int first = (!perz && z0 - 1 < 0) ? z0 : z0 - 1;
+        const int lastp = (!perz && z1 >= nz) ? nz - 1 : z1;
+        constexpr int XA = 16 / (int)sizeof(S);
+        const int xs = (x0 - 1 >= 0) ? (x0 - 1) / XA * XA : -XA;
+        auto issue = [&](int pz) __attribute__((always_inline)) {
+            if (tid == 0 && pz >= first && pz <= lastp) {
+                mbar_arrive_expect_tx(sbar, (uint32_t)K::STAGE_BYTES);
+                tma_load_4d(stage, &tmap, sbar, xs, y0 - 1, wrap_idx(pz, nz), 0);
+            }
+        };
+        bool ok = true;
+        issue(first);
+        int cx = gx, cy = gy;
+        bool load = true;
+        if (gx < 0 || gx >= nx) { if (perx && gx >= -1 && gx <= nx) cx = wrap_idx(gx, nx); else load = false; }
+        if (gy < 0 || gy >= ny) { if (pery && gy >= -1 && gy <= ny) cy = wrap_idx(gy, ny); else load = false; }
+        const bool boxed = load && cx == gx && cy == gy;
+        const bool yreal = (gy >= 0 && gy < ny) || (pery && gy >= -1 && gy <= ny);
+        const bool xghost = !perx && (gx == -1 || gx == nx) && yreal;
+        const bool yghost = !pery && (gy == -1 || gy == ny) && gx >= -1 && gx <= nx;
+        const bool urow = row >= 1 && row <= K::TYI;  // columns whose u0 the consumers read
+        int m = 0;  // real planes read from the stage so far
+        // step 1 for real plane pz into its ring and u0 slots
+        auto make_plane = [&](int pz) __attribute__((always_inline)) {
+            const int gz = wrap_idx(pz, nz);
+            float2 G[9];
+            float g9;
+            ok = ok && mbar_wait(sbar, (uint32_t)(m & 1));
+            m++;
+            {
+                const S *sb = reinterpret_cast<const S *>(stage) + row * K::BX + ((x0 - 1) - xs + lane);
+                if (boxed) {
+#pragma unroll
+                    for (int j = 0; j < 9; j++)
+                        G[j] = f2(stage_value(sb + j * (RY * K::BX)), stage_value(sb + (18 - j) * (RY * K::BX)));
+                    g9 = stage_value(sb + 9 * (RY * K::BX));
+                } else if (load) {
+                    const int64_t off = (int64_t)gz * p.plane + (int64_t)cy * p.px + cx;
+#pragma unroll
+                    for (int j = 0; j < 9; j++)
+                        G[j] = f2((float)Store<S>::ld(src + j * p.dstride + off),
+                                  (float)Store<S>::ld(src + (18 - j) * p.dstride + off));
+                    g9 = (float)Store<S>::ld(src + 9 * p.dstride + off);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 9; j++) G[j] = f2(0.0f, 0.0f);
+                    g9 = 0.0f;
+                }
+            }
+            named_bar(1, K::NPROD);  // the stage has been read: the next plane may land in it
+            // the next real plane in order
+            issue(pz + 1 <= lastp ? pz + 1 : lastp + 1);
+            float *o = R(slot_of(pz), row, lane);
+            const int us = (nidx(pz) % 3) * K::NUC + (row - 1) * 32 + lane;
+            if (!load) {
+#pragma unroll
+                for (int i = 0; i < CS / 2; i++) st2(o + 2 * i, f2(0.0f, 0.0f));
+                return;
+            }
+            float Gh[3] = {0.0f, 0.0f, 0.0f};
+            if (FORCE) {
+                const int64_t ci = (int64_t)cx + (int64_t)nx * ((int64_t)cy + (int64_t)ny * gz);
+                cell_G<3, float>(p, ci, ncell, ct, Gh);
+            }
+            float2 F[9], U[9];
+            float f9, u9, mo[10];
+            step1_pairs<FORCE>(G, g9, Gh, cf, F, f9, U, u9, mo);
+#pragma unroll
+            for (int j = 0; j < 9; j++) st2(o + 2 * j, F[j]);
+            st2(o + pr::REST, f2(f9, mo[0]));
+#pragma unroll
+            for (int a = 0; a < 3; a++) st2(o + pr::ma(a), f2(mo[1 + a], mo[4 + a]));
+            st2(o + pr::XY, f2(mo[7], mo[8]));
+            st2(o + pr::YZ, f2(mo[9], mo[8]));
+            if (urow) {
+#pragma unroll
+                for (int j = 0; j < 9; j++) st2(u0b + us * K::UP + 2 * j, U[j]);
+                u0r[us] = u9;
+            }
+        };
+        // step 2 (reading R3: ghost = 2 f0 - f1, x then y): fbar+ and, by linearity, its moments
+        auto ghosts_xy = [&](int pz) __attribute__((always_inline)) {
+            const int sl = slot_of(pz);
+            if (xwall_tile) {
+                named_bar(1, K::NPROD);
+                if (xghost) {
+                    const int d1 = gx < 0 ? 1 : -1;
+                    float *o = R(sl, row, lane);
+                    const float *a = R(sl, row, lane + d1), *b = R(sl, row, lane + 2 * d1);
+#pragma unroll
+                    for (int i = 0; i < CS / 2; i++) st2(o + 2 * i, ghost2(ld2(a + 2 * i), ld2(b + 2 * i)));
+                }
+            }
+            if (ywall_tile) {
+                named_bar(1, K::NPROD);
+                if (yghost) {
+                    const int d1 = gy < 0 ? 1 : -1;
+                    float *o = R(sl, row, lane);
+                    const float *a = R(sl, row + d1, lane), *b = R(sl, row + 2 * d1, lane);
+#pragma unroll
+                    for (int i = 0; i < CS / 2; i++) st2(o + 2 * i, ghost2(ld2(a + 2 * i), ld2(b + 2 * i)));
+                }
+            }
+        };
+        // a ghost plane beyond a non-periodic z wall (whole region)
+        auto ghost_z = [&](int pz) __attribute__((always_inline)) {
+            float *o = R(slot_of(pz), row, lane);
+            const float *a = R(slot_of(pz < 0 ? 0 : nz - 1), row, lane);
+            const float *b = R(slot_of(pz < 0 ? 1 : nz - 2), row, lane);
+#pragma unroll
+            for (int i = 0; i < CS / 2; i++) st2(o + 2 * i, ghost2(ld2(a + 2 * i), ld2(b + 2 * i)));
+        };
+        // x interfaces of plane q (steps 3-7; every plane that the consumers update), for the
+        // rows that own them, into +x slot q % 2: beta parts exchanged by shuffles, step 5 at x
+        // walls from x_c, the interface that the next lane inward owns
+        const bool need_x = xrow && gy >= 0 && gy < ny && lane <= K::TXI && gx >= -1 && gx < nx;
+        auto x_faces = [&](int q) __attribute__((always_inline)) {
+            if (!xrow) return;  // halo rows own no x interface
+            float2 Cy[9], Cz[9];
+            float dy[4], dz[4];
+            cdiff(q, AY, Cy);
+            cdiff(q, AZ, Cz);
+            mdiff(q, AY, dy);
+            mdiff(q, AZ, dz);
+            float2 fxp[5];
+#pragma unroll
+            for (int i = 0; i < 5; i++) fxp[i] = f2(0.0f, 0.0f);
+            float2 alx[5], bex[5];
+            float Ax[4], Bx[4];
+            parts(AX, R(slot_of(q), row, lane), Cy, Cz, dy, dz, alx, bex, Ax, Bx);
+            float2 F[5];
+            float jb[3];
+#pragma unroll
+            for (int i = 0; i < 5; i++)
+                F[i] = __fadd2_rn(alx[i], f2(__shfl_down_sync(0xffffffffu, bex[i].x, 1),
+                                             __shfl_down_sync(0xffffffffu, bex[i].y, 1)));
+            float drb = Ax[0] + __shfl_down_sync(0xffffffffu, Bx[0], 1);
+#pragma unroll
+            for (int a = 0; a < 3; a++) jb[a] = Ax[1 + a] + __shfl_down_sync(0xffffffffu, Bx[1 + a], 1);
+            float Gb[3] = {0.0f, 0.0f, 0.0f};
+            if (FORCE && need_x) faceG(0, gx + 1, gy, q, Gb);
+            if (xwall_tile) {
+                // the wall interfaces take step 5 from x_c, the interface that the next lane
+                // inward owns (lane + 1 at the low wall, lane - 1 at the high wall); every lane
+                // takes part in the exchange. The first member of each x pair has e_x = -1.
+                float Fv[NF], Fn[NF], jd[3], ju[3], Gd[3] = {0.0f, 0.0f, 0.0f}, Gu[3] = {0.0f, 0.0f, 0.0f};
+                float2 Fn2[5];
+#pragma unroll
+                for (int i = 0; i < 5; i++)
+                    Fn2[i] = f2(__shfl_up_sync(0xffffffffu, F[i].x, 1), __shfl_down_sync(0xffffffffu, F[i].y, 1));
+                from_pairs(AX, F, Fv);
+                from_pairs(AX, Fn2, Fn);
+                const float dd = __shfl_down_sync(0xffffffffu, drb, 1), du = __shfl_up_sync(0xffffffffu, drb, 1);
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    jd[a] = __shfl_down_sync(0xffffffffu, jb[a], 1);
+                    ju[a] = __shfl_up_sync(0xffffffffu, jb[a], 1);
+                    if (FORCE) {
+                        Gd[a] = __shfl_down_sync(0xffffffffu, Gb[a], 1);
+                        Gu[a] = __shfl_up_sync(0xffffffffu, Gb[a], 1);
+                    }
+                }
+                if (need_x && gx == -1) neq_wall<Q, 0, FORCE, 0>(p, cf, Fv, drb, jb, Fn, dd, jd, Gd);
+                if (need_x && gx == nx - 1) neq_wall<Q, 0, FORCE, 1>(p, cf, Fv, drb, jb, Fn, du, ju, Gu);
+                to_pairs(AX, Fv, F);
+            }
+            if (need_x) relax_face(AX, F, drb, jb, Gb, fxp);
+            float *o = fxb + ((q & 1) * K::NUC + (row - 1) * 32 + lane) * K::FS;
+#pragma unroll
+            for (int i = 0; i < 5; i++) st2(o + 2 * i, fxp[i]);
+        };
+        auto leave = [&]() __attribute__((always_inline)) {
+            if (tid == 0) mbar_wait(sbar, (uint32_t)(m & 1));  // a copy still in flight: bounded wait
+        };
+
+        // prologue: planes z0 - 1 .. z0 + 1 (a ghost plane below z = 0 after the planes it needs)
+        for (int pz = z0 - 1; pz <= z0 + 1; pz++) {
+            if (!perz && (pz < 0 || pz >= nz)) continue;
+            make_plane(pz);
+        }
+        for (int pz = z0 - 1; pz <= z0 + 1; pz++) {
+            if (!perz && (pz < 0 || pz >= nz)) continue;
+            ghosts_xy(pz);
+        }
+        if (named_bar_or(1, K::NPROD, !ok)) { leave(); return; }
+        for (int pz = z0 - 1; pz <= z0 + 1; pz++)
+            if (!perz && (pz < 0 || pz >= nz)) ghost_z(pz);
+        x_faces(z0);  // reads rows of plane z0 (made before the barrier above) and own columns
+        for (int pz = z0 - 1; pz <= z0 + 1; pz++) mbar_arrive(full + slot_of(pz));
+        // the rest of the chunk, each plane into a slot the consumers have released
+        for (int pz = z0 + 2; pz <= z1; pz++) {
+            const int n = nidx(pz);
+            if (n >= 4) ok = ok && mbar_wait(empty + (n & 3), (uint32_t)(((n >> 2) - 1) & 1));
+            if (perz || pz < nz) {
+                make_plane(pz);
+                ghosts_xy(pz);
+            } else if (pz == nz) {
+                ghost_z(pz);
+            }
+            // plane pz - 1 was made an iteration ago (its rows are visible); of plane pz the x
+            // faces read only the thread's own column
+            x_faces(pz - 1);
+            if (named_bar_or(1, K::NPROD, !ok)) { leave(); return; }
+            mbar_arrive(full + (n & 3));
+        }
+        return;
+    }
+
+    // =============================== consumers ===============================
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(K::CONS_REGS));
+    const bool inner = lane >= 1 && lane <= K::TXI && row >= 1 && row <= K::TYI;
+    const bool upd = inner && gx < nx && gy < ny;
+    const bool ycol = lane >= 1 && lane <= K::TXI && gx >= 0 && gx < nx && gy >= -1 && gy <= ny;
+    const bool need_y = ycol && row <= K::TYI && gy < ny;
+    uint32_t seed = 0;  // stochastic rounding of 16-bit stores
+    if constexpr (sizeof(S) == 2) seed = store_seed(*p.step_ctr + p.step_off);
+    auto wait_full = [&](int pz) __attribute__((always_inline)) -> bool {
+        const int n = nidx(pz);
+        return mbar_wait(full + (n & 3), (uint32_t)((n >> 2) & 1));
+    };
+    auto release = [&](int pz) __attribute__((always_inline)) {
+        if (pz >= z0 - 1) mbar_arrive(empty + slot_of(pz));
+    };
+    auto cons_bar = [&]() __attribute__((always_inline)) { named_bar(2, K::NCONS); };
+    auto cons_bar_or = [&](bool v) __attribute__((always_inline)) { return named_bar_or(2, K::NCONS, v); };
     bool ok = true;
     for (int pz = z0 - 1; pz <= z0 + 1; pz++) ok = ok && wait_full(pz);
     if (cons_bar_or(!ok)) return;
@@ -761,21 +827,19 @@ __global__ void __launch_bounds__(512, 1)
     for (int i = 0; i < 5; i++) alz[i] = fzm[i] = f2(0.0f, 0.0f);
 #pragma unroll
     for (int i = 0; i < 4; i++) Az[i] = 0.0f;
-    // carried too, by the rows that own x interfaces: the x and y differences of the current
-    // plane, formed with the z parts of the previous iteration and used again by the x and y
-    // parts of this one
-    const bool xrow = row >= 1 && row <= K::TYI;  // warp-uniform
-    float2 cAX[9], cAY[9];
-    float mAX[4], mAY[4];
+    // carried too, by the rows that own x interfaces: the x differences of the current plane,
+    // formed with the z parts of the previous iteration and used again by the y parts of this one
+    float2 cAX[9];
+    float mAX[4];
     if (xrow) {
         cdiff(z0, AX, cAX);
-        cdiff(z0, AY, cAY);
         mdiff(z0, AX, mAX);
-        mdiff(z0, AY, mAY);
     }
     if (upd) {
-        float2 bz[5];
-        float Bz[4];
+        float2 bz[5], cAY[9];
+        float Bz[4], mAY[4];
+        cdiff(z0, AY, cAY);
+        mdiff(z0, AY, mAY);
         parts(AZ, R(slot_of(z0), row, lane), cAX, cAY, mAX, mAY, alz, bz, Az, Bz);
         const Pairs5 r = direct_face_ws<FORCE>(p, cf, ring, 2, z0 - 1, z0, row, lane, gx, gy, z0, cth);
 #pragma unroll
@@ -803,56 +867,10 @@ __global__ void __launch_bounds__(512, 1)
             for (int i = 0; i < 5; i++) fzp[i] = r.v[i];
         }
 
-        // ---- P3: x interfaces of plane kz (beta parts exchanged by shuffles) ----
         float2 Cz[9];
         float dz[4];
         cdiff(kz, AZ, Cz);
         mdiff(kz, AZ, dz);
-        float2 fxp[5];
-#pragma unroll
-        for (int i = 0; i < 5; i++) fxp[i] = f2(0.0f, 0.0f);
-        if (xrow) {  // halo rows own no x interface
-            float2 alx[5], bex[5];
-            float Ax[4], Bx[4];
-            parts(AX, cur, cAY, Cz, mAY, dz, alx, bex, Ax, Bx);
-            float2 F[5];
-            float jb[3];
-#pragma unroll
-            for (int i = 0; i < 5; i++)
-                F[i] = __fadd2_rn(alx[i], f2(__shfl_down_sync(0xffffffffu, bex[i].x, 1),
-                                             __shfl_down_sync(0xffffffffu, bex[i].y, 1)));
-            float drb = Ax[0] + __shfl_down_sync(0xffffffffu, Bx[0], 1);
-#pragma unroll
-            for (int a = 0; a < 3; a++) jb[a] = Ax[1 + a] + __shfl_down_sync(0xffffffffu, Bx[1 + a], 1);
-            float Gb[3] = {0.0f, 0.0f, 0.0f};
-            if (FORCE && need_x) faceG(0, gx + 1, gy, kz, Gb);
-            if (xwall_tile) {
-                // the wall interfaces take step 5 from x_c, the interface that the next lane
-                // inward owns (lane + 1 at the low wall, lane - 1 at the high wall); every lane
-                // takes part in the exchange. The first member of each x pair has e_x = -1.
-                float Fv[NF], Fn[NF], jd[3], ju[3], Gd[3] = {0.0f, 0.0f, 0.0f}, Gu[3] = {0.0f, 0.0f, 0.0f};
-                float2 Fn2[5];
-#pragma unroll
-                for (int i = 0; i < 5; i++)
-                    Fn2[i] = f2(__shfl_up_sync(0xffffffffu, F[i].x, 1), __shfl_down_sync(0xffffffffu, F[i].y, 1));
-                from_pairs(AX, F, Fv);
-                from_pairs(AX, Fn2, Fn);
-                const float dd = __shfl_down_sync(0xffffffffu, drb, 1), du = __shfl_up_sync(0xffffffffu, drb, 1);
-#pragma unroll
-                for (int a = 0; a < 3; a++) {
-                    jd[a] = __shfl_down_sync(0xffffffffu, jb[a], 1);
-                    ju[a] = __shfl_up_sync(0xffffffffu, jb[a], 1);
-                    if (FORCE) {
-                        Gd[a] = __shfl_down_sync(0xffffffffu, Gb[a], 1);
-                        Gu[a] = __shfl_up_sync(0xffffffffu, Gb[a], 1);
-                    }
-                }
-                if (need_x && gx == -1) neq_wall<Q, 0, FORCE, 0>(p, cf, Fv, drb, jb, Fn, dd, jd, Gd);
-                if (need_x && gx == nx - 1) neq_wall<Q, 0, FORCE, 1>(p, cf, Fv, drb, jb, Fn, du, ju, Gu);
-                to_pairs(AX, Fv, F);
-            }
-            if (need_x) relax_face(AX, F, drb, jb, Gb, fxp);
-        }
         // ---- P4: y parts of plane kz; publish beta_y, B_y; y interfaces ----
         float2 aly[5];
         float Ay[4];
@@ -877,19 +895,19 @@ __global__ void __launch_bounds__(512, 1)
             }
         }
         // ---- P2: z parts of plane kz+1 and the z interface kz+1/2, before the first consumer
-        //      barrier: they need nothing from the y exchange, so the x interfaces, the y parts
-        //      and the z interface form one barrier-free phase of independent chains ----
+        //      barrier: they need nothing from the y exchange, so the y parts and the z
+        //      interface form one barrier-free phase of independent chains ----
         float2 alzn[5];
         float Azn[4];
         if (xrow) {
             cdiff(kz + 1, AX, cAX);
-            cdiff(kz + 1, AY, cAY);
             mdiff(kz + 1, AX, mAX);
-            mdiff(kz + 1, AY, mAY);
         }
         if (upd) {
-            float2 bezn[5];
-            float Bzn[4];
+            float2 bezn[5], cAY[9];
+            float Bzn[4], mAY[4];
+            cdiff(kz + 1, AY, cAY);
+            mdiff(kz + 1, AY, mAY);
             parts(AZ, R(slot_of(kz + 1), row, lane), cAX, cAY, mAX, mAY, alzn, bezn, Azn, Bzn);
             if (!zdir) {
                 float2 F[5];
@@ -928,13 +946,15 @@ __global__ void __launch_bounds__(512, 1)
         cons_bar();
 
         // ---- P5: steps 8-9, update of cell (gx, gy, kz) ----
-        float2 fxm[5];
-        if (xrow) {
-#pragma unroll
-            for (int i = 0; i < 5; i++)
-                fxm[i] = f2(__shfl_up_sync(0xffffffffu, fxp[i].x, 1), __shfl_up_sync(0xffffffffu, fxp[i].y, 1));
-        }
         if (upd) {
+            // f at the cell's +x and -x interfaces, from the producer warps
+            float2 fxp[5], fxm[5];
+            const float *xo = fxb + ((kz & 1) * K::NUC + (row - 1) * 32 + lane) * K::FS;
+#pragma unroll
+            for (int i = 0; i < 5; i++) {
+                fxp[i] = ld2(xo + 2 * i);
+                fxm[i] = ld2(xo - K::FS + 2 * i);
+            }
             const float *ym = xf + ((row - 1) * 32 + lane) * K::FS;
             const int us = (nidx(kz) % 3) * K::NUC + (row - 1) * 32 + lane;
             const float *u0 = u0b + us * K::UP;

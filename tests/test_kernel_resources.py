@@ -29,7 +29,7 @@ def _find(res, *parts):
 
 def test_d3q19_warp_specialised_kernel_does_not_spill(res):
     # fused_step3d_ws<19, S, false> (the benchmark's force-free instantiation) under its register
-    # split of 72 (producers) / 184 (consumers) registers
+    # split of 96 (producers) / 160 (consumers) registers
     for k, v in _find(res, "fused_step3d_wsILi19E", "Lb0E").items():
         assert v["regs"] == 128 and v["spill_stores"] == 0, (k, v)
 
