@@ -471,26 +471,21 @@ __global__ void __launch_bounds__(512, 1)
     constexpr std::integral_constant<int, 1> AY{};
     constexpr std::integral_constant<int, 2> AZ{};
 
-    // central differences of the own column's pairs at plane pz along t, C[j] for the pairs
-    // with components along t and one other axis (a velocity along one axis only has no
-    // tangential part), and of its moments: dM[0] of M_t, dM[1 + a] of M_at
-    auto cdiff = [&](int pz, auto tc, float2 C[9]) __attribute__((always_inline)) {
+    // Central differences of a column's pairs, C[j] for the pairs with components along t and
+    // one other axis (a velocity along one axis only has no tangential part), and of its
+    // moments: dM[0] of M_t, dM[1 + a] of M_at. lo and hi point at the column's two neighbours
+    // along t. In the plane (t = x, y) they are the cell pointer -+ the neighbour's offset:
+    // every caller is a row 1..TYI thread, or (along x) a lane 1..TXI thread, so both
+    // neighbours lie in the ring.
+    auto cdiff = [&](const float *lo, const float *hi, auto tc, float2 C[9]) __attribute__((always_inline)) {
         constexpr int t = decltype(tc)::value;
-        const float *lo, *hi;
-        if constexpr (t == 0) { lo = R(slot_of(pz), row, max(lane - 1, 0)); hi = R(slot_of(pz), row, min(lane + 1, 31)); }
-        else if constexpr (t == 1) { lo = R(slot_of(pz), max(row - 1, 0), lane); hi = R(slot_of(pz), min(row + 1, RY - 1), lane); }
-        else { lo = R(slot_of(pz - 1), row, lane); hi = R(slot_of(pz + 1), row, lane); }
         sfor<9>([&](auto jc) {
             constexpr int j = jc;
             if constexpr (pr::nnz(j) == 2 && pr::e(j, t) != 0) C[j] = sub2(ld2(hi + 2 * j), ld2(lo + 2 * j));
         });
     };
-    auto mdiff = [&](int pz, auto tc, float dM[4]) __attribute__((always_inline)) {
+    auto mdiff = [&](const float *lo, const float *hi, auto tc, float dM[4]) __attribute__((always_inline)) {
         constexpr int t = decltype(tc)::value;
-        const float *lo, *hi;
-        if constexpr (t == 0) { lo = R(slot_of(pz), row, max(lane - 1, 0)); hi = R(slot_of(pz), row, min(lane + 1, 31)); }
-        else if constexpr (t == 1) { lo = R(slot_of(pz), max(row - 1, 0), lane); hi = R(slot_of(pz), min(row + 1, RY - 1), lane); }
-        else { lo = R(slot_of(pz - 1), row, lane); hi = R(slot_of(pz + 1), row, lane); }
         const float2 d1 = sub2(ld2(hi + pr::ma(t)), ld2(lo + pr::ma(t)));  // (M_t, M_tt)
         dM[0] = d1.x;
         dM[1 + t] = d1.y;
@@ -506,6 +501,11 @@ __global__ void __launch_bounds__(512, 1)
             dM[2] = d2.x;
             dM[1] = d2.y;
         }
+    };
+    constexpr int NX1 = CS, NY1 = 32 * CS;  // ring offsets of the x and y neighbours
+    // the thread's own column in the ring slot of plane pz
+    auto P = [&](int pz) __attribute__((always_inline)) -> const float * {
+        return ring + slot_of(pz) * K::PLANE + (row * 32 + lane) * CS;
     };
     // Per-cell parts of the interface normal to d (face_parts of dugks_step3d.cuh on pairs):
     // AL/BE for the five crossing pairs, A = (A0, A1[3]), B likewise. c: the cell in the ring;
@@ -613,8 +613,9 @@ __global__ void __launch_bounds__(512, 1)
         const bool yghost = !pery && (gy == -1 || gy == ny) && gx >= -1 && gx <= nx;
         const bool urow = row >= 1 && row <= K::TYI;  // columns whose u0 the consumers read
         int m = 0;  // real planes read from the stage so far
-        // step 1 for real plane pz into its ring and u0 slots
-        auto make_plane = [&](int pz) __attribute__((always_inline)) {
+        // step 1 for real plane pz into its ring and u0 slots; false: a wait gave up (every
+        // producer thread learns it at the same barrier)
+        auto make_plane = [&](int pz) __attribute__((always_inline)) -> bool {
             const int gz = wrap_idx(pz, nz);
             float2 G[9];
             float g9;
@@ -640,7 +641,9 @@ __global__ void __launch_bounds__(512, 1)
                     g9 = 0.0f;
                 }
             }
-            named_bar(1, K::NPROD);  // the stage has been read: the next plane may land in it
+            // the stage has been read: the next plane may land in it; every producer thread has
+            // also finished the previous plane (its rows are visible to the x interfaces)
+            if (named_bar_or(1, K::NPROD, !ok)) return false;
             // the next real plane in order
             issue(pz + 1 <= lastp ? pz + 1 : lastp + 1);
             float *o = R(slot_of(pz), row, lane);
@@ -648,7 +651,7 @@ __global__ void __launch_bounds__(512, 1)
             if (!load) {
 #pragma unroll
                 for (int i = 0; i < CS / 2; i++) st2(o + 2 * i, f2(0.0f, 0.0f));
-                return;
+                return true;
             }
             float Gh[3] = {0.0f, 0.0f, 0.0f};
             if (FORCE) {
@@ -670,6 +673,7 @@ __global__ void __launch_bounds__(512, 1)
                 for (int j = 0; j < 9; j++) st2(u0b + us * K::UP + 2 * j, U[j]);
                 u0r[us] = u9;
             }
+            return true;
         };
         // step 2 (reading R3: ghost = 2 f0 - f1, x then y): fbar+ and, by linearity, its moments
         auto ghosts_xy = [&](int pz) __attribute__((always_inline)) {
@@ -709,18 +713,19 @@ __global__ void __launch_bounds__(512, 1)
         const bool need_x = xrow && gy >= 0 && gy < ny && lane <= K::TXI && gx >= -1 && gx < nx;
         auto x_faces = [&](int q) __attribute__((always_inline)) {
             if (!xrow) return;  // halo rows own no x interface
+            const float *pq = P(q), *pm = P(q - 1), *pp = P(q + 1);
             float2 Cy[9], Cz[9];
             float dy[4], dz[4];
-            cdiff(q, AY, Cy);
-            cdiff(q, AZ, Cz);
-            mdiff(q, AY, dy);
-            mdiff(q, AZ, dz);
+            cdiff(pq - NY1, pq + NY1, AY, Cy);
+            cdiff(pm, pp, AZ, Cz);
+            mdiff(pq - NY1, pq + NY1, AY, dy);
+            mdiff(pm, pp, AZ, dz);
             float2 fxp[5];
 #pragma unroll
             for (int i = 0; i < 5; i++) fxp[i] = f2(0.0f, 0.0f);
             float2 alx[5], bex[5];
             float Ax[4], Bx[4];
-            parts(AX, R(slot_of(q), row, lane), Cy, Cz, dy, dz, alx, bex, Ax, Bx);
+            parts(AX, pq, Cy, Cz, dy, dz, alx, bex, Ax, Bx);
             float2 F[5];
             float jb[3];
 #pragma unroll
@@ -769,7 +774,7 @@ __global__ void __launch_bounds__(512, 1)
         // prologue: planes z0 - 1 .. z0 + 1 (a ghost plane below z = 0 after the planes it needs)
         for (int pz = z0 - 1; pz <= z0 + 1; pz++) {
             if (!perz && (pz < 0 || pz >= nz)) continue;
-            make_plane(pz);
+            if (!make_plane(pz)) { leave(); return; }
         }
         for (int pz = z0 - 1; pz <= z0 + 1; pz++) {
             if (!perz && (pz < 0 || pz >= nz)) continue;
@@ -785,15 +790,15 @@ __global__ void __launch_bounds__(512, 1)
             const int n = nidx(pz);
             if (n >= 4) ok = ok && mbar_wait(empty + (n & 3), (uint32_t)(((n >> 2) - 1) & 1));
             if (perz || pz < nz) {
-                make_plane(pz);
+                if (!make_plane(pz)) { leave(); return; }
                 ghosts_xy(pz);
-            } else if (pz == nz) {
+            } else {  // pz == nz: the ghost plane above the top wall
+                if (named_bar_or(1, K::NPROD, !ok)) { leave(); return; }
                 ghost_z(pz);
             }
-            // plane pz - 1 was made an iteration ago (its rows are visible); of plane pz the x
-            // faces read only the thread's own column
+            // plane pz - 1 was made an iteration ago and is visible since the barrier above; of
+            // plane pz the x faces read only the thread's own column
             x_faces(pz - 1);
-            if (named_bar_or(1, K::NPROD, !ok)) { leave(); return; }
             mbar_arrive(full + (n & 3));
         }
         return;
@@ -832,15 +837,17 @@ __global__ void __launch_bounds__(512, 1)
     float2 cAX[9];
     float mAX[4];
     if (xrow) {
-        cdiff(z0, AX, cAX);
-        mdiff(z0, AX, mAX);
+        const float *c0 = P(z0);
+        cdiff(c0 - NX1, c0 + NX1, AX, cAX);
+        mdiff(c0 - NX1, c0 + NX1, AX, mAX);
     }
     if (upd) {
+        const float *c0 = P(z0);
         float2 bz[5], cAY[9];
         float Bz[4], mAY[4];
-        cdiff(z0, AY, cAY);
-        mdiff(z0, AY, mAY);
-        parts(AZ, R(slot_of(z0), row, lane), cAX, cAY, mAX, mAY, alz, bz, Az, Bz);
+        cdiff(c0 - NY1, c0 + NY1, AY, cAY);
+        mdiff(c0 - NY1, c0 + NY1, AY, mAY);
+        parts(AZ, c0, cAX, cAY, mAX, mAY, alz, bz, Az, Bz);
         const Pairs5 r = direct_face_ws<FORCE>(p, cf, ring, 2, z0 - 1, z0, row, lane, gx, gy, z0, cth);
 #pragma unroll
         for (int i = 0; i < 5; i++) fzm[i] = r.v[i];
@@ -850,7 +857,7 @@ __global__ void __launch_bounds__(512, 1)
         // ---- plane kz+1 (fbar+, moments, ghosts) from the producer warps; planes z0 - 1 .. z0 + 1
         //      were awaited before the loop ----
         if (kz > z0) ok = ok && wait_full(kz + 1);
-        const float *cur = R(slot_of(kz), row, lane);
+        const float *cur = P(kz), *prv = P(kz - 1), *nxt = P(kz + 1);
         // the direct paths of this iteration (a y wall row's +y interface, the +z interface below
         // a z wall) first, while the march holds the fewest values: they read only the ring
         float2 fyp[5], fzp[5];
@@ -869,8 +876,8 @@ __global__ void __launch_bounds__(512, 1)
 
         float2 Cz[9];
         float dz[4];
-        cdiff(kz, AZ, Cz);
-        mdiff(kz, AZ, dz);
+        cdiff(prv, nxt, AZ, Cz);
+        mdiff(prv, nxt, AZ, dz);
         // ---- P4: y parts of plane kz; publish beta_y, B_y; y interfaces ----
         float2 aly[5];
         float Ay[4];
@@ -882,8 +889,8 @@ __global__ void __launch_bounds__(512, 1)
             } else {
                 float2 Cx[9];
                 float dx[4];
-                cdiff(kz, AX, Cx);
-                mdiff(kz, AX, dx);
+                cdiff(cur - NX1, cur + NX1, AX, Cx);
+                mdiff(cur - NX1, cur + NX1, AX, dx);
                 parts(AY, cur, Cx, Cz, dx, dz, aly, bey, Ay, By);
             }
             if (row >= 1) {
@@ -900,15 +907,15 @@ __global__ void __launch_bounds__(512, 1)
         float2 alzn[5];
         float Azn[4];
         if (xrow) {
-            cdiff(kz + 1, AX, cAX);
-            mdiff(kz + 1, AX, mAX);
+            cdiff(nxt - NX1, nxt + NX1, AX, cAX);
+            mdiff(nxt - NX1, nxt + NX1, AX, mAX);
         }
         if (upd) {
             float2 bezn[5], cAY[9];
             float Bzn[4], mAY[4];
-            cdiff(kz + 1, AY, cAY);
-            mdiff(kz + 1, AY, mAY);
-            parts(AZ, R(slot_of(kz + 1), row, lane), cAX, cAY, mAX, mAY, alzn, bezn, Azn, Bzn);
+            cdiff(nxt - NY1, nxt + NY1, AY, cAY);
+            mdiff(nxt - NY1, nxt + NY1, AY, mAY);
+            parts(AZ, nxt, cAX, cAY, mAX, mAY, alzn, bezn, Azn, Bzn);
             if (!zdir) {
                 float2 F[5];
                 float jb[3];
