@@ -35,6 +35,11 @@ def _decode(a, store):
 # 16-bit results carry one stochastic rounding of the stored value: up to one unit in the
 # last place, 2^-7 (BF16) or 2^-10 (FP16) of the value, on top of the FP32 arithmetic.
 LEGS = [(19, 0, 0.0), (19, 1, 2.0 ** -7), (19, 2, 2.0 ** -10), (27, 0, 0.0)]
+# Windows across z-chunk boundaries of the throughput kernels' launch: on 152 SMs the 256^3 cube
+# runs in chunks of 52 planes (D3Q19: 9 x 43 tiles), so z = 52, 104, 156, 208 start a chunk,
+# whose first interface takes the direct path and whose ring is filled anew. Each window below
+# spans one of them by at least two planes on either side.
+CHUNK_WINDOWS = [(122, 122, 47), (40, 200, 99), (200, 40, 151), (150, 150, 203)]
 
 
 @pytest.mark.parametrize("q,store,ulp", LEGS)
@@ -52,7 +57,7 @@ def test_256_cube_sampled_windows(q, store, ulp):
     s.close()
     o_tmp = Oracle((4, 4, 4), q, nu=cfg["nu"], dt=cfg["dt"])
     _, Wt = o_tmp.lattice()
-    for lo in starts(N, WIN, np.random.default_rng(7)):
+    for lo in starts(N, WIN, np.random.default_rng(7)) + CHUNK_WINDOWS:
         zs, ys, xs = slice(lo[2], lo[2] + WIN), slice(lo[1], lo[1] + WIN), slice(lo[0], lo[0] + WIN)
         win0 = g0[:, zs, ys, xs]
         o = Oracle((WIN, WIN, WIN), q, nu=cfg["nu"], dt=cfg["dt"], rt=cfg["rt"], rho0=cfg["rho0"],
