@@ -96,27 +96,34 @@ __device__ __forceinline__ void cell_sums_f(const StepParams &p, const S *src, i
     }
 }
 
+// Element offset of cell n (x fastest) in the padded state layout: n itself when the rows carry
+// no padding, which spares the 64-bit divisions.
+__device__ __forceinline__ int64_t cell_offset(const StepParams &p, int64_t n) {
+    if (p.px == p.nx) return n;
+    const int x = (int)(n % p.nx);
+    const int y = (int)((n / p.nx) % p.ny);
+    const int z = (int)(n / ((int64_t)p.nx * p.ny));
+    return (int64_t)z * p.plane + (int64_t)y * p.px + x;
+}
+
 // Cell moments in double from the stored state: drho = sum g, u = c/rho0 sum e g + G dt/2
-// (the sums of 32- and 16-bit states in compensated FP32, converted once).
+// (the sums of 32- and 16-bit states in compensated FP32, converted once). cr0 = c / rho0,
+// divided once by the caller (the incompressible model's factor).
 template <int Q, class S>
 __device__ __forceinline__ void cell_moments_dd(const StepParams &p, const S *src, int64_t n, int64_t ncell, double ct,
-                                                double dtc, double c, double &drho, double u[3]) {
+                                                double dtc, double c, double cr0, double &drho, double u[3]) {
     if constexpr (sizeof(S) == 8) {
         cell_moments_d<Q, S>(p, src, n, ncell, ct, dtc, c, drho, u);
     } else {
         constexpr int D = Lat<Q>::D;
-        const int x = (int)(n % p.nx);
-        const int y = (int)((n / p.nx) % p.ny);
-        const int z = (int)(n / ((int64_t)p.nx * p.ny));
-        const int64_t off = (int64_t)z * p.plane + (int64_t)y * p.px + x;
         float r[2], j[3][2];
-        cell_sums_f<Q, S>(p, src, off, r, j);
+        cell_sums_f<Q, S>(p, src, cell_offset(p, n), r, j);
         drho = (double)r[0] + (double)r[1];
-        const double rd = p.model == 1 ? (double)p.rho0 + drho : (double)p.rho0;
+        const double cr = p.model == 1 ? c / ((double)p.rho0 + drho) : cr0;
         for (int a = 0; a < 3; a++) {
             double G = a < D ? (double)p.g[a] : 0.0;
             if (p.field && a < D) G += (double)p.field[a * ncell + n];
-            u[a] = a < D ? c / rd * ((double)j[a][0] + (double)j[a][1]) + G * ct * dtc : 0.0;
+            u[a] = a < D ? cr * ((double)j[a][0] + (double)j[a][1]) + G * ct * dtc : 0.0;
         }
     }
 }
@@ -126,12 +133,8 @@ template <int Q, class S>
 __device__ __forceinline__ void cell_moments_out_f(const StepParams &p, const S *src, int64_t n, int64_t ncell,
                                                    float ctdt, float c_over_rho0, float rt, float *out) {
     constexpr int D = Lat<Q>::D;
-    const int x = (int)(n % p.nx);
-    const int y = (int)((n / p.nx) % p.ny);
-    const int z = (int)(n / ((int64_t)p.nx * p.ny));
-    const int64_t off = (int64_t)z * p.plane + (int64_t)y * p.px + x;
     float r[2], j[3][2];
-    cell_sums_f<Q, S>(p, src, off, r, j);
+    cell_sums_f<Q, S>(p, src, cell_offset(p, n), r, j);
     out[n] = (r[0] + r[1]) * rt;
     // c / rho0, or c / rho in the original model
     const float cr = p.model == 1 ? c_over_rho0 * (float)p.rho0 / ((float)p.rho0 + (r[0] + r[1])) : c_over_rho0;
@@ -171,15 +174,15 @@ constexpr int RES_THREADS = 256;
 constexpr int RES_SLOTS = 8;
 
 template <int Q, class S>
-__global__ void __launch_bounds__(RES_THREADS) residual_kernel(const StepParams p, double ct, double c, double *uprev,
-                                                                int have_prev, double *partials) {
+__global__ void __launch_bounds__(RES_THREADS) residual_kernel(const StepParams p, double ct, double c, double cr0,
+                                                                double *uprev, int have_prev, double *partials) {
     constexpr int D = Lat<Q>::D;
     const int64_t ncell = (int64_t)p.nx * p.ny * p.nz;
     const S *src = reinterpret_cast<const S *>(p.src);
     double s[RES_SLOTS] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < ncell; n += (int64_t)gridDim.x * blockDim.x) {
         double drho, u[3];
-        cell_moments_dd<Q, S>(p, src, n, ncell, ct, 0.5 * p.dt, c, drho, u);
+        cell_moments_dd<Q, S>(p, src, n, ncell, ct, 0.5 * p.dt, c, cr0, drho, u);
         for (int a = 0; a < D; a++) {
             const double du = u[a] - (have_prev ? uprev[a * ncell + n] : 0.0);
             s[0] += du * du;
@@ -259,10 +262,13 @@ static cudaError_t residual_q(int store, const StepParams &p, double t, double r
                               double *partials, int nblocks, double *out, cudaStream_t st) {
     const double c = sqrt(3.0 * rt);
     const double ct = cos(p.omega * t);
-    if (store == 0) residual_kernel<Q, float><<<nblocks, RES_THREADS, 0, st>>>(p, ct, c, uprev, have_prev, partials);
-    else if (store == 1) residual_kernel<Q, __nv_bfloat16><<<nblocks, RES_THREADS, 0, st>>>(p, ct, c, uprev, have_prev, partials);
-    else if (store == 2) residual_kernel<Q, __half><<<nblocks, RES_THREADS, 0, st>>>(p, ct, c, uprev, have_prev, partials);
-    else residual_kernel<Q, double><<<nblocks, RES_THREADS, 0, st>>>(p, ct, c, uprev, have_prev, partials);
+    const double cr0 = c / p.rho0;
+    if (store == 0) residual_kernel<Q, float><<<nblocks, RES_THREADS, 0, st>>>(p, ct, c, cr0, uprev, have_prev, partials);
+    else if (store == 1)
+        residual_kernel<Q, __nv_bfloat16><<<nblocks, RES_THREADS, 0, st>>>(p, ct, c, cr0, uprev, have_prev, partials);
+    else if (store == 2)
+        residual_kernel<Q, __half><<<nblocks, RES_THREADS, 0, st>>>(p, ct, c, cr0, uprev, have_prev, partials);
+    else residual_kernel<Q, double><<<nblocks, RES_THREADS, 0, st>>>(p, ct, c, cr0, uprev, have_prev, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     residual_final<<<1, 32, 0, st>>>(partials, nblocks, out);
