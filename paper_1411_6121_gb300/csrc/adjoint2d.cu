@@ -871,6 +871,9 @@ AdjParams<T> base_params(const dugks_t h, const AdjBufs &B) {
 
 // One reverse step at the state g~^n held in `state` (t_n = tn): lambda' in lam1 -> lam0.
 // Four launches: cell recompute, interior and frame interfaces, all cells (frame blocks first).
+// The two interface kernels write disjoint interfaces and read only the cell recompute's
+// output and lambda', so the frame ones run on the tape's second stream beside the interior
+// ones (fork after the cell recompute, join before the cells).
 template <class T>
 cudaError_t reverse_step(AdjParams<T> a, const dugks_t h, const void *state, double tn, const void *lam1,
                          void *lam0, int64_t *launches) {
@@ -887,16 +890,27 @@ cudaError_t reverse_step(AdjParams<T> a, const dugks_t h, const void *state, dou
     adj_cells_fwd<T><<<blocks_for(nc, 256), 256, 0, st>>>(a);
     int64_t n = 1;
     const Rect r0 = face_rect(0, nx, ny, a.per[0], a.per[1]), r1 = face_rect(1, nx, ny, a.per[0], a.per[1]);
-    if (rect_count(r0) + rect_count(r1) > 0) {
+    const int64_t ff = frame_count(r0) + frame_count(r1);
+    const bool fast = rect_count(r0) + rect_count(r1) > 0;
+    const AdjointTape &t = h->tape;
+    const bool split = fast && ff > 0 && t.aux;
+    if (split) {
+        cudaEventRecord(t.fork, st);
+        cudaStreamWaitEvent(t.aux, t.fork, 0);
+    }
+    if (ff > 0) {
+        adj_faces_frame<T><<<blocks_for(ff, 8), 128, 0, split ? t.aux : st>>>(a, ff);  // eight interfaces per block
+        n++;
+    }
+    if (fast) {
         const int w = std::max(rect_empty(r0) ? 0 : r0.x1 - r0.x0 + 1, rect_empty(r1) ? 0 : r1.x1 - r1.x0 + 1);
         const int hh = std::max(rect_empty(r0) ? 0 : r0.y1 - r0.y0 + 1, rect_empty(r1) ? 0 : r1.y1 - r1.y0 + 1);
         adj_faces_fast<T><<<dim3((w + 31) / 32, (hh + 3) / 4, 2), dim3(32, 4), 0, st>>>(a);
         n++;
     }
-    const int64_t ff = frame_count(r0) + frame_count(r1);
-    if (ff > 0) {
-        adj_faces_frame<T><<<blocks_for(ff, 8), 128, 0, st>>>(a, ff);  // eight interfaces per block
-        n++;
+    if (split) {
+        cudaEventRecord(t.join, t.aux);
+        cudaStreamWaitEvent(st, t.join, 0);
     }
     {
         const Rect rc = cell_rect(nx, ny, a.per[0], a.per[1]);
@@ -951,6 +965,12 @@ int enqueue_adjoint(dugks_t h, const float *dL_dmom, float *dL_dfield, void *dL_
     if (e == cudaSuccess) e = cudaMemsetAsync(t.dW, 0, sizeof(double) * 2 * nwall, st);
     if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "adjoint: %s", cudaGetErrorString(e));
     AdjParams<T> a = base_params<T>(h, B);
+    if (!t.aux) {  // the second stream of the reverse steps, made once per tape
+        e = cudaStreamCreateWithFlags(&t.aux, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.join, cudaEventDisableTiming);
+        if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "adjoint: %s", cudaGetErrorString(e));
+    }
     {  // seed at the end of the rollout
         const double tend = (double)(t.step0 + t.steps) * h->dt;
         AdjParams<T> s = a;
@@ -1067,6 +1087,11 @@ void adjoint_release(dugks_t h) {
     if (t.h_wall) cudaFreeHost(t.h_wall);
     for (auto &gr : t.graphs) cudaGraphExecDestroy(gr.exec);
     t.graphs.clear();
+    if (t.fork) cudaEventDestroy(t.fork);
+    if (t.join) cudaEventDestroy(t.join);
+    if (t.aux) cudaStreamDestroy(t.aux);
+    t.aux = nullptr;
+    t.fork = t.join = nullptr;
     t.scratch = nullptr;
     t.dG = t.dW = t.dW_face = t.h_wall = nullptr;
     t.zero = nullptr;
