@@ -656,6 +656,9 @@ __global__ void __launch_bounds__(128, 4) adj_faces_fast(const AdjParams<T> a) {
 // The frame interfaces of both axes, one per half-warp.
 template <class T>
 __global__ void __launch_bounds__(128) adj_faces_frame(const AdjParams<T> a, int64_t ntot) {
+    // the interior interfaces, launched next as a programmatic dependent, need nothing of this
+    // kernel: let them start at once
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
     if (t < ntot) faces_frame_item(a, t);
 }
@@ -872,8 +875,10 @@ AdjParams<T> base_params(const dugks_t h, const AdjBufs &B) {
 // One reverse step at the state g~^n held in `state` (t_n = tn): lambda' in lam1 -> lam0.
 // Four launches: cell recompute, interior and frame interfaces, all cells (frame blocks first).
 // The two interface kernels write disjoint interfaces and read only the cell recompute's
-// output and lambda', so the frame ones run on the tape's second stream beside the interior
-// ones (fork after the cell recompute, join before the cells).
+// output and lambda', so they run side by side: the frame kernel first, and the interior one
+// launched as its programmatic dependent (it may start as soon as every frame block has
+// started, which the frame kernel signals at once). The cell recompute, before the frame
+// kernel, is complete by then; the cells kernel, an ordinary launch, waits for both.
 template <class T>
 cudaError_t reverse_step(AdjParams<T> a, const dugks_t h, const void *state, double tn, const void *lam1,
                          void *lam0, int64_t *launches) {
@@ -891,26 +896,25 @@ cudaError_t reverse_step(AdjParams<T> a, const dugks_t h, const void *state, dou
     int64_t n = 1;
     const Rect r0 = face_rect(0, nx, ny, a.per[0], a.per[1]), r1 = face_rect(1, nx, ny, a.per[0], a.per[1]);
     const int64_t ff = frame_count(r0) + frame_count(r1);
-    const bool fast = rect_count(r0) + rect_count(r1) > 0;
-    const AdjointTape &t = h->tape;
-    const bool split = fast && ff > 0 && t.aux;
-    if (split) {
-        cudaEventRecord(t.fork, st);
-        cudaStreamWaitEvent(t.aux, t.fork, 0);
-    }
     if (ff > 0) {
-        adj_faces_frame<T><<<blocks_for(ff, 8), 128, 0, split ? t.aux : st>>>(a, ff);  // eight interfaces per block
+        adj_faces_frame<T><<<blocks_for(ff, 8), 128, 0, st>>>(a, ff);  // eight interfaces per block
         n++;
     }
-    if (fast) {
+    if (rect_count(r0) + rect_count(r1) > 0) {
         const int w = std::max(rect_empty(r0) ? 0 : r0.x1 - r0.x0 + 1, rect_empty(r1) ? 0 : r1.x1 - r1.x0 + 1);
         const int hh = std::max(rect_empty(r0) ? 0 : r0.y1 - r0.y0 + 1, rect_empty(r1) ? 0 : r1.y1 - r1.y0 + 1);
-        adj_faces_fast<T><<<dim3((w + 31) / 32, (hh + 3) / 4, 2), dim3(32, 4), 0, st>>>(a);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((w + 31) / 32, (hh + 3) / 4, 2);
+        cfg.blockDim = dim3(32, 4);
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = ff > 0 ? 1 : 0;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, adj_faces_fast<T>, a);
+        if (e != cudaSuccess) return e;
         n++;
-    }
-    if (split) {
-        cudaEventRecord(t.join, t.aux);
-        cudaStreamWaitEvent(st, t.join, 0);
     }
     {
         const Rect rc = cell_rect(nx, ny, a.per[0], a.per[1]);
@@ -965,12 +969,6 @@ int enqueue_adjoint(dugks_t h, const float *dL_dmom, float *dL_dfield, void *dL_
     if (e == cudaSuccess) e = cudaMemsetAsync(t.dW, 0, sizeof(double) * 2 * nwall, st);
     if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "adjoint: %s", cudaGetErrorString(e));
     AdjParams<T> a = base_params<T>(h, B);
-    if (!t.aux) {  // the second stream of the reverse steps, made once per tape
-        e = cudaStreamCreateWithFlags(&t.aux, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.fork, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.join, cudaEventDisableTiming);
-        if (e != cudaSuccess) return handle_fail(h, DUGKS_E_CUDA, "adjoint: %s", cudaGetErrorString(e));
-    }
     {  // seed at the end of the rollout
         const double tend = (double)(t.step0 + t.steps) * h->dt;
         AdjParams<T> s = a;
@@ -1087,11 +1085,6 @@ void adjoint_release(dugks_t h) {
     if (t.h_wall) cudaFreeHost(t.h_wall);
     for (auto &gr : t.graphs) cudaGraphExecDestroy(gr.exec);
     t.graphs.clear();
-    if (t.fork) cudaEventDestroy(t.fork);
-    if (t.join) cudaEventDestroy(t.join);
-    if (t.aux) cudaStreamDestroy(t.aux);
-    t.aux = nullptr;
-    t.fork = t.join = nullptr;
     t.scratch = nullptr;
     t.dG = t.dW = t.dW_face = t.h_wall = nullptr;
     t.zero = nullptr;

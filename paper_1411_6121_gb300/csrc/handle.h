@@ -38,10 +38,6 @@ struct AdjointTape {
         int64_t launches;
     };
     std::vector<SegGraph> graphs;
-    // A second stream for the frame interfaces of a reverse step, which run beside the interior
-    // ones (fork and join by these events; captured as parallel branches of a segment graph).
-    cudaStream_t aux = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 }  // namespace dugks
