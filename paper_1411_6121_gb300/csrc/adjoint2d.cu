@@ -641,26 +641,27 @@ __device__ __noinline__ void faces_frame_item(const AdjParams<T> &a, int64_t t) 
     }
 }
 
-// Interior interfaces of both axes (blockIdx.z = axis), 2D blocks over the fast rectangle.
+// Every interface of both axes in one launch of 128-thread blocks: the frame blocks first
+// (eight frame interfaces per block, one per half-warp), then 32 x 4 tiles of the interior
+// rectangle of x interfaces (nt0 tiles, tx0 per row), then those of y interfaces (tx1 per row).
 template <class T>
-__global__ void __launch_bounds__(128, 4) adj_faces_fast(const AdjParams<T> a) {
-    const int d = blockIdx.z;
+__global__ void __launch_bounds__(128, 6) adj_faces_all(const AdjParams<T> a, int64_t nframe, int nfb, int nt0,
+                                                         int tx0, int tx1) {
+    if ((int)blockIdx.x < nfb) {
+        const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+        if (t < nframe) faces_frame_item(a, t);
+        return;
+    }
+    int b = (int)blockIdx.x - nfb;
+    const int d = b < nt0 ? 0 : 1;
+    if (d) b -= nt0;
+    const int tx = d ? tx1 : tx0;
     const Rect r = face_rect(d, a.n[0], a.n[1], a.per[0], a.per[1]);
-    const int i = r.x0 + blockIdx.x * blockDim.x + threadIdx.x, j = r.y0 + blockIdx.y * blockDim.y + threadIdx.y;
+    const int i = r.x0 + (b % tx) * 32 + (threadIdx.x & 31), j = r.y0 + (b / tx) * 4 + (threadIdx.x >> 5);
     if (i > r.x1 || j > r.y1) return;
     const int64_t f = fidx(a, d, i, j);
     if (d == 0) face_fast<T, 0>(a, i, j, f, nface(a, 0));
     else face_fast<T, 1>(a, i, j, f, nface(a, 1));
-}
-
-// The frame interfaces of both axes, one per half-warp.
-template <class T>
-__global__ void __launch_bounds__(128) adj_faces_frame(const AdjParams<T> a, int64_t ntot) {
-    // the interior interfaces, launched next as a programmatic dependent, need nothing of this
-    // kernel: let them start at once
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
-    if (t < ntot) faces_frame_item(a, t);
 }
 
 // dL/dGh summed over the interfaces whose acceleration averages cell (x, y), with the
@@ -873,12 +874,8 @@ AdjParams<T> base_params(const dugks_t h, const AdjBufs &B) {
 }
 
 // One reverse step at the state g~^n held in `state` (t_n = tn): lambda' in lam1 -> lam0.
-// Four launches: cell recompute, interior and frame interfaces, all cells (frame blocks first).
-// The two interface kernels write disjoint interfaces and read only the cell recompute's
-// output and lambda', so they run side by side: the frame kernel first, and the interior one
-// launched as its programmatic dependent (it may start as soon as every frame block has
-// started, which the frame kernel signals at once). The cell recompute, before the frame
-// kernel, is complete by then; the cells kernel, an ordinary launch, waits for both.
+// Three launches: cell recompute, all interfaces (frame blocks first), all cells (frame blocks
+// first).
 template <class T>
 cudaError_t reverse_step(AdjParams<T> a, const dugks_t h, const void *state, double tn, const void *lam1,
                          void *lam0, int64_t *launches) {
@@ -894,27 +891,17 @@ cudaError_t reverse_step(AdjParams<T> a, const dugks_t h, const void *state, dou
     const int64_t nc = h->ncell;
     adj_cells_fwd<T><<<blocks_for(nc, 256), 256, 0, st>>>(a);
     int64_t n = 1;
-    const Rect r0 = face_rect(0, nx, ny, a.per[0], a.per[1]), r1 = face_rect(1, nx, ny, a.per[0], a.per[1]);
-    const int64_t ff = frame_count(r0) + frame_count(r1);
-    if (ff > 0) {
-        adj_faces_frame<T><<<blocks_for(ff, 8), 128, 0, st>>>(a, ff);  // eight interfaces per block
-        n++;
-    }
-    if (rect_count(r0) + rect_count(r1) > 0) {
-        const int w = std::max(rect_empty(r0) ? 0 : r0.x1 - r0.x0 + 1, rect_empty(r1) ? 0 : r1.x1 - r1.x0 + 1);
-        const int hh = std::max(rect_empty(r0) ? 0 : r0.y1 - r0.y0 + 1, rect_empty(r1) ? 0 : r1.y1 - r1.y0 + 1);
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((w + 31) / 32, (hh + 3) / 4, 2);
-        cfg.blockDim = dim3(32, 4);
-        cfg.stream = st;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        at[0].val.programmaticStreamSerializationAllowed = ff > 0 ? 1 : 0;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        const cudaError_t e = cudaLaunchKernelEx(&cfg, adj_faces_fast<T>, a);
-        if (e != cudaSuccess) return e;
-        n++;
+    {
+        const Rect r0 = face_rect(0, nx, ny, a.per[0], a.per[1]), r1 = face_rect(1, nx, ny, a.per[0], a.per[1]);
+        const int64_t nframe = frame_count(r0) + frame_count(r1);
+        const int nfb = (int)((nframe + 7) / 8);
+        const int tx0 = rect_empty(r0) ? 0 : (r0.x1 - r0.x0 + 32) / 32, ty0 = rect_empty(r0) ? 0 : (r0.y1 - r0.y0 + 4) / 4;
+        const int tx1 = rect_empty(r1) ? 0 : (r1.x1 - r1.x0 + 32) / 32, ty1 = rect_empty(r1) ? 0 : (r1.y1 - r1.y0 + 4) / 4;
+        const int nb = nfb + tx0 * ty0 + tx1 * ty1;
+        if (nb > 0) {
+            adj_faces_all<T><<<nb, 128, 0, st>>>(a, nframe, nfb, tx0 * ty0, tx0, tx1);
+            n++;
+        }
     }
     {
         const Rect rc = cell_rect(nx, ny, a.per[0], a.per[1]);
