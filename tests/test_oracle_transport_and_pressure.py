@@ -22,13 +22,25 @@
    steady solution u = dp / (2 rho0 nu L) y (H - y) with p linear in x. The oracle reproduces
    the linear pressure exactly (to rounding), the parabola at second order under refinement,
    and D3Q19 on the same flow, uniform along z, reproduces D2Q9 (D3Q19 projected onto the
-   x-y plane is D2Q9: weights 1/3 + 2/18 = 4/9, 1/18 + 2/36 = 1/9, 1/36)."""
+   x-y plane is D2Q9: weights 1/3 + 2/18 = 4/9, 1/18 + 2/36 = 1/9, 1/36).
+
+3. The 3D scheme on a forced shear flow: u_x = u0 sin(2 pi y) sin(2 pi z) with
+   F_x = 8 pi^2 nu u_x is an exact steady Navier-Stokes solution (u . grad u = 0 and
+   nu lap u = -F). The steady field of the oracle is exactly this mode (its remainder is at
+   rounding), and its amplitude converges at second order in dx at a fixed time step, to a
+   limit within the Knudsen scale (k tau c)^2 of u0. This pins the 3D lattices, the force
+   term and the viscosity (eq. tau = nu / RT) in a second flow. It does not pin the
+   tangential gradients: dropping them, flipping their sign, halving them or taking the
+   cross points as the mean of two cells moves the converged amplitude by at most 1e-3 of
+   itself (5e-5 on D3Q19), because the steady flux hardly depends on them; test 1 is their
+   pin."""
 import numpy as np
 import pytest
 
 from oracle import Oracle
 from oracle.oracle import rel_change
 from paper_1411_6121_gb300 import workloads as W
+from tests import analytic as A
 
 DT = 0.5
 KAPPA = 0.5 * DT  # h c / dx with RT = 1/3 (c = 1), dx = 1
@@ -133,3 +145,45 @@ def test_neq_pressure_poiseuille():
     assert np.abs(m19[:, 0] - m19[:, 1]).max() < 1e-14
     assert np.abs(m19[[0, 1, 2], 0] - m8).max() < 1e-10 * np.abs(m8).max()
     assert np.abs(m19[3]).max() < 1e-14
+
+
+def _forced_shear_amplitude(q, N, dt, rt=5.0, nu=0.01, u0=1e-3):
+    """Steady amplitude of u_x on the mode sin(2 pi y) sin(2 pi z), over u0, on a 1 x N x N
+    periodic box (the flow is uniform along x)."""
+    dx = 1.0 / N
+    c = A.cell_centres(N)
+    Z, Y = np.meshgrid(c, c, indexing="ij")
+    mode = (np.sin(2 * np.pi * Y) * np.sin(2 * np.pi * Z)).ravel()  # x fastest, then y, then z
+    field = np.zeros((3, N * N))
+    field[0] = 8 * np.pi ** 2 * nu * u0 * mode
+    o = Oracle((1, N, N), q, nu=nu, dt=dt, dx=dx, rt=rt, field=field, bcs=W.all_periodic())
+    u = np.zeros((3, N * N))
+    u[0] = u0 * mode
+    o.init(u=u)
+    K = max(1, int(round(0.2 / (nu * 8 * np.pi ** 2) / dt)))  # e^-0.2 of the slowest mode
+    prev = o.moments()[1:]
+    while True:
+        o.step(K)
+        cur = o.moments()[1:]
+        if rel_change(cur, prev) < 1e-7:
+            break
+        prev = cur
+    a = (cur[0] @ mode) / (mode @ mode)
+    # the steady field is the mode: nothing else is forced, and the cross flow stays zero
+    assert np.linalg.norm(cur[0] - a * mode) < 1e-8 * np.linalg.norm(a * mode)
+    assert np.abs(cur[1:]).max() < 1e-8 * u0
+    return a / u0
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_forced_shear_3d_second_order(q):
+    rt, nu = 5.0, 0.01
+    dt = 0.5 / 32 / np.sqrt(3 * rt)  # CFL 0.5 on the finest mesh, the same step on all three
+    a = [_forced_shear_amplitude(q, N, dt, rt, nu) for N in (8, 16, 32)]
+    ratio = (a[0] - a[1]) / (a[1] - a[2])
+    assert abs(ratio - 4.0) < 0.3, (a, ratio)  # oracle: 4.15 on both lattices
+    limit = a[2] + (a[2] - a[1]) / (ratio - 1)
+    k = 2 * np.pi * np.sqrt(2)
+    knudsen = (k * nu / rt * np.sqrt(3 * rt)) ** 2  # (k tau c)^2 = 0.0047
+    assert abs(limit - 1.0) < knudsen, (limit, knudsen)  # oracle: 1 - 1.2e-4 (D3Q19), 1 + 1.2e-3 (D3Q27)
+    assert a[2] - 1.0 < 0.01  # the finest mesh within 1%
