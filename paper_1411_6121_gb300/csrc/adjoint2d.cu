@@ -67,6 +67,9 @@ struct AdjParams {
     const T *state;          // g~^n (padded layout)
     T *phi;                  // [Q][ncell] fbar+ of the cells
     T *mom;                  // [3][ncell] drho, m_x, m_y of the cells (m in units of c)
+    const T *nstate;         // g~^{n-1} for the next reverse step's recompute, or null
+    T nctc;                  // cos(omega t_{n-1}) / c
+    T *nmom;                 // its cell moments (the other moments buffer)
     const T *lam1;           // lambda' [Q][ncell]
     T *fb[2];                // adjoint of the step-4 values [Q][nface_d]
     T *gb[2];                // adjoint of the interface acceleration Gh [2][nface_d]
@@ -572,27 +575,37 @@ __device__ __forceinline__ void cell_fast(const AdjParams<T> &a, int x, int y, i
 }
 
 // ---- kernels ----
+// fbar+ (step 1, eq. f_bar_+) and the moments (eq. macro_values) of cell c of `state` into
+// a.phi and `mom`, with ctc = cos(omega t) / c at that state's time. Not inlined: the
+// recompute kernel and the cells kernel that carries the next step's recompute run the same
+// code, so the sweep's bits do not depend on which of them computed a step.
+template <class T>
+__device__ __noinline__ void fwd_cell(const AdjParams<T> &a, const T *state, T ctc, T *mom, int64_t c) {
+    const int64_t nc = ncell(a);
+    const int x = (int)(c % a.n[0]), y = (int)(c / a.n[0]);
+    T g[Q], Gh[2], dr, m[2];
+#pragma unroll
+    for (int k = 0; k < Q; k++) g[k] = state[k * a.dstride + (int64_t)y * a.px + x];
+#pragma unroll
+    for (int comp = 0; comp < 2; comp++) Gh[comp] = (a.g[comp] + field_at(a, comp, x, y)) * ctc;
+    moments2(a, g, Gh, a.wcell, dr, m);
+    const T gm = (Gh[0] * m[0] + Gh[1] * m[1]) * a.inv_rho0;
+#pragma unroll
+    for (int k = 0; k < Q; k++) {
+        const T q = geq(a, k, dr, m);
+        const T s = T(3) * (Gh[0] * (T)L9::e(k, 0) + Gh[1] * (T)L9::e(k, 1) - gm);
+        a.phi[k * nc + c] = g[k] + a.b1 * (q - g[k]) + a.c1 * s * (L9::wt<T>(k) * a.rho0 + q);
+    }
+    mom[c] = dr;
+    mom[nc + c] = m[0];
+    mom[2 * nc + c] = m[1];
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) adj_cells_fwd(const AdjParams<T> a) {
     const int64_t nc = ncell(a);
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(c % a.n[0]), y = (int)(c / a.n[0]);
-        T g[Q], Gh[2], dr, m[2];
-        #pragma unroll
-        for (int k = 0; k < Q; k++) g[k] = a.state[k * a.dstride + (int64_t)y * a.px + x];
-        cell_Gh(a, x, y, Gh);
-        moments2(a, g, Gh, a.wcell, dr, m);
-        const T gm = (Gh[0] * m[0] + Gh[1] * m[1]) * a.inv_rho0;
-        #pragma unroll
-        for (int k = 0; k < Q; k++) {
-            const T q = geq(a, k, dr, m);
-            const T s = T(3) * (Gh[0] * (T)L9::e(k, 0) + Gh[1] * (T)L9::e(k, 1) - gm);
-            a.phi[k * nc + c] = g[k] + a.b1 * (q - g[k]) + a.c1 * s * (L9::wt<T>(k) * a.rho0 + q);
-        }
-        a.mom[c] = dr;
-        a.mom[nc + c] = m[0];
-        a.mom[2 * nc + c] = m[1];
-    }
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x)
+        fwd_cell(a, a.state, a.ctc, a.mom, c);
 }
 
 // The t-th interface of the frame of both axes (walls: NEQ and dL/du_w; x_c interfaces;
@@ -741,19 +754,28 @@ __device__ __noinline__ void cells_frame_item(const AdjParams<T> &a, int64_t t) 
 
 // All cells in one launch of 128-thread blocks: frame blocks first (a half-warp per frame cell),
 // then 32 x 4 tiles of the fast rectangle (tx x ty blocks).
+// With a.nstate set, the blocks then recompute the next reverse step's fbar+ and moments,
+// one cell per thread, the interior tiles first (the frame blocks are the longest): this
+// step's interfaces no longer read a.phi, and each cell's moments go to the other buffer, so
+// no block reads what another overwrites.
 template <class T>
-__global__ void __launch_bounds__(128) adj_cells_all(const AdjParams<T> a, int nfb, int tx, int ty) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 7 : 5) adj_cells_all(const AdjParams<T> a, int nfb, int tx, int ty) {
+    const Rect r = cell_rect(a.n[0], a.n[1], a.per[0], a.per[1]);
     if ((int)blockIdx.x < nfb) {  // eight frame cells per block, one per half-warp
-        const Rect r = cell_rect(a.n[0], a.n[1], a.per[0], a.per[1]);
         const int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 4);
         if (t < frame_count(r)) cells_frame_item(a, t);
-        return;
+    } else {
+        const int b = blockIdx.x - nfb;
+        const int x = r.x0 + (b % tx) * 32 + (threadIdx.x & 31), y = r.y0 + (b / tx) * 4 + (threadIdx.x >> 5);
+        if (x <= r.x1 && y <= r.y1) cell_fast(a, x, y, x + (int64_t)a.n[0] * y);
     }
-    const int b = blockIdx.x - nfb;
-    const Rect r = cell_rect(a.n[0], a.n[1], a.per[0], a.per[1]);
-    const int x = r.x0 + (b % tx) * 32 + (threadIdx.x & 31), y = r.y0 + (b / tx) * 4 + (threadIdx.x >> 5);
-    if (x > r.x1 || y > r.y1) return;
-    cell_fast(a, x, y, x + (int64_t)a.n[0] * y);
+    if (a.nstate) {
+        const int64_t nc = ncell(a);
+        const int nb = (int)gridDim.x, bi = (int)blockIdx.x;
+        const int rb = bi >= nfb ? bi - nfb : bi + (nb - nfb);  // tiles take blocks 0 .. nb - nfb - 1
+        for (int64_t c = rb * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)nb * blockDim.x)
+            fwd_cell(a, a.nstate, a.nctc, a.nmom, c);
+    }
 }
 
 // Loss seed from dL/d(moments) [3][ncell] (p, u_x, u_y as dugks_moments returns them):
@@ -804,14 +826,14 @@ int blocks_for(int64_t n, int threads) {
 
 // Work buffers carved from one allocation (element size es, 256-byte aligned pieces).
 struct AdjBufs {
-    void *phi, *mom, *fb[2], *gb[2], *lam[2];
+    void *phi, *mom[2], *fb[2], *gb[2], *lam[2];
 };
 
 size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 
 size_t scratch_bytes(int64_t nx, int64_t ny, size_t es) {
     const int64_t nc = nx * ny, n0 = (nx + 1) * ny, n1 = nx * (ny + 1);
-    return al256(es * Q * nc) + al256(es * 3 * nc) + al256(es * Q * n0) + al256(es * Q * n1) + al256(es * 2 * n0) +
+    return al256(es * Q * nc) + 2 * al256(es * 3 * nc) + al256(es * Q * n0) + al256(es * Q * n1) + al256(es * 2 * n0) +
            al256(es * 2 * n1) + 2 * al256(es * Q * nc);
 }
 
@@ -820,7 +842,8 @@ AdjBufs carve(void *base, int64_t nx, int64_t ny, size_t es) {
     char *p = (char *)base;
     AdjBufs B;
     B.phi = p; p += al256(es * Q * nc);
-    B.mom = p; p += al256(es * 3 * nc);
+    B.mom[0] = p; p += al256(es * 3 * nc);
+    B.mom[1] = p; p += al256(es * 3 * nc);
     B.fb[0] = p; p += al256(es * Q * n0);
     B.fb[1] = p; p += al256(es * Q * n1);
     B.gb[0] = p; p += al256(es * 2 * n0);
@@ -863,7 +886,7 @@ AdjParams<T> base_params(const dugks_t h, const AdjBufs &B) {
     a.g[1] = (T)p.g[1];
     a.field = p.field;
     a.phi = (T *)B.phi;
-    a.mom = (T *)B.mom;
+    a.mom = (T *)B.mom[0];
     for (int d = 0; d < 2; d++) {
         a.fb[d] = (T *)B.fb[d];
         a.gb[d] = (T *)B.gb[d];
@@ -873,24 +896,40 @@ AdjParams<T> base_params(const dugks_t h, const AdjBufs &B) {
     return a;
 }
 
-// One reverse step at the state g~^n held in `state` (t_n = tn): lambda' in lam1 -> lam0.
-// Three launches: cell recompute, all interfaces (frame blocks first), all cells (frame blocks
-// first).
+// cos(omega t) / c at the time t of a state, as the recompute of that state uses it.
+template <class T>
+T force_factor(const dugks_t h, double t) {
+    return (T)(cos(h->force.omega * t) * (1.0 / h->c));
+}
+
+// One reverse step at the state g~^n held in `state` (t_n = tn): lambda' in lam1 -> lam0,
+// with the cell moments of g~^n in `mom`. Launches: the cell recompute unless the previous
+// reverse step's cells kernel made it (have_fwd), all interfaces (frame blocks first), and
+// all cells (frame blocks first), which also recompute g~^{n-1} = `next` (at time tnext) into
+// a.phi and `nmom` when `next` is given.
 template <class T>
 cudaError_t reverse_step(AdjParams<T> a, const dugks_t h, const void *state, double tn, const void *lam1,
-                         void *lam0, int64_t *launches) {
+                         void *lam0, void *mom, bool have_fwd, const void *next, double tnext, void *nmom,
+                         int64_t *launches) {
     const double om = h->force.omega, inv_c = 1.0 / h->c;
-    a.ctc = (T)(cos(om * tn) * inv_c);
+    a.ctc = force_factor<T>(h, tn);
     a.cthc = (T)(cos(om * (tn + 0.5 * h->dt)) * inv_c);
     a.cwh = (T)cos(om * (tn + 0.5 * h->dt));
     a.state = (const T *)state;
     a.lam1 = (const T *)lam1;
     a.lam0 = (T *)lam0;
+    a.mom = (T *)mom;
+    a.nstate = (const T *)next;
+    a.nmom = (T *)nmom;
+    a.nctc = next ? force_factor<T>(h, tnext) : T(0);
     cudaStream_t st = h->stream;
     const int nx = (int)h->nx, ny = (int)h->ny;
     const int64_t nc = h->ncell;
-    adj_cells_fwd<T><<<blocks_for(nc, 256), 256, 0, st>>>(a);
-    int64_t n = 1;
+    int64_t n = 0;
+    if (!have_fwd) {
+        adj_cells_fwd<T><<<blocks_for(nc, 256), 256, 0, st>>>(a);
+        n++;
+    }
     {
         const Rect r0 = face_rect(0, nx, ny, a.per[0], a.per[1]), r1 = face_rect(1, nx, ny, a.per[0], a.per[1]);
         const int64_t nframe = frame_count(r0) + frame_count(r1);
@@ -935,9 +974,14 @@ cudaError_t enqueue_segment(dugks_t h, const AdjParams<T> &a, const AdjBufs &B, 
         if (e != cudaSuccess) return e;
         (*launches)++;
     }
+    // step j's cell moments are in mom[j & 1]; each cells kernel but the segment's last also
+    // recomputes step j - 1
     for (int64_t j = len - 1; j >= 0; j--) {
         const double tn = (double)(t.step0 + start + j) * h->dt;
-        cudaError_t e = reverse_step<T>(a, h, t.seg[(size_t)j], tn, B.lam[cur], B.lam[cur ^ 1], launches);
+        const double tprev = (double)(t.step0 + start + j - 1) * h->dt;
+        cudaError_t e = reverse_step<T>(a, h, t.seg[(size_t)j], tn, B.lam[cur], B.lam[cur ^ 1], B.mom[j & 1],
+                                        j < len - 1, j > 0 ? t.seg[(size_t)j - 1] : nullptr, tprev,
+                                        B.mom[(j - 1) & 1], launches);
         if (e != cudaSuccess) return e;
         cur ^= 1;
     }
