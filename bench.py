@@ -67,12 +67,38 @@ def hbm_peak():
         return 6800.0, "fallback"
 
 
+def strip_comments(src):
+    """C/C++ source without its comments and blank lines (string and character literals kept)."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        elif c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        else:
+            out.append(c)
+            i += 1
+    lines = (l.rstrip() for l in "".join(out).splitlines())
+    return "\n".join(l for l in lines if l)
+
+
 def kernel_source_hash():
+    """Hash of the step kernels' code (comments excluded), to tell whether the DRAM counters of
+    the committed profile were taken on this code."""
     h = hashlib.sha1()
     for name in ("dugks_step3d.cuh", "dugks_step3d_ws.cuh", "tma.cuh", "dugks_step.cuh", "dugks_device.cuh",
                  "step3d_q19.cu"):
-        with open(os.path.join(ROOT, "paper_1411_6121_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1411_6121_gb300", "csrc", name), encoding="utf-8") as f:
+            h.update(strip_comments(f.read()).encode())
     return h.hexdigest()[:12]
 
 

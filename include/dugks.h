@@ -3,7 +3,7 @@
  * gas kinetic scheme (DUGKS) with force term of Wu, Shi, Chai and Wang (arXiv 1411.6121).
  *
  * One handle (dugks_t) owns one simulation on one CUDA device: the cell-averaged
- * distribution f~ of the paper (Sec. 2.2, eq. evolution_equation) on a uniform Cartesian
+ * distribution f~ of the paper (Sec. 2.2, eq. (16)) on a uniform Cartesian
  * mesh with the D2Q9 or D3Q19 (or D3Q27) velocity set, and everything the time step needs.
  * Every entry point returns DUGKS_OK (0) or a negative DUGKS_E_* code; none throws,
  * aborts or exits. dugks_last_error() gives a one-line reason for the last failure on a
@@ -65,14 +65,14 @@ extern "C" {
 
 /* Boundary conditions of Sec. 2.4 applied at a domain face. */
 #define DUGKS_BC_PERIODIC 0
-#define DUGKS_BC_NEQ_VELOCITY 1 /* eq. NEQ, velocity condition: u_a = u_w, rho_a = rho(x_c)  */
-#define DUGKS_BC_NEQ_PRESSURE 2 /* eq. NEQ, pressure condition: rho_a = rho0 + p_w/RT, u_a = u(x_c) */
-#define DUGKS_BC_BOUNCE_BACK 3  /* eq. BB: fbar_k = fbar_-k + 2 rho0 W_k xi_k.u_w / RT for xi.n < 0
+#define DUGKS_BC_NEQ_VELOCITY 1 /* eq. (32), velocity condition: u_a = u_w, rho_a = rho(x_c)  */
+#define DUGKS_BC_NEQ_PRESSURE 2 /* eq. (32), pressure condition: rho_a = rho0 + p_w/RT, u_a = u(x_c) */
+#define DUGKS_BC_BOUNCE_BACK 3  /* eq. (31): fbar_k = fbar_-k + 2 rho0 W_k xi_k.u_w / RT for xi.n < 0
                                    (rho_w = rho0), at the wall interface before step 6        */
 
-/* Equilibrium models (Sec. 2.1-2.2). The incompressible model is the paper's: eq. icfeq with
- * rho0 u = sum xi f~ + rho0 G dt/2 (eq. macro_values). The original DUGKS, the model it is
- * compared against, uses eq. feq with rho u = sum xi f~ + rho G dt/2. */
+/* Equilibrium models (Sec. 2.1-2.2). The incompressible model is the paper's: eq. (6) with
+ * rho0 u = sum xi f~ + rho0 G dt/2 (eq. (27)). The original DUGKS, the model it is
+ * compared against, uses eq. (5) with rho u = sum xi f~ + rho G dt/2. */
 #define DUGKS_MODEL_INCOMPRESSIBLE 0
 #define DUGKS_MODEL_ORIGINAL 1
 
@@ -105,7 +105,7 @@ typedef struct {
     dugks_face_bc face[6]; /* -x, +x, -y, +y, -z, +z */
 } dugks_boundaries;
 
-/* Acceleration G(x, t) = (g + field(x)) * cos(omega t) of eq. S (Sec. 2.2). field is a
+/* Acceleration G(x, t) = (g + field(x)) * cos(omega t) of eq. (9) (Sec. 2.2). field is a
  * DEVICE pointer to [dim][ncell] floats or NULL; the handle reads it during every step, so
  * it must stay valid (and may be rewritten between steps) until it is replaced by
  * dugks_set_force_field or the handle is destroyed. */
@@ -148,7 +148,7 @@ int dugks_create(const dugks_mesh *mesh, int32_t lattice, double nu, double dt,
                  const dugks_opts *opts, dugks_t *out);
 
 /* Initial state as in Sec. 3 ("the equilibrium distribution is initialised by"):
- * f~ = f_eq(rho0 + p/RT, u) of eq. icfeq, computed on the device. p: HOST [ncell] doubles
+ * f~ = f_eq(rho0 + p/RT, u) of eq. (6), computed on the device. p: HOST [ncell] doubles
  * or NULL (p = 0); u: HOST [dim][ncell] doubles or NULL (rest). Resets the clock to t = 0.
  * Synchronous. */
 int dugks_init(dugks_t h, const double *p, const double *u);
@@ -157,7 +157,7 @@ int dugks_init(dugks_t h, const double *p, const double *u);
  * per step). Asynchronous; returns after enqueueing. */
 int dugks_step(dugks_t h, int64_t n);
 
-/* Macroscopic fields of the current state (eq. macro_values with G(t)):
+/* Macroscopic fields of the current state (eq. (27) with G(t)):
  * out[0][n] = p = (rho - rho0) RT, out[1+a][n] = u_a, i.e. [dim+1][ncell] floats.
  * out_is_device: 1 if out is device memory, 0 for host memory (pinned or pageable).
  * Synchronous. */
@@ -287,7 +287,7 @@ void dugks_batch_destroy(dugks_batch_t b);
  *   nx, ny, nz, lattice: the mesh and velocity set (nz = 1 and DUGKS_D2Q9 in 2D).
  *   rt, rho0: RT and rho0 of the simulation.
  *   shift:  HOST [3] doubles or NULL: the uniform part of the velocity shift of eq.
- *           macro_values, G(t) dt/2 (u = c/rho0 sum_k e_k g~_k + shift).
+ *           (27), G(t) dt/2 (u = c/rho0 sum_k e_k g~_k + shift).
  *   shift_field: DEVICE [dim][ncell] floats or NULL: the per-cell part of that shift.
  *   uprev:  DEVICE [dim][ncell] doubles owned by the caller: the velocity of the previous
  *           call, read when have_prev != 0 and overwritten with the current velocity.

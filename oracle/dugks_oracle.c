@@ -29,29 +29,29 @@
  *      wall normal, applied axis by axis (x, then y, then z) over the already-extended
  *      range of the earlier axes, which fills edge and corner ghosts. Periodic axes fill
  *      their ghost layer with the periodic image.
- *  R4  NEQ boundary (Sec. 2.4, eq. NEQ): x_c is the midpoint of the boundary cell's
+ *  R4  NEQ boundary (Sec. 2.4, eq. (32)): x_c is the midpoint of the boundary cell's
  *      interface opposite the wall; (rho_c, u_c) are the step-6 moments of the step-4
  *      value there. Velocity condition: u_a = u_w, rho_a = rho_c. Pressure condition:
  *      rho_a = rho0 + p_w / RT, u_a = u_c. Applied, as the Appendix's step 5 says, to
  *      fbar before step 7, only for xi . n < 0 (n the outward normal of the domain), with
- *      the equilibrium of eq. icfeq.
+ *      the equilibrium of eq. (6).
  *  R5  Step 3 cross points: the mean of the 4 cells that share the cross point (the
  *      vertex in 2D, the edge midpoint in 3D). Step 4 tangential gradients difference the
  *      two cross points on the interface; the normal gradient differences the two cells.
- *  R6  The cell moments entering step 1 are those of the current F (eq. macro_values,
+ *  R6  The cell moments entering step 1 are those of the current F (eq. (27),
  *      i.e. step 10 of the previous step, or of the initial F at the first step).
- *  R7  Initial state: F = f_eq(rho0 + p/RT, u) of eq. icfeq (the paper initialises "the
+ *  R7  Initial state: F = f_eq(rho0 + p/RT, u) of eq. (6) (the paper initialises "the
  *      equilibrium distribution" from the fields), with no force correction.
  *  R8  D3Q19 (not in the paper, which uses D3Q27) is the D3Q27 set of Sec. 2.3 with its 8
  *      corner velocities removed and the standard weights 1/3, 1/18, 1/36; it has the
- *      same moments up to fourth order, which is all eq. icfeq uses.
+ *      same moments up to fourth order, which is all eq. (6) uses.
  *  R9  Pressure p = (rho - rho0) RT (the paper initialises rho = rho0 + p/RT).
- *  R14 Bounce-back (Sec. 2.4, eq. BB) is applied, like NEQ, to fbar at the wall interface
+ *  R14 Bounce-back (Sec. 2.4, eq. (31)) is applied, like NEQ, to fbar at the wall interface
  *      in the Appendix's step 5: for xi_k . n < 0, fbar_k = fbar_(-k) + 2 rho_w W_k
  *      xi_k . u_w / RT, with the opposite velocity's step-4 value at the same interface
  *      and rho_w = rho0 (the incompressible limit the paper names).
- *  R16 The original DUGKS (the comparison model of Sec. 2.1 and 2.2, model = 1): eq. feq
- *      in place of eq. icfeq everywhere f_eq appears (step 1, the NEQ equilibria, step 7,
+ *  R16 The original DUGKS (the comparison model of Sec. 2.1 and 2.2, model = 1): eq. (5)
+ *      in place of eq. (6) everywhere f_eq appears (step 1, the NEQ equilibria, step 7,
  *      the force term S, the initial state), with rho u = sum xi f~ + rho G dt/2 at cells
  *      and the same with h at interfaces; the incompressible model is model = 0.
  *  R17 Oscillating wall pressure (the pressure-driven Womersley flow of Sec. 3.3): a
@@ -109,8 +109,8 @@ typedef struct {
     int bc_type[6];   /* faces -x,+x,-y,+y,-z,+z */
     double bc_u[6][3];/* wall velocity u_w (velocity condition) */
     double bc_p[6];   /* wall pressure p_w (pressure condition) */
-    int model;        /* 0: the incompressible model (eq. icfeq, eq. macro_values);
-                         1: the original DUGKS (eq. feq, rho u = sum xi f~ + rho G dt/2) */
+    int model;        /* 0: the incompressible model (eq. (6), eq. (27));
+                         1: the original DUGKS (eq. (5), rho u = sum xi f~ + rho G dt/2) */
     double bc_p_amp[6];/* pressure condition: p_w(t) = bc_p + bc_p_amp cos(omega t) */
     const double *faces[3]; /* non-uniform mesh (reading R18): the n+1 interface
                                coordinates per axis, or NULL for uniform spacing dx */
@@ -187,7 +187,7 @@ static void build_lattice(ostate *s)
 }
 
 /* ---------------------------------------------------------------------------------
- * Equilibrium of the incompressible model, eq. icfeq:
+ * Equilibrium of the incompressible model, eq. (6):
  *   f_eq_k = W_k { rho + rho0 [ xi_k.u/RT + (xi_k.u)^2/(2 RT^2) - |u|^2/(2RT) ] }.
  * --------------------------------------------------------------------------------- */
 static real feq(const ostate *s, int k, real rho, const real u[3])
@@ -199,12 +199,12 @@ static real feq(const ostate *s, int k, real rho, const real u[3])
         uu += u[a] * u[a];
     }
     const real bracket = xu / rt + xu * xu / (2.0 * rt * rt) - uu / (2.0 * rt);
-    /* the original DUGKS (reading R16), eq. feq: W_k rho [1 + bracket] */
+    /* the original DUGKS (reading R16), eq. (5): W_k rho [1 + bracket] */
     if (s->cfg.model == 1) return s->W[k] * rho * (1.0 + bracket);
     return s->W[k] * (rho + rho0 * bracket);
 }
 
-/* Force term, eq. S: S_k = G.(xi_k - u)/RT f_eq_k (with f_eq of eq. icfeq). */
+/* Force term, eq. (9): S_k = G.(xi_k - u)/RT f_eq_k (with f_eq of eq. (6)). */
 static real source(const ostate *s, int k, const real G[3], const real u[3], real fe)
 {
     real gx = 0;
@@ -220,7 +220,7 @@ static int opposite(const ostate *s, int k)
     return k;
 }
 
-/* Macroscopic variables, eq. macro_values (cell, weight dt/2) and the Appendix's step 6
+/* Macroscopic variables, eq. (27) (cell, weight dt/2) and the Appendix's step 6
  * (interface, weight h/2): rho = sum_k f_k, rho0 u = sum_k xi_k f_k + rho0 G w. The original
  * DUGKS (reading R16) divides by and weights the force with rho instead:
  * rho u = sum_k xi_k f_k + rho G w. */
@@ -340,9 +340,9 @@ static void step_once(ostate *s)
     const double t = s->t;
     int x[3];
 
-    /* Step 1: fbar+ at X_c from eq. f_bar_+:
+    /* Step 1: fbar+ at X_c from eq. (24):
      *   fbar+ = (2tau-h)/(2tau+dt) f~ + 3h/(2tau+dt) f_eq + 3 tau h/(2tau+dt) S,
-     * with rho, u the moments of f~ (eq. macro_values, reading R6). */
+     * with rho, u the moments of f~ (eq. (27), reading R6). */
     const double a1 = (2 * tau - h) / (2 * tau + dt);
     const double b1 = 3 * h / (2 * tau + dt);
     const double c1 = 3 * tau * h / (2 * tau + dt);
@@ -443,7 +443,7 @@ static void step_once(ostate *s)
                 }
     }
 
-    /* Step 4: fbar(x_b, t+h) = fbar+(x_b) - h xi . sigma_b (eq. gradient). Normal
+    /* Step 4: fbar(x_b, t+h) = fbar+(x_b) - h xi . sigma_b (eq. (23)). Normal
      * component of sigma_b: difference of the two cells; tangential components:
      * difference of the two cross points on the interface (reading R5). */
     for (int d = 0; d < D; d++) {
@@ -484,8 +484,8 @@ static void step_once(ostate *s)
                 }
     }
 
-    /* Step 5: boundary processing of fbar at the wall interfaces: NEQ, eq. NEQ
-     * (reading R4), or bounce-back, eq. BB (reading R14). */
+    /* Step 5: boundary processing of fbar at the wall interfaces: NEQ, eq. (32)
+     * (reading R4), or bounce-back, eq. (31) (reading R14). */
     for (int d = 0; d < D; d++) {
         if (s->cfg.bc_type[2 * d] == BC_PERIODIC) continue;
         for (int side = 0; side < 2; side++) {
@@ -533,7 +533,7 @@ static void step_once(ostate *s)
     }
 
     /* Step 6: rho, u at X_b (weight h/2 on G). Step 7: the original distribution at the
-     * interface, eq. original_f solved for f:
+     * interface, eq. (20) solved for f:
      *   f = 2tau/(2tau+h) fbar + h/(2tau+h) f_eq + tau h/(2tau+h) S. */
     const double a7 = 2 * tau / (2 * tau + h);
     const double b7 = h / (2 * tau + h);
@@ -563,7 +563,7 @@ static void step_once(ostate *s)
     }
 
     /* Step 8: micro-flux m = sum over the cell's interfaces of (xi.n_j) f(x_j) s_j
-     * (eq. microflux); on the uniform mesh s_j = dx^(D-1), on a non-uniform one the cell's
+     * (eq. (13)); on the uniform mesh s_j = dx^(D-1), on a non-uniform one the cell's
      * extent across the other axes (R18). */
     const double area = D == 3 ? dx * dx : dx;
     const double vol = D == 3 ? dx * dx * dx : dx * dx;
@@ -591,8 +591,8 @@ static void step_once(ostate *s)
                 }
             }
 
-    /* Step 9: f~+ = 4/3 fbar+ - 1/3 f~ (eq. f_tilde_+), then
-     * f~(t+dt) = f~+ - dt/|V| m (eq. evolution_equation). */
+    /* Step 9: f~+ = 4/3 fbar+ - 1/3 f~ (eq. (25)), then
+     * f~(t+dt) = f~+ - dt/|V| m (eq. (16)). */
     for (x[2] = 0; x[2] < s->n[2]; x[2]++)
         for (x[1] = 0; x[1] < s->n[1]; x[1]++)
             for (x[0] = 0; x[0] < s->n[0]; x[0]++) {
@@ -746,7 +746,7 @@ int oracle_set_field(void *p, const double *field)
     return 0;
 }
 
-/* Initial state, reading R7: f~ = f_eq(rho0 + p/RT, u) (eq. icfeq). p: [ncell] or NULL
+/* Initial state, reading R7: f~ = f_eq(rho0 + p/RT, u) (eq. (6)). p: [ncell] or NULL
  * (zero); u: [dim][ncell] or NULL (rest). Resets the clock to t = 0. */
 int oracle_init(void *p, const double *pres, const double *vel)
 {
@@ -772,7 +772,7 @@ int oracle_step(void *p, long nsteps)
 double oracle_time(void *p) { return ((ostate *)p)->t; }
 long oracle_step_count(void *p) { return ((ostate *)p)->step; }
 
-/* Moments of the current state (eq. macro_values with G(t)): out[(dim+1)][ncell] =
+/* Moments of the current state (eq. (27) with G(t)): out[(dim+1)][ncell] =
  * p = (rho - rho0) RT (reading R9), then u_x, u_y[, u_z]. out_im: imaginary parts (the
  * complex-step derivative direction), may be NULL. */
 int oracle_moments(void *p, double *out, double *out_im)
@@ -848,7 +848,7 @@ int oracle_set_wall_u_im(void *p, const double *im)
 #endif
 
 /* Conservation sums over X_c of the current state: out[0] = sum rho, out[1+a] = sum
- * rho0 u_a with u from eq. macro_values (per cell, no volume factor). */
+ * rho0 u_a with u from eq. (27) (per cell, no volume factor). */
 int oracle_sums(void *p, double *out)
 {
     ostate *s = (ostate *)p;

@@ -6,15 +6,15 @@
 // velocities u_w. For lambda' = dL/dg~^{n+1} one reverse step forms
 //     lambda = (dPhi/dg~^n)^T lambda',  dL/dG += (dPhi/dG)^T lambda',  dL/du_w += (dPhi/du_w)^T lambda'
 // by running the sub-steps backwards in three gather-form kernels:
-//   adj_cells_fwd (per cell)       recomputes the cell moments (eq. macro_values) and
-//                                  fbar+ (step 1, eq. f_bar_+);
+//   adj_cells_fwd (per cell)       recomputes the cell moments (eq. (27)) and
+//                                  fbar+ (step 1, eq. (24));
 //   adj_faces     (per interface)  recomputes steps 3-7 and pulls lambda' back through the
 //                                  flux (steps 8-9), the interface relaxation (step 7,
-//                                  eq. original_f), the interface moments (step 6) and the
-//                                  wall condition (step 5: eq. NEQ, or eq. BB), down to the
+//                                  eq. (20)), the interface moments (step 6) and the
+//                                  wall condition (step 5: eq. (32), or eq. (31)), down to the
 //                                  adjoint of the step-4 values and of the interface
 //                                  acceleration;
-//   adj_cells     (per cell)       transposes the reconstruction (steps 3-4, eq. gradient)
+//   adj_cells     (per cell)       transposes the reconstruction (steps 3-4, eq. (23))
 //                                  and the ghost extrapolation (step 2), then pulls the
 //                                  adjoint of fbar+ back through step 1 and the cell moments
 //                                  to g~^n and G.
@@ -23,7 +23,7 @@
 // one velocity per lane. Every output element is a gather written by one thread, or by one lane
 // after a fixed-order butterfly over the velocities (no atomics), so the sweep is bitwise
 // reproducible. Arithmetic in the storage type of the handle (float or double). The adjoint
-// covers the incompressible model (eq. icfeq).
+// covers the incompressible model (eq. (6)).
 //
 // Interfaces: normal to x, (i, j) with i in [0, nx], j in [0, ny), between cells (i-1, j)
 // and (i, j), index i + (nx+1) j; normal to y, (i, j) with i in [0, nx), j in [0, ny],
@@ -131,7 +131,7 @@ __device__ __forceinline__ T phi_ext(const AdjParams<T> &a, int k, int x, int y)
     return wy[0] * (wx[0] * p00 + wx[1] * p10) + wy[1] * (wx[0] * p01 + wx[1] * p11);
 }
 
-// ---- steps 3-4: step-4 value of velocity k at interface (d, i, j) (eq. gradient with the
+// ---- steps 3-4: step-4 value of velocity k at interface (d, i, j) (eq. (23) with the
 // step-3 cross points): 1/2 (L + R) - kappa e_d (R - L) - kappa/4 e_t [(L+R)_{t+1} - (L+R)_{t-1}] ----
 template <class T>
 __device__ __forceinline__ T recon(const AdjParams<T> &a, int d, int i, int j, int k) {
@@ -177,7 +177,7 @@ __device__ __forceinline__ T recon_T(const AdjParams<T> &a, int k, int x, int y)
     return v;
 }
 
-// ---- equilibrium (eq. icfeq, deviation form, m = rho0 u / c) and its derivative ----
+// ---- equilibrium (eq. (6), deviation form, m = rho0 u / c) and its derivative ----
 template <class T>
 __device__ __forceinline__ T geq(const AdjParams<T> &a, int k, T dr, const T m[2]) {
     const T em = (T)L9::e(k, 0) * m[0] + (T)L9::e(k, 1) * m[1];
@@ -282,7 +282,7 @@ struct FaceLane {
     T F, Fc;               // step-4 value of the lane's velocity (incoming ones replaced at a
                            // wall, step 5) and its value at x_c (wall only)
     T dr, m[2], Gh[2];     // step-6 moments and the interface acceleration
-    int wall, side, bb;    // bb: bounce-back wall (eq. BB)
+    int wall, side, bb;    // bb: bounce-back wall (eq. (31))
     T drc, mc[2];          // moments at x_c (wall only)
     T ma[2];               // m_a of step 5 (wall only)
 };
@@ -299,7 +299,7 @@ __device__ __forceinline__ void face_forward_lane(const AdjParams<T> &a, int d, 
     s.Fc = T(0);
     s.bb = s.wall && a.bc[2 * d + s.side] == DUGKS_BC_BOUNCE_BACK;
     if (s.bb) {
-        // step 5, eq. BB: the incoming velocity takes its opposite's value (lane 8 - k of the
+        // step 5, eq. (31): the incoming velocity takes its opposite's value (lane 8 - k of the
         // half) plus 6 W_k e_k.m_w
         const T Fo = __shfl_sync(0xffffu << (threadIdx.x & 16), s.F, Q - 1 - k, 16);
         const int sgn = s.side == 0 ? -1 : 1;
@@ -354,7 +354,7 @@ __device__ __forceinline__ void face_adjoint_lane(const AdjParams<T> &a, int d, 
         if (hashi) v += a.lam1[k * nc + chi];
     }
     const T fbar = a.two_kappa * (T)ed * v;
-    // step 7 (eq. original_f) at the step-6 moments, then step 6
+    // step 7 (eq. (20)) at the step-6 moments, then step 6
     T bdr, bm[2], bG[2];
     relax_T_one(a, k, fbar, s.dr, s.m, s.Gh, a.b7, a.c7, bdr, bm, bG);
     bdr = wsum(bdr);
@@ -368,7 +368,7 @@ __device__ __forceinline__ void face_adjoint_lane(const AdjParams<T> &a, int d, 
     Wb[0] = Wb[1] = T(0);
     if (!wall) return;
     if (s.bb) {
-        // step 5, eq. BB: F_k = F_-k + 6 W_k e_k.m_w for incoming k: the weight of an
+        // step 5, eq. (31): F_k = F_-k + 6 W_k e_k.m_w for incoming k: the weight of an
         // incoming velocity passes to its opposite (lane 8 - k) and to u_w
         const int sgn = s.side == 0 ? -1 : 1;
         const bool incoming = act && sgn * ed < 0;
@@ -380,7 +380,7 @@ __device__ __forceinline__ void face_adjoint_lane(const AdjParams<T> &a, int d, 
         Wb[1] = wsum(c6 * e1);
         return;
     }
-    // step 5 (eq. NEQ): F_k = geq_k(drho_a, m_a) + Fc_k - geq_k(drho_c, m_c), incoming k.
+    // step 5 (eq. (32)): F_k = geq_k(drho_a, m_a) + Fc_k - geq_k(drho_c, m_c), incoming k.
     // Velocity condition: drho_a = drho_c (the W_k terms cancel), m_a from u_w.
     // Pressure condition: m_a = m_c (the m terms cancel), drho_a fixed.
     const int wid = 2 * d + s.side;
@@ -575,7 +575,7 @@ __device__ __forceinline__ void cell_fast(const AdjParams<T> &a, int x, int y, i
 }
 
 // ---- kernels ----
-// fbar+ (step 1, eq. f_bar_+) and the moments (eq. macro_values) of cell c of `state` into
+// fbar+ (step 1, eq. (24)) and the moments (eq. (27)) of cell c of `state` into
 // a.phi and `mom`, with ctc = cos(omega t) / c at that state's time. Not inlined: the
 // recompute kernel and the cells kernel that carries the next step's recompute run the same
 // code, so the sweep's bits do not depend on which of them computed a step.
@@ -721,7 +721,7 @@ __device__ __noinline__ void cells_frame_item(const AdjParams<T> &a, int64_t t) 
     T wx[3], wy[3];
     const int nux = ext_users<T>(x, a.n[0], a.per[0], ux, wx);
     const int nuy = ext_users<T>(y, a.n[1], a.per[1], uy, wy);
-    // adjoint of fbar+ of this cell: eq. f_tilde_+ (4/3 fbar+) and every interface value
+    // adjoint of fbar+ of this cell: eq. (25) (4/3 fbar+) and every interface value
     // reconstructed from it, directly or through a ghost / periodic image
     const T l1 = act ? a.lam1[k * nc + c] : T(0);
     T pb = T(0);
@@ -731,7 +731,7 @@ __device__ __noinline__ void cells_frame_item(const AdjParams<T> &a, int64_t t) 
             for (int q = 0; q < nuy; q++) v += wx[p] * wy[q] * recon_T(a, k, ux[p], uy[q]);
         pb = v;
     }
-    // step 1 (eq. f_bar_+) and the cell moments (eq. macro_values)
+    // step 1 (eq. (24)) and the cell moments (eq. (27))
     const T dr = a.mom[c];
     const T m[2] = {a.mom[nc + c], a.mom[2 * nc + c]};
     T Gh[2];
@@ -779,7 +779,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 7 : 5) adj_cells_all(con
 }
 
 // Loss seed from dL/d(moments) [3][ncell] (p, u_x, u_y as dugks_moments returns them):
-// p = RT sum g~, u = c/rho0 sum e g~ + G cos(omega t) dt/2 (eq. macro_values).
+// p = RT sum g~, u = c/rho0 sum e g~ + G cos(omega t) dt/2 (eq. (27)).
 template <class T>
 __global__ void adj_seed(const AdjParams<T> a, const float *dLdm, T rt, T c_over_rho0, double gdt) {
     const int64_t nc = ncell(a);

@@ -59,11 +59,11 @@ StepParams dugks::handle_params(const dugks_t h) {
     const double tau = h->tau, dt = h->dt, hh = 0.5 * h->dt;
     p.rho0 = h->rho0;
     p.inv_c = (1.0 / h->c);
-    // step 1, eq. f_bar_+
+    // step 1, eq. (24)
     p.a1 = ((2 * tau - hh) / (2 * tau + dt));
     p.b1 = (3 * hh / (2 * tau + dt));
     p.c1 = (3 * tau * hh / (2 * tau + dt));
-    // step 7, eq. original_f solved for f
+    // step 7, eq. (20) solved for f
     p.a7 = (2 * tau / (2 * tau + hh));
     p.b7 = (hh / (2 * tau + hh));
     p.c7 = (tau * hh / (2 * tau + hh));

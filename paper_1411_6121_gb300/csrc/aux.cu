@@ -6,7 +6,7 @@
 namespace dugks {
 
 // Initial state (Sec. 3: the equilibrium is initialised from the given fields):
-// g~ = f_eq(rho0 + p/RT, u) - W rho0 of eq. icfeq (eq. feq for the original model: rho in
+// g~ = f_eq(rho0 + p/RT, u) - W rho0 of eq. (6) (eq. (5) for the original model: rho in
 // place of rho0 in the velocity part), evaluated in double and rounded once.
 template <int Q, class S>
 __global__ void init_kernel(const StepParams p, const double *pres, const double *vel, double rt, double c) {
@@ -51,7 +51,7 @@ __device__ __forceinline__ void cell_moments_d(const StepParams &p, const S *src
         for (int a = 0; a < D; a++) j[a] += Lat<Q>::e(k, a) * g;
     }
     drho = r;
-    // u = c j / rho0 + G dt/2 (eq. macro_values); c j / rho + G dt/2 in the original model
+    // u = c j / rho0 + G dt/2 (eq. (27)); c j / rho + G dt/2 in the original model
     const double rd = p.model == 1 ? (double)p.rho0 + r : (double)p.rho0;
     for (int a = 0; a < 3; a++) {
         double G = a < D ? (double)p.g[a] : 0.0;
@@ -146,7 +146,7 @@ __device__ __forceinline__ void cell_moments_out_f(const StepParams &p, const S 
     }
 }
 
-// Moments (eq. macro_values): out[0] = p = (rho - rho0) RT, out[1+a] = u_a; [dim+1][ncell].
+// Moments (eq. (27)): out[0] = p = (rho - rho0) RT, out[1+a] = u_a; [dim+1][ncell].
 template <int Q, class S>
 __global__ void moments_kernel(const StepParams p, double ct, double rt, double c, float *out) {
     constexpr int D = Lat<Q>::D;

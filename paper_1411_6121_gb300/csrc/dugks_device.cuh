@@ -1,8 +1,8 @@
 // dugks_device.cuh -- device-side building blocks of the fused DUGKS time step (sm_103a).
 //
 // Notation follows Wu, Shi, Chai and Wang (arXiv 1411.6121): f~ cell averages, fbar+ the
-// auxiliary distribution of eq. f_bar_+, fbar the interface distribution at t + h
-// (eq. interfaceEvof), f the original distribution at the interface (eq. original_f).
+// auxiliary distribution of eq. (24), fbar the interface distribution at t + h
+// (eq. (21)), f the original distribution at the interface (eq. (20)).
 // Storage and arithmetic use the deviation from the rest equilibrium, g = f - W rho0: every
 // linear map of the scheme has coefficients summing to one (steps 1, 3, 7, 9) or zero
 // (gradients, the closed-surface flux), so the deviation form is the same algebra with
@@ -264,19 +264,19 @@ struct StepParams {
     int64_t dstride;    // plane * nz: distance between directions
     double rho0;
     double inv_c;       // 1 / c
-    double a1, b1, c1;  // step 1 (eq. f_bar_+): fbar+ = a1 g~ + b1 geq + c1 S
-    double a7, b7, c7;  // step 7 (eq. original_f): f = a7 fbar + b7 geq + c7 S
-    double kappa;       // h c / dx: reconstruction (eq. gradient)
-    double two_kappa;   // dt c / dx: flux (eq. evolution_equation)
+    double a1, b1, c1;  // step 1 (eq. (24)): fbar+ = a1 g~ + b1 geq + c1 S
+    double a7, b7, c7;  // step 7 (eq. (20)): f = a7 fbar + b7 geq + c7 S
+    double kappa;       // h c / dx: reconstruction (eq. (23))
+    double two_kappa;   // dt c / dx: flux (eq. (16))
     double c_over_rho0; // c / rho0: velocity moment
-    double wcell;       // dt / 2: force weight in the cell moments (eq. macro_values)
+    double wcell;       // dt / 2: force weight in the cell moments (eq. (27))
     double wface;       // h / 2: force weight in the interface moments (Appendix step 6)
     double g[3];        // uniform acceleration
     const float *field;        // [dim][ncell] acceleration field or null
     double omega, dt;          // G(t) = (g + field) cos(omega t)
     const long long *step_ctr; // device step counter: t_n = (*step_ctr + step_off) dt
     int step_off;
-    int model;                 // 0: incompressible model (eq. icfeq); 1: original DUGKS (eq. feq)
+    int model;                 // 0: incompressible model (eq. (6)); 1: original DUGKS (eq. (5))
     // non-uniform mesh (Sec. 3.4): per axis a, metric[a] = [wf (n+1) | idc (n+1) | idx (n)]:
     // the weight of the high cell at interface i, 1 / (centre distance across i), 1 / (width
     // of cell i); eg[a][side]: the ghost extrapolation coefficient, ghost = f0 + eg (f1 - f0)
@@ -355,7 +355,7 @@ __device__ __forceinline__ T wmul(int k, T x) {
 }
 
 // ---------------------------------------------------------------------------------
-// Moments of a deviation distribution g = f - W rho0 (eq. macro_values / Appendix step 6),
+// Moments of a deviation distribution g = f - W rho0 (eq. (27) / Appendix step 6),
 // in units of the particle speed c: drho = sum_k g_k, m = sum_k e_k g_k + rho0 Gh w, where
 // Gh = G / c and w the force weight (dt/2 at cells, h/2 at interfaces). The velocity is
 // u = c m / rho0. Working with m keeps every constant that feeds back into the momentum
@@ -414,7 +414,7 @@ __device__ __forceinline__ void moments(const T g[Q], const T rGh[3], T w, T &dr
     }
 }
 
-// Equilibrium deviation of eq. icfeq in the variables above:
+// Equilibrium deviation of eq. (6) in the variables above:
 //   geq_k = W_k [ drho + 3 e_k.m + (4.5 (e_k.m)^2 - 1.5 m.m) / rho0 ].
 template <int Q, class T>
 __device__ __forceinline__ T geq_k(int k, T drho, const T m[3], T mm, T inv_rho0) {
@@ -433,9 +433,9 @@ __device__ __forceinline__ T geq_k(int k, T drho, const T m[3], T mm, T inv_rho0
 // paper's equations are applied as y = g + b (geq - g) + c S, which keeps exact levels
 // exact in finite precision):
 //   out_k = g_k + b (geq_k - g_k) + c S_k,  S_k = 3 (Gh.e_k - Gh.m / rho0) (W_k rho0 + geq_k)
-// (eq. S with G.(xi - u)/RT = 3 (Gh.e - Gh.u/c) for xi = c e, c^2 = 3 RT).
-// Step 1 (eq. f_bar_+) uses b = 3h/(2tau+dt), c = 3 tau h/(2tau+dt); step 7
-// (eq. original_f) uses b = h/(2tau+h), c = tau h/(2tau+h). FORCE = false drops S
+// (eq. (9) with G.(xi - u)/RT = 3 (Gh.e - Gh.u/c) for xi = c e, c^2 = 3 RT).
+// Step 1 (eq. (24)) uses b = 3h/(2tau+dt), c = 3 tau h/(2tau+dt); step 7
+// (eq. (20)) uses b = h/(2tau+h), c = tau h/(2tau+h). FORCE = false drops S
 // (G = 0 everywhere). Opposite velocities share e.m and the quadratic part of geq.
 // In FP32 the equilibrium is rounded once at the scale of its odd term 3 W e.m: with
 // 3W = W3h + W3l and W = Wh + Wl split into heads and tails, geq = W3h e.m + (W3l e.m + W q)

@@ -3,16 +3,16 @@
 //
 // A CTA owns a TX x TY tile of cell columns and marches through its z range (2.5D
 // blocking). For every z plane it
-//   1. loads g~ for the tile plus a one-cell halo and forms fbar+ (step 1, eq. f_bar_+)
+//   1. loads g~ for the tile plus a one-cell halo and forms fbar+ (step 1, eq. (24))
 //      into a three-plane shared-memory ring, filling wall ghost cells by linear
 //      extrapolation (step 2) in the order x, y, z;
 //   2. reconstructs fbar at every x, y and z interface of the tile's cells (steps 3-4,
-//      eq. gradient: two-cell mean, normal difference, cross-point tangential
-//      differences), applies the NEQ condition at wall interfaces (step 5, eq. NEQ),
+//      eq. (23): two-cell mean, normal difference, cross-point tangential
+//      differences), applies the NEQ condition at wall interfaces (step 5, eq. (32)),
 //      takes the interface moments (step 6) and forms the original f (step 7,
-//      eq. original_f) for the directions that cross the interface;
+//      eq. (20)) for the directions that cross the interface;
 //   3. updates the cell: f~(t+dt) = 4/3 fbar+ - 1/3 f~ - dt/|V| flux (steps 8-9,
-//      eqs. f_tilde_+ and evolution_equation).
+//      eqs. (25) and (16)).
 // Each interface value is computed once and used by both adjacent cells, so the discrete
 // flux telescopes exactly (mass conservation to rounding).
 #pragma once
@@ -34,7 +34,7 @@ struct StepShape {
     static constexpr size_t smem_bytes = smem_floats * sizeof(T);
 };
 
-// Step 4 (eq. gradient): fbar(x_b, t+h) = fbar+(x_b) - h xi . sigma_b for every velocity,
+// Step 4 (eq. (23)): fbar(x_b, t+h) = fbar+(x_b) - h xi . sigma_b for every velocity,
 // at the interface normal to axis d between cells L and R. fbar+(x_b) is the mean of L and
 // R (step 3); the normal gradient is (R - L)/dx; the gradient along a tangential axis t is
 // the difference of the two cross points on the interface, each the mean of the 4 cells
@@ -106,9 +106,9 @@ __device__ __forceinline__ void reconstruct_nu(const T *L, const T *R, const T *
     }
 }
 
-// The model switch of the reference path. For the incompressible model (eq. icfeq,
-// eq. macro_values) the momentum variable is m = rho0 u / c and f_eq, S divide by rho0;
-// returns 1/rho0. For the original DUGKS (p.model == 1: eq. feq, rho u = sum xi f~ + rho G w)
+// The model switch of the reference path. For the incompressible model (eq. (6),
+// eq. (27)) the momentum variable is m = rho0 u / c and f_eq, S divide by rho0;
+// returns 1/rho0. For the original DUGKS (p.model == 1: eq. (5), rho u = sum xi f~ + rho G w)
 // m = rho u / c: the force shift that moments() applied with rho0 is completed to
 // rho = rho0 + drho, and 1/rho is returned for f_eq and S. ORIG = false compiles the switch
 // out (kernels that only run the incompressible model).
@@ -124,14 +124,14 @@ __device__ __forceinline__ T original_model(const StepParams &p, const Coef<T> &
 // Steps 5-7 at one interface normal to axis d. F: step-4 values (modified in place by the
 // wall condition, NEQ or bounce-back, when wall != 0). Fc: step-4 values at x_c, the boundary
 // cell's opposite interface (read only by NEQ). side: 0 for the low wall (outward normal -e_d),
-// 1 for the high wall. Writes the original f of eq. original_f for the velocities with
+// 1 for the high wall. Writes the original f of eq. (20) for the velocities with
 // e_d != 0 into out[flux_index(d, k)] (stride 1). ORIG as in original_model.
 template <int Q, int d, class T, bool ORIG = true>
 __device__ __forceinline__ void interface_f(const StepParams &p, const Coef<T> &cf, T F[Q], const T Gh[3], int wall,
                                             int side, const T *Fc, const T Ghc[3], T *out) {
     constexpr int D = Lat<Q>::D;
     if (wall && p.bc[2 * d + side] == 3) {
-        // Step 5, eq. BB: F_k = F_-k + 2 rho0 W_k xi_k.u_w / RT for xi . n < 0, i.e.
+        // Step 5, eq. (31): F_k = F_-k + 2 rho0 W_k xi_k.u_w / RT for xi . n < 0, i.e.
         // g_k = g_-k + 6 W_k e_k.m_w with m_w = rho0 u_w / c (deviations: W_k = W_-k)
         const int wid = 2 * d + side;
         T mw[3];
@@ -153,7 +153,7 @@ __device__ __forceinline__ void interface_f(const StepParams &p, const Coef<T> &
             }
         });
     } else if (wall) {
-        // Step 5, eq. NEQ: f(x_w) = f_eq(rho_a, u_a) + [f(x_c) - f_eq(rho_c, u_c)] for
+        // Step 5, eq. (32): f(x_w) = f_eq(rho_a, u_a) + [f(x_c) - f_eq(rho_c, u_c)] for
         // xi . n < 0, applied to fbar (Appendix step 5) with the moments of step 6 at x_c.
         const int wid = 2 * d + side;
         T drc, mc[3];
@@ -571,7 +571,7 @@ __device__ __forceinline__ void step_tile(const StepParams &p, int x0, int y0, i
                     acc = fmaT((T)Lat<Q>::e(k, 2), zf_hi[i] - zf_lo[i], acc);
                 }
                 const T gold = (T)Store<S>::ld(src + k * p.dstride + off);
-                // eq. f_tilde_+ in increment form: 4/3 fbar+ - 1/3 f~ = fbar+ + (fbar+ - f~)/3
+                // eq. (25) in increment form: 4/3 fbar+ - 1/3 f~ = fbar+ + (fbar+ - f~)/3
                 const T v = fmaT(T(1) / T(3), ph[k] - gold, ph[k]) - cf.two_kappa * acc;
                 store_state<S>(dst + k * p.dstride + off, v, sizeof(S) == 2 ? rnd.bits<k>() : 0u);
             });

@@ -401,8 +401,8 @@ __device__ __forceinline__ void step2d_tile(const StepParams &p, unsigned char *
                 constexpr int i = flux_index<9>(1, k);
                 acc = fmaf((float)Lat<9>::e(k, 1), fyp[i] - ym[i], acc);
             }
-            // eq. f_tilde_+ in increment form (4/3 fbar+ - 1/3 f~), then the flux of
-            // eq. evolution_equation
+            // eq. (25) in increment form (4/3 fbar+ - 1/3 f~), then the flux of
+            // eq. (16)
             const float u0 = fmaf(1.0f / 3.0f, f[k] - g[k], f[k]);
             store_state<S>(dst + k * p.dstride + off, fmaf(-cf.two_kappa, acc, u0), sizeof(S) == 2 ? rnd.bits<k>() : 0u);
         });

@@ -9,7 +9,7 @@
 //    its z range keeping fbar+ (step 1) and its moments for three planes in a
 //    shared-memory ring.
 //  * Step 3-4 reconstruction is split per cell. For the interface normal to d between
-//    cells L and R (eq. gradient with the cross-point tangential gradients):
+//    cells L and R (eq. (23) with the cross-point tangential gradients):
 //        F_k = alpha_k(L) + beta_k(R),
 //        alpha_k = (1/2 + kappa e_dk) fbar+_k - kappa/4 sum_t e_tk C^t_k,
 //        beta_k  = (1/2 - kappa e_dk) fbar+_k - kappa/4 sum_t e_tk C^t_k,
@@ -213,8 +213,8 @@ __device__ __forceinline__ void face_relax(const Coef<float> &cf, const float *F
 // over all velocities, without the force shift), and the same at x_c, the boundary cell's
 // opposite interface (Fc, drc, jc, with its acceleration Ghc). The velocities that enter from
 // the wall (e_d > 0 at the low wall, SIDE 0; e_d < 0 at the high wall, SIDE 1) become
-// f_eq(rho_a, u_a) + [Fc - f_eq(rho_c, u_c)] (eq. NEQ), or, at a bounce-back wall, the
-// opposite velocity's value plus the wall term of eq. BB. The interface moments take the
+// f_eq(rho_a, u_a) + [Fc - f_eq(rho_c, u_c)] (eq. (32)), or, at a bounce-back wall, the
+// opposite velocity's value plus the wall term of eq. (31). The interface moments take the
 // moments of that change, so step 6 sees the moments of the modified values.
 template <int Q, int d, bool FORCE, int SIDE>
 __device__ __forceinline__ void neq_wall(const StepParams &p, const Coef<float> &cf, float *F, float &drb,
@@ -222,7 +222,7 @@ __device__ __forceinline__ void neq_wall(const StepParams &p, const Coef<float> 
                                          const float Ghc[3]) {
     constexpr int wid = 2 * d + SIDE;
     if (p.bc[wid] == 3) {
-        // eq. BB instead: F_k = F_-k + 6 W_k e_k.m_w (m_w = rho0 u_w / c), from this
+        // eq. (31) instead: F_k = F_-k + 6 W_k e_k.m_w (m_w = rho0 u_w / c), from this
         // interface's own values
         float mw[3];
 #pragma unroll
@@ -334,7 +334,7 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, const CUtens
     const Coef<float> cf(p);
 
     const int lane = threadIdx.x, row = threadIdx.y;
-    // own u0 = fbar+ + (fbar+ - f~)/3 (the cell's part of eq. f_tilde_+) of planes with
+    // own u0 = fbar+ + (fbar+ - f~)/3 (the cell's part of eq. (25)) of planes with
     // even / odd index
     float *usb = xf + K::NT * K::FS + (row * 32 + lane) * (2 * K::US);
     auto US = [&](int pz) __attribute__((always_inline)) -> float * { return usb + (pz & 1) * K::US; };
@@ -432,7 +432,7 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, const CUtens
     bool wait_ok = true;  // false once a copy did not land (the CTA then leaves, see below)
 
     // ---- step 1 for the own column at plane pz into the ring; u0 = fbar+ + (fbar+ - f~)/3
-    //      (the cell's part of eq. f_tilde_+, applied in increment form) is returned ----
+    //      (the cell's part of eq. (25), applied in increment form) is returned ----
     auto make_phi = [&](int pz, float *u0) __attribute__((always_inline)) {
         float *o = R(slot_of(pz), row, lane);
         const S *sb = nullptr;
@@ -798,7 +798,7 @@ __device__ __forceinline__ void step3d_segment(const StepParams &p, const CUtens
                     constexpr int i = flux_index<Q>(2, k);
                     acc = fmaf((float)Lat<Q>::e(k, 2), fzp[i] - fzm[i], acc);
                 }
-                // eq. evolution_equation: f~(t+dt) = f~+ - dt/|V| flux
+                // eq. (16): f~(t+dt) = f~+ - dt/|V| flux
                 store_state<S>(dst + k * p.dstride + off, fmaf(-cf.two_kappa, acc, u0[k]),
                                sizeof(S) == 2 ? rnd.bits<k>() : 0u);
             });

@@ -138,7 +138,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Step 1 (eq. f_bar_+ with eq. icfeq) for one D3Q19 cell on pairs: G[j] = (g~_j, g~_{18-j}),
+// Step 1 (eq. (24) with eq. (6)) for one D3Q19 cell on pairs: G[j] = (g~_j, g~_{18-j}),
 // g9 the rest velocity, Gh the acceleration / c at t_n (FORCE). Writes fbar+ (F, f9),
 // u0 = fbar+ + (fbar+ - g~)/3 (U, u9) and the ten moments of fbar+ in the ring's order
 // (mo: M0, M_x, M_y, M_z, M_xx, M_yy, M_zz, M_xy, M_xz, M_yz). The momentum sums are exact
@@ -988,7 +988,7 @@ __global__ void __launch_bounds__(512, 1)
                     const float2 ev = f2((float)pr::e(j, 2), (float)-pr::e(j, 2));
                     acc = (pr::e(j, 0) != 0 || pr::e(j, 1) != 0) ? __ffma2_rn(ev, dv, acc) : __fmul2_rn(ev, dv);
                 }
-                // eq. evolution_equation: f~(t+dt) = f~+ - dt/|V| flux
+                // eq. (16): f~(t+dt) = f~+ - dt/|V| flux
                 const float2 v = __ffma2_rn(TK, acc, ld2(u0 + 2 * j));
                 store_state_pair<S>(dst + j * p.dstride + off, v.x, dst + (18 - j) * p.dstride + off, v.y,
                                     sizeof(S) == 2 ? rnd.word<j>() : 0u);

@@ -40,7 +40,7 @@ def pressure(p, amp=0.0):
 
 
 def bounce_back(u=(0.0, 0.0, 0.0)):
-    """Bounce-back wall (eq. BB) moving with velocity u."""
+    """Bounce-back wall (eq. (31)) moving with velocity u."""
     return (BC_BOUNCE_BACK, tuple(float(a) for a in u) + (0.0,) * (3 - len(u)), 0.0)
 
 

@@ -13,7 +13,7 @@ def cell_centres(n, length=1.0):
 
 
 def periodic_flow(x, y, u0, rho0, nu):
-    """Force-driven periodic flow, Sec. 3.1 (eq. PF_AS and the body force after it):
+    """Force-driven periodic flow, Sec. 3.1 (eq. (35) and the body force after it):
     u = u0 sin2pix sin2piy, v = u0 cos2pix cos2piy,
     p = rho0 u0^2 (cos4pix - cos4piy)/4, F = 8 pi^2 nu (u, v)."""
     u = u0 * np.sin(2 * np.pi * x) * np.sin(2 * np.pi * y)
@@ -25,13 +25,13 @@ def periodic_flow(x, y, u0, rho0, nu):
 
 
 def poiseuille(y, G, nu, H=1.0):
-    """Plane Poiseuille flow, Sec. 3.2 (eq. Poiseuille_AS) for walls at y = 0 and y = H:
+    """Plane Poiseuille flow, Sec. 3.2 (eq. (38)) for walls at y = 0 and y = H:
     u = G/(2 nu) y (H - y)."""
     return G / (2.0 * nu) * y * (H - y)
 
 
 def womersley_complex(y, t, G, omega, nu, Ly):
-    """Womersley velocity, Sec. 3.3 (eq. Wom_AS_Complex), for the pressure gradient
+    """Womersley velocity, Sec. 3.3 (eq. (39)), for the pressure gradient
     dP/dx = G cos(omega t): u = Re[ i G/omega (1 - cos(lam (2y/Ly - 1)) / cos(lam)) e^{i omega t} ].
     The printed definition of lambda is garbled; lam^2 = -i alpha^2 with alpha =
     (Ly/2) sqrt(omega/nu) is the reading that makes this solve u_t = -G cos(omega t) + nu u_yy
@@ -43,7 +43,7 @@ def womersley_complex(y, t, G, omega, nu, Ly):
 
 
 def womersley_real(y, t, G, omega, nu, Ly):
-    """Womersley velocity, real form of Sec. 3.3 (eq. Wom_AS_Velocity with K_r, K_i, K_a):
+    """Womersley velocity, real form of Sec. 3.3 (eq. (42) with K_r, K_i, K_a):
     u = G/omega [ -sin wt + (K_r sin wt + K_i cos wt)/K_a ], k = alpha/sqrt2,
     theta = k (2y/Ly - 1)."""
     alpha = 0.5 * Ly * np.sqrt(omega / nu)

@@ -47,7 +47,7 @@ CASES = {
     "periodic_wide": dict(shape=(10, 8), q=9, nu=0.04, dt=0.5, g=(1e-5, 2e-5, 0.0), bcs=W.all_periodic()),
     "cavity_wide": dict(shape=(9, 10), q=9, nu=0.04, dt=0.5,
                         bcs=[W.wall(), W.pressure(-1e-3), W.wall(), W.wall((0.05, 0.0, 0.0))]),
-    # bounce-back walls (eq. BB): a moving one, and beside NEQ walls
+    # bounce-back walls (eq. (31)): a moving one, and beside NEQ walls
     "bb_channel": dict(shape=(6, 5), q=9, nu=0.05, dt=0.5, g=(2e-5, 0.0, 0.0),
                        bcs=[W.periodic(), W.periodic(), W.bounce_back(), W.bounce_back((0.03, 0.0, 0.0))]),
     "bb_cavity_wide": dict(shape=(9, 10), q=9, nu=0.04, dt=0.5, g=(1e-5, 0.0, 0.0),
@@ -232,7 +232,7 @@ def test_adjoint_error_codes():
 
 
 def _host_u(state, cfg, field, steps):
-    """u(T) in FP64 from an FP64 state (eq. macro_values), for finite differences that
+    """u(T) in FP64 from an FP64 state (eq. (27)), for finite differences that
     must not be limited by the float32 moments output."""
     o = Oracle(**cfg)
     e, _ = o.lattice()

@@ -4,9 +4,9 @@ and test_gpu_adjoint.py).
 
 C0  D2Q9 force-driven channel 8 x 32 (periodic x, NEQ walls, nu = 0.01, G = 1e-5, CFL 0.5), from
     rest, to the steady criterion of Sec. 3.1 with K = 1000 and tolerance 1e-10, against the
-    parabola of Sec. 3.2 (eq. Poiseuille_AS) and the FP64 oracle's steady state (golden file).
+    parabola of Sec. 3.2 (eq. (38)) and the FP64 oracle's steady state (golden file).
 C1  D2Q9 Womersley channel 128 x 64 driven by G0 cos(omega t), Womersley numbers 3 to 10, ten
-    periods, eight phases of the last (Sec. 3.3, the force-driven form of eq. Wom_AS_Velocity);
+    periods, eight phases of the last (Sec. 3.3, the force-driven form of eq. (42));
     and the mesh-refinement sweep.
 C2  D2Q9 lid-driven cavity 1024^2 at Re = 1000, 200,000 steps in FP32, F16 and BF16 storage;
     its 128^2 twin against the oracle.

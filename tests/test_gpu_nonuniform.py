@@ -108,7 +108,7 @@ def test_nonuniform_couette_exact_on_gpu():
 
 @pytest.mark.parametrize("store", [0, 3])
 def test_nonuniform_original_model(store):
-    """The original DUGKS (eq. feq) on the tanh mesh: the model switch and the mesh metrics
+    """The original DUGKS (eq. (5)) on the tanh mesh: the model switch and the mesh metrics
     together, against the oracle with both."""
     case = CASES["cavity"]
     cfg = dict(q=9, nu=0.04, dt=_dt(case["faces"]), **case)

@@ -65,7 +65,7 @@ CASES_2D = {
     "cavity": dict(shape=(45, 38), q=9, nu=0.05, dt=0.5, bcs=W.cavity_bcs(2, 0.1)),
     "pressure": dict(shape=(36, 19), q=9, nu=0.04, dt=0.5,
                      bcs=[W.pressure(1e-3), W.pressure(-1e-3), W.wall(), W.wall()]),
-    # bounce-back walls (eq. BB): a closed box with a moving lid, and pressure-driven flow
+    # bounce-back walls (eq. (31)): a closed box with a moving lid, and pressure-driven flow
     # between bounce-back walls (NEQ pressure inlet and outlet)
     "bb_cavity": dict(shape=(45, 38), q=9, nu=0.05, dt=0.5,
                       bcs=[W.bounce_back(), W.bounce_back(), W.bounce_back(), W.bounce_back((0.1, 0.0))]),
@@ -258,7 +258,7 @@ ORIGINAL_CASES = {
 @pytest.mark.parametrize("name", sorted(ORIGINAL_CASES))
 @pytest.mark.parametrize("store", [0, 3])
 def test_original_model_state_elementwise(name, store):
-    """The original DUGKS (eq. feq, rho u = sum xi f~ + rho G dt/2) on the reference kernel
+    """The original DUGKS (eq. (5), rho u = sum xi f~ + rho G dt/2) on the reference kernel
     against the oracle's original model, with large velocities and pressure differences so the
     two models differ well beyond the tolerance."""
     from oracle import Oracle as Orc
@@ -285,7 +285,7 @@ def test_original_model_state_elementwise(name, store):
 
 
 def test_original_model_mass_under_force_fp64():
-    """With eq. feq the force term carries no mass: FP64 total mass stays to rounding."""
+    """With eq. (5) the force term carries no mass: FP64 total mass stays to rounding."""
     cfg = ORIGINAL_CASES["periodic_force"]
     p, u = W.random_state_fields(cfg["shape"], seed=5, u_amp=0.08, p_amp=3e-3)
     s = _sim(store=3, model=1, **cfg)

@@ -1,4 +1,4 @@
-"""Pins of the bounce-back wall (Sec. 2.4, eq. BB) in the oracle, by properties the equation
+"""Pins of the bounce-back wall (Sec. 2.4, eq. (31)) in the oracle, by properties the equation
 fixes exactly:
   * a bounce-back wall moving tangentially carries no mass. The incoming values are the
     outgoing ones plus 2 rho0 W_k xi_k.u_w / RT, whose xi_n moment cancels over the outgoing

@@ -3,7 +3,7 @@
 Every check is fixed by the mathematics of the scheme, not by re-running its formulas:
   * states that the paper's scheme must leave unchanged (rest, uniform flow, Couette);
   * symmetries (periodic translation, mirror);
-  * conservation and the momentum/mass bookkeeping of the force term (eqs. S, f_j+n);
+  * conservation and the momentum/mass bookkeeping of the force term (eqs. (9), (17));
   * closed-form flows (Couette exactly; Poiseuille, Kolmogorov and Womersley closely).
 """
 import numpy as np
@@ -116,8 +116,8 @@ def test_mass_conserved_periodic(q, shape):
 
 def test_force_bookkeeping_periodic():
     """With periodic boundaries the flux telescopes, so one step changes the totals only
-    through the collision and force terms of eq. f_j+n. Using sum_k xi_k S_k = rho G and
-    sum_k S_k = G.u (rho0 - rho)/RT (both from eqs. icfeq and S), per step
+    through the collision and force terms of eq. (17). Using sum_k xi_k S_k = rho G and
+    sum_k S_k = G.u (rho0 - rho)/RT (both from eqs. (6) and (9)), per step
       dJ = sum_cells dt (rho0 dt + 2 tau rho) G / (2 tau + dt),   J = sum_k xi_k f~,
       dM = sum_cells 2 tau dt/(2 tau + dt) G.u (rho0 - rho)/RT,   M = sum_k f~."""
     shape = (6, 5)
@@ -146,7 +146,7 @@ def test_force_bookkeeping_periodic():
 @pytest.mark.parametrize("q,shape,axis", [(9, (3, 8), 1), (19, (2, 6, 3), 1), (27, (2, 2, 6), 2)])
 def test_couette_is_exact(q, shape, axis):
     """A linear shear profile between a wall at rest and a moving wall (NEQ velocity
-    condition, eq. NEQ) is a steady state of the scheme to rounding: the linear
+    condition, eq. (32)) is a steady state of the scheme to rounding: the linear
     reconstruction and the linear ghost extrapolation are exact for it, and its
     non-equilibrium part is uniform, which the NEQ extrapolation copies exactly."""
     D = len(shape)
@@ -296,8 +296,8 @@ def test_table1_n64():
 
 
 def test_womersley_forms_agree():
-    """The complex form (eq. Wom_AS_Complex, with the reading lam^2 = -i alpha^2) and the
-    real K-form (eq. Wom_AS_Velocity) of Sec. 3.3 are the same function, and alpha = 3.963
+    """The complex form (eq. (39), with the reading lam^2 = -i alpha^2) and the
+    real K-form (eq. (42)) of Sec. 3.3 are the same function, and alpha = 3.963
     for the paper's nu = 1e-3, T = 100, Ly = 1."""
     Ly, nu, T = 1.0, 1e-3, 100.0
     omega = 2 * np.pi / T

@@ -1,4 +1,4 @@
-"""Pins of the oracle's velocity sets and equilibrium (Sec. 2.1, eq. icfeq; Sec. 2.3).
+"""Pins of the oracle's velocity sets and equilibrium (Sec. 2.1, eq. (6); Sec. 2.3).
 
 The checks are exact moment identities of Gauss-Hermite quadrature and of the He-Luo
 equilibrium, derived independently of the oracle's code: a dropped term, a wrong sign or a
@@ -62,7 +62,7 @@ def test_paper_index_order_and_weights():
 
 @pytest.mark.parametrize("q", [9, 19, 27])
 def test_equilibrium_moments(q):
-    """eq. icfeq: sum f_eq = rho, sum xi f_eq = rho0 u, sum xi xi f_eq = rho RT I + rho0 u u."""
+    """eq. (6): sum f_eq = rho, sum xi f_eq = rho0 u, sum xi xi f_eq = rho RT I + rho0 u u."""
     rng = np.random.default_rng(q)
     D = 2 if q == 9 else 3
     shape = (5, 4) if D == 2 else (3, 2, 2)
@@ -81,7 +81,7 @@ def test_equilibrium_moments(q):
     m2 = np.einsum("ka,kb,kn->abn", xi, xi, f)
     ref = rho[None, None, :] * rt * np.eye(D)[:, :, None] + rho0 * np.einsum("an,bn->abn", u, u)
     assert np.abs(m2 - ref).max() < 1e-13
-    # the incompressible form differs from the original eq. feq: rho enters only the
+    # the incompressible form differs from the original eq. (5): rho enters only the
     # zeroth-order term, so f_eq(rho, 0) = W rho and the velocity part is rho-independent.
     o.init(p=p, u=np.zeros((D, n)))
     f0 = o.get_state()

@@ -1,7 +1,7 @@
-"""Pins of the original DUGKS (the comparison model of Sec. 2.1-2.2: eq. feq with
+"""Pins of the original DUGKS (the comparison model of Sec. 2.1-2.2: eq. (5) with
 rho u = sum xi f~ + rho G dt/2) in the oracle, by what the equations fix exactly:
-  * eq. feq's moments: sum f_eq = rho, sum xi f_eq = rho u, sum xi xi f_eq = rho RT I + rho u u;
-  * with eq. feq the force term of eq. S has zero mass, sum_k S_k = G.(rho u - u rho)/RT = 0,
+  * eq. (5)'s moments: sum f_eq = rho, sum xi f_eq = rho u, sum xi xi f_eq = rho RT I + rho u u;
+  * with eq. (5) the force term of eq. (9) has zero mass, sum_k S_k = G.(rho u - u rho)/RT = 0,
     so a periodic box keeps its mass to rounding under any force. The incompressible model's S
     does not sum to zero when rho != rho0, which keeps the check discriminating;
   * at rho = rho0 the two equilibria coincide, so a uniform flow of density rho0 is a fixed

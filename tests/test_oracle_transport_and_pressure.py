@@ -1,6 +1,6 @@
 """Pins of two parts of the oracle that the flow tests leave loose.
 
-1. Steps 3-4 in 3D (eq. gradient with the cross points of step 3), through free transport.
+1. Steps 3-4 in 3D (eq. (23) with the cross points of step 3), through free transport.
    With tau -> infinity the collision coefficients of steps 1 and 7 vanish (b1 = 3h/(2 tau +
    dt) and b7 = h/(2 tau + h)), so one step moves every velocity independently:
    f~(n+1) = f~ - dt/dx xi_k . (flux difference) with the step-4 interface value. For a plane
@@ -17,7 +17,7 @@
    amplitude. Independently of the oracle, G_k agrees with exact transport
    exp(-i 2 kappa e_k . theta) to third order in theta (the scheme is second order).
 
-2. The NEQ pressure condition of Sec. 2.4 (eq. NEQ with rho_a = rho0 + p_w / RT, u_a = u_c).
+2. The NEQ pressure condition of Sec. 2.4 (eq. (32) with rho_a = rho0 + p_w / RT, u_a = u_c).
    A channel between a pressure inlet and outlet (p = +-dp/2) and NEQ no-slip walls has the
    steady solution u = dp / (2 rho0 nu L) y (H - y) with p linear in x. The oracle reproduces
    the linear pressure exactly (to rounding), the parabola at second order under refinement,
