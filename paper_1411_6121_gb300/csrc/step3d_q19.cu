@@ -119,7 +119,7 @@ static int zchunk_for(int64_t tiles, int nz, int64_t slots) {
     return (nz + best - 1) / best;
 }
 
-// The warp-specialised kernel (dugks_step3d_ws.cuh): 4 producer + 8 consumer warps, one CTA
+// The warp-specialised kernel (dugks_step3d_ws.cuh): 8 producer + 8 consumer warps, one CTA
 // per SM, 32 x 8 columns per tile.
 template <class S, bool FORCE>
 static cudaError_t launch_ws(const StepParams &p, cudaStream_t stream) {
