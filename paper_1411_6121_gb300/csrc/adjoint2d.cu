@@ -8,16 +8,18 @@
 // by running the sub-steps backwards in three gather-form kernels:
 //   adj_cells_fwd (per cell)       recomputes the cell moments (eq. (27)) and
 //                                  fbar+ (step 1, eq. (24));
-//   adj_faces     (per interface)  recomputes steps 3-7 and pulls lambda' back through the
+//   adj_faces_all (per interface)  recomputes steps 3-7 and pulls lambda' back through the
 //                                  flux (steps 8-9), the interface relaxation (step 7,
 //                                  eq. (20)), the interface moments (step 6) and the
 //                                  wall condition (step 5: eq. (32), or eq. (31)), down to the
 //                                  adjoint of the step-4 values and of the interface
 //                                  acceleration;
-//   adj_cells     (per cell)       transposes the reconstruction (steps 3-4, eq. (23))
+//   adj_cells_all (per cell)       transposes the reconstruction (steps 3-4, eq. (23))
 //                                  and the ghost extrapolation (step 2), then pulls the
 //                                  adjoint of fbar+ back through step 1 and the cell moments
-//                                  to g~^n and G.
+//                                  to g~^n and G; then it makes adj_cells_fwd's work for the
+//                                  next reverse step, which leaves adj_cells_fwd to the first
+//                                  reverse step of each checkpoint segment.
 // The interior of each kernel takes a fast path with compile-time velocities; the band along
 // walls, x_c interfaces and periodic seams takes the general path, one item per half-warp with
 // one velocity per lane. Every output element is a gather written by one thread, or by one lane
