@@ -5,7 +5,10 @@ sm_103a build (no GPU needed). Each budget is what a measured speed depends on:
     launches 512 threads at 128 registers and must not spill under its register split;
   * the batch's FP32 reference tiles run 4 CTAs of 256 threads (8 of 128) per SM only at
     <= 64 registers; 72 registers cost the 64-channel batch 15%;
-  * the D2Q9 throughput kernel (FP32) must not spill.
+  * the D2Q9 throughput kernel (FP32) must not spill;
+  * the adjoint's interface kernel runs 6 blocks of 128 threads per SM at <= 80 registers, and
+    its cells kernel (which also carries the next reverse step's recompute) 7 blocks at <= 72 in
+    FP32; neither spills, in FP32 or FP64.
 A change that breaks one of them shows here before any GPU run."""
 import pytest
 
@@ -55,3 +58,14 @@ def test_d3q27_throughput_kernel_spills_bounded(res):
     # x/y differences across the z march pushed it to 156)
     for k, v in _find(res, "fused_step3dILi27E", "Li8ELb0").items():
         assert v["spill_stores"] <= 64, (k, v)
+
+
+def test_adjoint_kernels_fit_their_blocks_per_sm(res):
+    for k, v in _find(res, "adj_faces_allIfE").items():
+        assert v["regs"] <= 80 and v["spill_stores"] == 0, (k, v)
+    for k, v in _find(res, "adj_cells_allIfE").items():
+        assert v["regs"] <= 72 and v["spill_stores"] == 0, (k, v)
+    for k, v in _find(res, "adj_faces_allIdE").items():
+        assert v["spill_stores"] == 0, (k, v)
+    for k, v in _find(res, "adj_cells_allIdE").items():
+        assert v["spill_stores"] == 0, (k, v)
